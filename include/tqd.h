@@ -1,0 +1,188 @@
+/*
+ * tqd.h -- C ABI of libtqd, a single-GPU differentiable state-vector
+ * simulator for GB300 (sm_103a).
+ *
+ * The library applies the gates of a parameterised circuit to a 2^n complex
+ * amplitude vector, evaluates Pauli-sum expectation values, and takes the
+ * adjoint (reverse-sweep) gradient of an expectation with respect to the gate
+ * angles, recomputing intermediate states instead of storing them.
+ *
+ * Paper: "TorchQuantumDistributed" (arXiv 2511.19291).
+ *   - state vector and gate (M, Q): Sec. 4.1, "Tensor dimension order";
+ *   - gate application Y = M x_Q X: Sec. 2.2 (contraction notation) and
+ *     Algorithm 1;
+ *   - measurement in the Z basis and expectation values: Sec. 2.2.1;
+ *   - backpropagation through unitaries by recomputation x = U^* y: Sec. 4.4.
+ *
+ * Conventions for every entry point:
+ *   - Qubit i is bit i of the flat amplitude index.  Amplitudes are
+ *     interleaved (re, im): float2 for TQD_C64, double2 for TQD_C128.
+ *   - For a k-qubit gate, wires[0] is the most significant bit of the gate's
+ *     local index; CNOT takes wires = {control, target}.
+ *   - R_P(t) = exp(-i t P / 2) for RX, RY, RZ; PHASE(t) = diag(1, e^{it});
+ *     CPHASE(t) = diag(1, 1, 1, e^{it}).
+ *   - Every call that takes a stream is asynchronous on that stream
+ *     (a cudaStream_t passed as void*; NULL is the legacy default stream).
+ *   - Arguments are validated on the host before any launch.  On error the
+ *     call returns a non-zero tqd_status, launches nothing and leaves a
+ *     message for tqd_last_error() (thread-local).  No C++ exception crosses
+ *     the ABI.
+ *   - Device pointers passed in are owned by the caller and must stay valid
+ *     until the work enqueued on the stream has finished.  Handles
+ *     (tqd_state, tqd_circuit) are owned by the caller and freed with the
+ *     matching *_free call; they may not be used by two streams at once.
+ */
+#ifndef LIBTQD_TQD_H_
+#define LIBTQD_TQD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TQD_OK = 0,
+    TQD_ERR_INVALID_ARG = 1, /* bad pointer, size, wire, index or alignment */
+    TQD_ERR_UNSUPPORTED = 2, /* valid request this build does not implement */
+    TQD_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    TQD_ERR_OOM = 4,         /* device or host allocation failed */
+    TQD_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    TQD_ERR_NUMERIC = 6      /* non-finite or out-of-range numeric input */
+} tqd_status;
+
+typedef enum { TQD_C64 = 0, TQD_C128 = 1 } tqd_dtype;
+
+typedef enum {
+    TQD_H = 0, TQD_X = 1, TQD_Y = 2, TQD_Z = 3, TQD_S = 4, TQD_T = 5,
+    TQD_RX = 6, TQD_RY = 7, TQD_RZ = 8, TQD_PHASE = 9,
+    TQD_CNOT = 10, TQD_CZ = 11, TQD_CPHASE = 12, TQD_SWAP = 13,
+    TQD_UNITARY1 = 14, /* arbitrary 2x2 unitary from the circuit's matrix table */
+    TQD_UNITARY2 = 15  /* arbitrary 4x4 unitary from the circuit's matrix table */
+} tqd_gate_kind;
+
+/* One gate (M, Q) of Sec. 4.1.  The angle of a parametric gate is
+ * dev_params[param_idx] when param_idx >= 0, otherwise `fixed`.  mat_idx is
+ * the offset, in complex entries, of a UNITARY1/UNITARY2 matrix (row-major)
+ * in the table given to tqd_circuit_create; -1 otherwise. */
+typedef struct {
+    uint32_t kind;
+    uint32_t nwires;
+    uint32_t wires[3];
+    int32_t param_idx;
+    double fixed;
+    int32_t mat_idx;
+    uint32_t reserved;
+} tqd_gate;
+
+/* coeff * i^{|x & z|} X^x Z^z: X on the bits of xmask, Z on the bits of
+ * zmask, a bit in both masks is Y. */
+typedef struct {
+    uint64_t xmask;
+    uint64_t zmask;
+    double coeff;
+} tqd_pauli_term;
+
+typedef enum {
+    TQD_PLAN_PLAIN = 0, /* one full-state sweep per gate (gate-by-gate path) */
+    TQD_PLAN_FUSED = 1  /* fused passes: low-qubit and mixed tiles, diagonal runs */
+} tqd_plan_mode;
+
+typedef struct {
+    uint32_t mode;        /* tqd_plan_mode */
+    uint32_t tile_qubits; /* fused tiles hold 2^tile_qubits amplitudes; 0 = default */
+    uint32_t low_qubits;  /* contiguous low qubits in every mixed tile; 0 = default */
+    uint32_t reserved[5]; /* must be zero */
+} tqd_plan_opts;
+
+typedef struct tqd_state tqd_state;
+typedef struct tqd_circuit tqd_circuit;
+
+/* ---------------------------------------------------------------- states */
+
+/* Wrap caller-owned device memory (e.g. a torch tensor) as an n-qubit state.
+ * dev_amps: device pointer, 256-byte aligned, at least 2^n * 8 (C64) or
+ * 2^n * 16 (C128) bytes.  1 <= n_qubits <= 34.  The handle never frees
+ * dev_amps.  Allocates only the small host handle. */
+tqd_status tqd_state_alloc(int n_qubits, tqd_dtype dtype, void *dev_amps, size_t bytes,
+                           tqd_state **out);
+
+/* psi = e_{basis_index} (the |0...0> reset of the appendix listings when
+ * basis_index = 0).  basis_index < 2^n. */
+tqd_status tqd_state_reset(tqd_state *state, uint64_t basis_index, void *stream);
+
+/* Frees the handle, never the amplitudes. NULL is accepted. */
+tqd_status tqd_state_free(tqd_state *state);
+
+/* -------------------------------------------------------------- circuits */
+
+/* Validate a gate list and build its launch plan (host work only, plus one
+ * device buffer for the per-gate matrices that tqd_apply_circuit fills from
+ * the angles on the device, so a captured CUDA graph stays valid as the
+ * angles change).  gates: host array of n_gates gates.  matrices: host array
+ * of n_matrix_entries complex entries as interleaved (re, im) doubles, read
+ * by UNITARY1/UNITARY2 gates; may be NULL when none is used.  opts may be
+ * NULL (fused plan, default tiles).  The library keeps its own copies. */
+tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
+                              const double *matrices, size_t n_matrix_entries,
+                              const tqd_plan_opts *opts, tqd_circuit **out);
+
+tqd_status tqd_circuit_free(tqd_circuit *circuit);
+
+/* Number of device launches one tqd_apply_circuit enqueues (for accounting). */
+tqd_status tqd_circuit_info(const tqd_circuit *circuit, int *n_passes, int *n_launches_apply,
+                            int *n_launches_backward);
+
+/* psi <- G_L ... G_1 psi (Sec. 4.1; gate semantics of Algorithm 1).
+ * dev_params: device array of n_params doubles (may be NULL when n_params
+ * is 0).  The state must have the circuit's qubit count. */
+tqd_status tqd_apply_circuit(tqd_state *state, const tqd_circuit *circuit, const double *dev_params,
+                             void *stream);
+
+/* ----------------------------------------------------------- observables */
+
+/* E = sum_j coeff_j <psi|P_j|psi> (Sec. 2.2.1), reduced in FP64, written to
+ * dev_out[0] (device).  terms: host array, copied into the launch.  Masks
+ * must lie below 2^n. */
+tqd_status tqd_expval(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms,
+                      double *dev_out, void *stream);
+
+/* Per-term values <psi|P_j|psi> (without coeff_j) to dev_out[0..n_terms);
+ * with Z_i terms this is measure_allZ of the appendix listings. */
+tqd_status tqd_expval_terms(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms,
+                            double *dev_out, void *stream);
+
+/* out = sum_j w_j coeff_j P_j psi.  dev_weights: device array of n_terms
+ * doubles, or NULL for all ones.  out must differ from psi and have the same
+ * qubit count and dtype. */
+tqd_status tqd_apply_observable(const tqd_state *psi, const tqd_pauli_term *terms, size_t n_terms,
+                                const double *dev_weights, tqd_state *out, void *stream);
+
+/* --------------------------------------------------------------- adjoint */
+
+/* Adjoint gradient (Sec. 4.4): with psi holding psi_L = U psi_0 (the state
+ * tqd_apply_circuit left), sets lambda = H psi_L for
+ * H = grad_scale * sum_j w_j coeff_j P_j, then sweeps the circuit in reverse,
+ * un-applying every gate from psi and lambda and adding
+ * 2 Re <lambda| dG/dtheta |psi_before> for every parametric gate to
+ * dev_grads[param_idx] (device, n_params doubles, accumulated, not zeroed).
+ * On return psi holds psi_0 again (the recomputation that replaces stored
+ * activations) and lambda holds U^dagger H psi_L.  lambda: a state of the
+ * same qubit count and dtype used as scratch.  dev_term_weights may be NULL
+ * (all ones). */
+tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *circuit,
+                        const double *dev_params, const tqd_pauli_term *terms, size_t n_terms,
+                        const double *dev_term_weights, double grad_scale, double *dev_grads,
+                        void *stream);
+
+/* ------------------------------------------------------------------ misc */
+
+const char *tqd_last_error(void);
+const char *tqd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBTQD_TQD_H_ */

@@ -1,0 +1,318 @@
+// api.cu -- the extern "C" entry points of libtqd: argument validation on the
+// host, handle management, and dispatch to the kernel launchers.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "plan.h"
+
+namespace tqd {
+
+static thread_local std::string g_error;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_error = buf;
+}
+
+int device_sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+// Makes `dev` current for the scope of one call and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static size_t amp_bytes(tqd_dtype d) { return d == TQD_C64 ? 8 : 16; }
+
+}  // namespace tqd
+
+using namespace tqd;
+
+#define CHECK_ARG(cond, ...)                  \
+    do {                                      \
+        if (!(cond)) {                        \
+            tqd::set_error(__VA_ARGS__);      \
+            return TQD_ERR_INVALID_ARG;       \
+        }                                     \
+    } while (0)
+
+#define CHECK_CUDA(expr)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            tqd::set_error("%s failed: %s", #expr, cudaGetErrorString(e_));               \
+            return e_ == cudaErrorMemoryAllocation ? TQD_ERR_OOM : TQD_ERR_CUDA;          \
+        }                                                                                 \
+    } while (0)
+
+#define GUARD(dev)                                                       \
+    DeviceGuard guard_(dev);                                             \
+    if (!guard_.ok) {                                                    \
+        tqd::set_error("cannot make device %d current", (int)(dev));     \
+        return TQD_ERR_CUDA;                                             \
+    }
+
+extern "C" {
+
+const char *tqd_last_error(void) { return g_error.c_str(); }
+
+const char *tqd_version(void) { return "tqd 0.1 (sm_103a)"; }
+
+// ----------------------------------------------------------------- states
+tqd_status tqd_state_alloc(int n_qubits, tqd_dtype dtype, void *dev_amps, size_t bytes, tqd_state **out) {
+    CHECK_ARG(out != nullptr, "tqd_state_alloc: out is NULL");
+    *out = nullptr;
+    CHECK_ARG(n_qubits >= 1 && n_qubits <= 34, "tqd_state_alloc: n_qubits %d outside [1, 34]", n_qubits);
+    CHECK_ARG(dtype == TQD_C64 || dtype == TQD_C128, "tqd_state_alloc: unknown dtype %d", (int)dtype);
+    CHECK_ARG(dev_amps != nullptr, "tqd_state_alloc: dev_amps is NULL");
+    CHECK_ARG(((uintptr_t)dev_amps & 255) == 0, "tqd_state_alloc: dev_amps is not 256-byte aligned");
+    const size_t need = ((size_t)1 << n_qubits) * amp_bytes(dtype);
+    CHECK_ARG(bytes >= need, "tqd_state_alloc: buffer of %zu bytes, %d qubits need %zu", bytes, n_qubits, need);
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, dev_amps);
+    if (e != cudaSuccess) {
+        set_error("tqd_state_alloc: cudaPointerGetAttributes: %s", cudaGetErrorString(e));
+        return TQD_ERR_CUDA;
+    }
+    CHECK_ARG(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged,
+              "tqd_state_alloc: dev_amps is not device memory");
+    tqd_state *s = new (std::nothrow) tqd_state;
+    if (!s) {
+        set_error("tqd_state_alloc: out of host memory");
+        return TQD_ERR_OOM;
+    }
+    s->n = n_qubits;
+    s->dtype = dtype;
+    s->amps = dev_amps;
+    s->bytes = bytes;
+    s->device = attr.device;
+    s->work = nullptr;
+    s->work_len = 0;
+    *out = s;
+    return TQD_OK;
+}
+
+tqd_status tqd_state_reset(tqd_state *state, uint64_t basis_index, void *stream) {
+    CHECK_ARG(state != nullptr, "tqd_state_reset: state is NULL");
+    CHECK_ARG(basis_index < ((uint64_t)1 << state->n), "tqd_state_reset: basis index out of range");
+    GUARD(state->device);
+    CHECK_CUDA(launch_reset(state, basis_index, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+tqd_status tqd_state_free(tqd_state *state) {
+    if (!state) return TQD_OK;
+    if (state->work) {
+        DeviceGuard g(state->device);
+        cudaFree(state->work);
+    }
+    delete state;
+    return TQD_OK;
+}
+
+// --------------------------------------------------------------- circuits
+tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
+                              const double *matrices, size_t n_matrix_entries, const tqd_plan_opts *opts,
+                              tqd_circuit **out) {
+    CHECK_ARG(out != nullptr, "tqd_circuit_create: out is NULL");
+    *out = nullptr;
+    CHECK_ARG(n_qubits >= 1 && n_qubits <= 34, "tqd_circuit_create: n_qubits %d outside [1, 34]", n_qubits);
+    CHECK_ARG(n_gates == 0 || gates != nullptr, "tqd_circuit_create: gates is NULL");
+    CHECK_ARG(n_gates <= (1u << 24), "tqd_circuit_create: too many gates");
+    CHECK_ARG(n_params >= 0, "tqd_circuit_create: negative n_params");
+    CHECK_ARG(n_matrix_entries == 0 || matrices != nullptr, "tqd_circuit_create: matrices is NULL");
+    tqd_plan_opts o;
+    memset(&o, 0, sizeof(o));
+    o.mode = TQD_PLAN_FUSED;
+    if (opts) {
+        o = *opts;
+        CHECK_ARG(o.mode == TQD_PLAN_PLAIN || o.mode == TQD_PLAN_FUSED, "tqd_circuit_create: unknown plan mode");
+        for (int i = 0; i < 5; ++i) CHECK_ARG(o.reserved[i] == 0, "tqd_circuit_create: reserved opts not zero");
+    }
+    std::vector<GateH> gs(n_gates);
+    for (size_t i = 0; i < n_gates; ++i) {
+        const tqd_gate &g = gates[i];
+        CHECK_ARG(g.kind <= TQD_UNITARY2, "gate %zu: unknown kind %u", i, g.kind);
+        const int k = gate_arity((int)g.kind);
+        CHECK_ARG((int)g.nwires == k, "gate %zu: kind %u takes %d wires, got %u", i, g.kind, k, g.nwires);
+        for (int a = 0; a < k; ++a) {
+            CHECK_ARG(g.wires[a] < (uint32_t)n_qubits, "gate %zu: wire %u >= n_qubits %d", i, g.wires[a], n_qubits);
+            for (int b = 0; b < a; ++b)
+                CHECK_ARG(g.wires[a] != g.wires[b], "gate %zu: duplicate wire %u", i, g.wires[a]);
+        }
+        if (g.param_idx >= 0) {
+            CHECK_ARG(gate_parametric((int)g.kind), "gate %zu: kind %u takes no angle", i, g.kind);
+            CHECK_ARG(g.param_idx < n_params, "gate %zu: param_idx %d >= n_params %d", i, g.param_idx, n_params);
+        } else {
+            CHECK_ARG(g.param_idx == -1, "gate %zu: param_idx %d (use -1 for a fixed angle)", i, g.param_idx);
+        }
+        if (!isfinite(g.fixed)) {
+            set_error("gate %zu: non-finite fixed angle", i);
+            return TQD_ERR_NUMERIC;
+        }
+        if (g.kind == TQD_UNITARY1 || g.kind == TQD_UNITARY2) {
+            const size_t d2 = g.kind == TQD_UNITARY1 ? 4 : 16;
+            CHECK_ARG(g.mat_idx >= 0 && (size_t)g.mat_idx + d2 <= n_matrix_entries,
+                      "gate %zu: matrix index %d outside the table of %zu entries", i, g.mat_idx, n_matrix_entries);
+        }
+        GateH &h = gs[i];
+        h.kind = (int)g.kind;
+        h.nw = k;
+        for (int a = 0; a < 3; ++a) h.w[a] = a < k ? (int)g.wires[a] : 0;
+        h.param = g.param_idx;
+        h.fixed = g.fixed;
+        h.mat = (g.kind == TQD_UNITARY1 || g.kind == TQD_UNITARY2) ? g.mat_idx : -1;
+    }
+    for (size_t i = 0; i < 2 * n_matrix_entries; ++i) {
+        if (!isfinite(matrices[i])) {
+            set_error("tqd_circuit_create: non-finite matrix entry");
+            return TQD_ERR_NUMERIC;
+        }
+    }
+    tqd_circuit *c = new (std::nothrow) tqd_circuit();
+    if (!c) {
+        set_error("tqd_circuit_create: out of host memory");
+        return TQD_ERR_OOM;
+    }
+    c->n = n_qubits;
+    c->n_params = n_params;
+    c->opts = o;
+    c->gates = std::move(gs);
+    c->table.assign(matrices ? matrices : (const double *)nullptr,
+                    matrices ? matrices + 2 * n_matrix_entries : (const double *)nullptr);
+    tqd_status st = build_circuit(c);
+    if (st != TQD_OK) {
+        tqd_circuit_free(c);
+        return st;
+    }
+    *out = c;
+    return TQD_OK;
+}
+
+tqd_status tqd_circuit_free(tqd_circuit *c) {
+    if (!c) return TQD_OK;
+    release_circuit(c);
+    delete c;
+    return TQD_OK;
+}
+
+tqd_status tqd_circuit_info(const tqd_circuit *c, int *n_passes, int *n_launches_apply, int *n_launches_backward) {
+    CHECK_ARG(c != nullptr, "tqd_circuit_info: circuit is NULL");
+    if (n_passes) *n_passes = c->n_passes;
+    if (n_launches_apply) *n_launches_apply = c->launches_apply;
+    if (n_launches_backward) *n_launches_backward = c->launches_backward;
+    return TQD_OK;
+}
+
+tqd_status tqd_apply_circuit(tqd_state *state, const tqd_circuit *c, const double *dev_params, void *stream) {
+    CHECK_ARG(state != nullptr && c != nullptr, "tqd_apply_circuit: NULL state or circuit");
+    CHECK_ARG(state->n == c->n, "tqd_apply_circuit: state has %d qubits, circuit %d", state->n, c->n);
+    CHECK_ARG(c->n_params == 0 || dev_params != nullptr, "tqd_apply_circuit: dev_params is NULL");
+    GUARD(state->device);
+    CHECK_CUDA(run_forward(state, c, dev_params, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+// ------------------------------------------------------------ observables
+static tqd_status check_terms(const tqd_state *st, const tqd_pauli_term *terms, size_t n_terms, const char *who) {
+    CHECK_ARG(n_terms == 0 || terms != nullptr, "%s: terms is NULL", who);
+    const uint64_t lim = st->n >= 64 ? ~0ull : (((uint64_t)1 << st->n) - 1);
+    for (size_t j = 0; j < n_terms; ++j) {
+        CHECK_ARG((terms[j].xmask & ~lim) == 0 && (terms[j].zmask & ~lim) == 0,
+                  "%s: term %zu acts on a qubit >= %d", who, j, st->n);
+        if (!isfinite(terms[j].coeff)) {
+            set_error("%s: term %zu has a non-finite coefficient", who, j);
+            return TQD_ERR_NUMERIC;
+        }
+    }
+    return TQD_OK;
+}
+
+tqd_status tqd_expval(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms, double *dev_out,
+                      void *stream) {
+    CHECK_ARG(state != nullptr, "tqd_expval: state is NULL");
+    CHECK_ARG(dev_out != nullptr, "tqd_expval: dev_out is NULL");
+    tqd_status st = check_terms(state, terms, n_terms, "tqd_expval");
+    if (st != TQD_OK) return st;
+    GUARD(state->device);
+    CHECK_CUDA(launch_expval(state, group_terms(terms, n_terms), (int)n_terms, 0, dev_out, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+tqd_status tqd_expval_terms(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms, double *dev_out,
+                            void *stream) {
+    CHECK_ARG(state != nullptr, "tqd_expval_terms: state is NULL");
+    CHECK_ARG(n_terms == 0 || dev_out != nullptr, "tqd_expval_terms: dev_out is NULL");
+    CHECK_ARG(n_terms < (1u << 20), "tqd_expval_terms: too many terms");
+    tqd_status st = check_terms(state, terms, n_terms, "tqd_expval_terms");
+    if (st != TQD_OK) return st;
+    GUARD(state->device);
+    CHECK_CUDA(launch_expval(state, group_terms(terms, n_terms), (int)n_terms, 1, dev_out, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+tqd_status tqd_apply_observable(const tqd_state *psi, const tqd_pauli_term *terms, size_t n_terms,
+                                const double *dev_weights, tqd_state *out, void *stream) {
+    CHECK_ARG(psi != nullptr && out != nullptr, "tqd_apply_observable: NULL state");
+    CHECK_ARG(psi != out && psi->amps != out->amps, "tqd_apply_observable: out must not alias psi");
+    CHECK_ARG(psi->n == out->n && psi->dtype == out->dtype, "tqd_apply_observable: state shapes differ");
+    tqd_status st = check_terms(psi, terms, n_terms, "tqd_apply_observable");
+    if (st != TQD_OK) return st;
+    GUARD(psi->device);
+    CHECK_CUDA(launch_apply_observable(psi, group_terms(terms, n_terms), dev_weights, 1.0, out,
+                                       (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *c, const double *dev_params,
+                        const tqd_pauli_term *terms, size_t n_terms, const double *dev_term_weights,
+                        double grad_scale, double *dev_grads, void *stream) {
+    CHECK_ARG(psi != nullptr && lambda != nullptr && c != nullptr, "tqd_backward: NULL handle");
+    CHECK_ARG(psi != lambda && psi->amps != lambda->amps, "tqd_backward: lambda must not alias psi");
+    CHECK_ARG(psi->n == c->n && lambda->n == c->n, "tqd_backward: qubit counts differ");
+    CHECK_ARG(psi->dtype == lambda->dtype, "tqd_backward: psi and lambda dtypes differ");
+    CHECK_ARG(c->n_params == 0 || dev_params != nullptr, "tqd_backward: dev_params is NULL");
+    CHECK_ARG(c->n_params == 0 || dev_grads != nullptr, "tqd_backward: dev_grads is NULL");
+    if (!isfinite(grad_scale)) {
+        tqd::set_error("tqd_backward: non-finite grad_scale");
+        return TQD_ERR_NUMERIC;
+    }
+    tqd_status st = check_terms(psi, terms, n_terms, "tqd_backward");
+    if (st != TQD_OK) return st;
+    GUARD(psi->device);
+    CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(terms, n_terms), dev_term_weights, grad_scale,
+                            dev_grads, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+}  // extern "C"

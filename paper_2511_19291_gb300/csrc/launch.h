@@ -1,0 +1,42 @@
+// launch.h -- host launchers of the libtqd kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace tqd {
+
+// Grid for the full-state streaming kernels: a multiple of the SM count.
+int stream_grid(uint64_t units, int threads);
+
+// Per-gate matrices from the angles (double and float copies).
+cudaError_t launch_prep(const tqd_circuit *c, const double *dev_params, cudaStream_t s);
+
+// psi = e_j.
+cudaError_t launch_reset(tqd_state *st, uint64_t j, cudaStream_t s);
+
+// Gate-by-gate path: one full-state kernel for gate g (adjoint: its inverse).
+cudaError_t launch_plain_gate(tqd_state *st, const tqd_circuit *c, int g, bool adjoint, cudaStream_t s);
+
+// Gate-by-gate reverse step: contribution of gate g to its parameter's
+// gradient from (psi, lambda), then both un-applied.  partials: pblk doubles.
+cudaError_t launch_plain_adjoint_gate(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int g,
+                                      double *partials, int pblk, cudaStream_t s);
+
+// Sum gradient partials into grads (fixed order).
+cudaError_t launch_grad_finalize(const tqd_circuit *c, int nblk, double *dev_grads, cudaStream_t s);
+
+// Pauli sums.  mode 0: total E; mode 1: per-term values.
+cudaError_t launch_expval(const tqd_state *st, const std::vector<PauliGroup> &groups, int n_terms,
+                          int mode, double *dev_out, cudaStream_t s);
+// out = scale * sum_j w_j c_j P_j psi.
+cudaError_t launch_apply_observable(const tqd_state *psi, const std::vector<PauliGroup> &groups,
+                                    const double *dev_weights, double scale, tqd_state *out,
+                                    cudaStream_t s);
+
+// Grows st->work to at least `len` doubles (stream-ordered).
+cudaError_t ensure_work(tqd_state *st, size_t len, cudaStream_t s);
+
+}  // namespace tqd

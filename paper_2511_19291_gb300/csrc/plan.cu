@@ -1,0 +1,140 @@
+// plan.cu -- circuit planning (host) and the forward / backward executors.
+#include <string.h>
+
+#include <vector>
+
+#include "launch.h"
+#include "plan.h"
+
+namespace tqd {
+
+template <typename T>
+static cudaError_t upload(T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Blocks used by every gate-by-gate adjoint step of an n-qubit state.
+static int plain_adjoint_blocks(int n) {
+    if (n < 4) return 1;
+    return stream_grid(((uint64_t)1 << n) / 4, 256);
+}
+
+tqd_status build_circuit(tqd_circuit *c) {
+    const int ng = (int)c->gates.size();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    c->device = dev;
+    c->d_gates = nullptr;
+    c->d_table = nullptr;
+    c->d_mats64 = nullptr;
+    c->d_mats32 = nullptr;
+    c->d_partials = nullptr;
+    c->d_slot_sums = nullptr;
+    c->d_param_ptr = nullptr;
+    c->d_param_slots = nullptr;
+
+    // gradient slots: one per parametric gate that reads the parameter vector
+    c->grad_slot.assign(ng, -1);
+    c->n_slots = 0;
+    std::vector<std::vector<int>> by_param(c->n_params);
+    for (int g = 0; g < ng; ++g) {
+        const GateH &h = c->gates[g];
+        if (h.param >= 0 && gate_parametric(h.kind)) {
+            c->grad_slot[g] = c->n_slots;
+            by_param[h.param].push_back(c->n_slots);
+            ++c->n_slots;
+        }
+    }
+    std::vector<int> ptr(c->n_params + 1, 0), slots;
+    for (int p = 0; p < c->n_params; ++p) {
+        ptr[p + 1] = ptr[p] + (int)by_param[p].size();
+        for (int s : by_param[p]) slots.push_back(s);
+    }
+    c->pblk = plain_adjoint_blocks(c->n);
+
+    std::vector<GateDev> gd(ng);
+    for (int g = 0; g < ng; ++g) {
+        gd[g].kind = c->gates[g].kind;
+        gd[g].param = c->gates[g].param;
+        gd[g].mat = c->gates[g].mat;
+        gd[g].pad = 0;
+        gd[g].fixed = c->gates[g].fixed;
+    }
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t err) {
+        set_error("tqd_circuit_create: %s", cudaGetErrorString(err));
+        return err == cudaErrorMemoryAllocation ? TQD_ERR_OOM : TQD_ERR_CUDA;
+    };
+    if ((e = upload(&c->d_gates, gd)) != cudaSuccess) return fail(e);
+    if ((e = upload(&c->d_table, c->table)) != cudaSuccess) return fail(e);
+    if (ng > 0) {
+        if ((e = cudaMalloc((void **)&c->d_mats64, (size_t)ng * MAT_STRIDE * sizeof(double))) != cudaSuccess)
+            return fail(e);
+        if ((e = cudaMalloc((void **)&c->d_mats32, (size_t)ng * MAT_STRIDE * sizeof(float))) != cudaSuccess)
+            return fail(e);
+    }
+    if (c->n_slots > 0) {
+        if ((e = cudaMalloc((void **)&c->d_partials, (size_t)c->n_slots * c->pblk * sizeof(double))) != cudaSuccess)
+            return fail(e);
+        if ((e = cudaMalloc((void **)&c->d_slot_sums, (size_t)c->n_slots * sizeof(double))) != cudaSuccess)
+            return fail(e);
+    }
+    if ((e = upload(&c->d_param_ptr, ptr)) != cudaSuccess) return fail(e);
+    if ((e = upload(&c->d_param_slots, slots)) != cudaSuccess) return fail(e);
+
+    // plain plan: one launch per gate (two for 2-qubit permutations in reverse)
+    c->n_passes = ng;
+    c->launches_apply = ng + (ng > 0 ? 1 : 0);
+    int back = 0;
+    for (int g = 0; g < ng; ++g) {
+        const GateH &h = c->gates[g];
+        const bool one = gate_arity(h.kind) == 1 || h.kind == TQD_CPHASE || h.kind == TQD_CZ || c->n < 4;
+        back += one ? 1 : 2;
+    }
+    c->launches_backward = back + (ng > 0 ? 1 : 0) + (c->n_slots > 0 ? 2 : 0);
+    return TQD_OK;
+}
+
+void release_circuit(tqd_circuit *c) {
+    cudaFree(c->d_gates);
+    cudaFree(c->d_table);
+    cudaFree(c->d_mats64);
+    cudaFree(c->d_mats32);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_slot_sums);
+    cudaFree(c->d_param_ptr);
+    cudaFree(c->d_param_slots);
+}
+
+cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s) {
+    cudaError_t e = launch_prep(c, dev_params, s);
+    if (e != cudaSuccess) return e;
+    for (int g = 0; g < (int)c->gates.size(); ++g) {
+        e = launch_plain_gate(psi, c, g, false, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
+                         const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
+                         double *dev_grads, cudaStream_t s) {
+    cudaError_t e = launch_prep(c, dev_params, s);
+    if (e != cudaSuccess) return e;
+    e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s);
+    if (e != cudaSuccess) return e;
+    const int nblk = plain_adjoint_blocks(c->n);
+    for (int g = (int)c->gates.size() - 1; g >= 0; --g) {
+        const int slot = c->grad_slot[g];
+        double *part = slot >= 0 ? c->d_partials + (size_t)slot * c->pblk : nullptr;
+        e = launch_plain_adjoint_gate(psi, lam, c, g, part, c->pblk, s);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_grad_finalize(c, nblk, dev_grads, s);
+}
+
+}  // namespace tqd

@@ -1,0 +1,22 @@
+// plan.h -- circuit planning and the forward / backward executors (internal).
+#pragma once
+
+#include <vector>
+
+#include "internal.h"
+
+namespace tqd {
+
+// Validated circuit -> device buffers and launch plan.
+tqd_status build_circuit(tqd_circuit *c);
+void release_circuit(tqd_circuit *c);
+
+// psi <- U psi (prep + plain or fused passes).
+cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s);
+
+// lambda = scale * H psi, reverse sweep, gradients accumulated into dev_grads.
+cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
+                         const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
+                         double *dev_grads, cudaStream_t s);
+
+}  // namespace tqd

@@ -1,0 +1,308 @@
+"""Python front end of libtqd: argument marshalling only.
+
+Every step of the simulation runs in the CUDA library; this module turns
+torch tensors and the gate/term descriptions of ``workloads`` into the C ABI
+arguments (device pointers, sizes, the current CUDA stream).
+
+* ``State``      -- a 2^n complex64/complex128 CUDA tensor wrapped as a tqd_state
+* ``Circuit``    -- a planned gate list (tqd_circuit)
+* ``Observable`` -- a marshalled Pauli sum
+* ``apply``, ``expval``, ``expval_terms``, ``apply_observable``, ``backward``
+* ``expval_fn``  -- differentiable E(theta) (torch.autograd.Function)
+* ``measure_allz_fn`` -- differentiable per-qubit <Z_i> (the appendix's measure_allZ)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from . import workloads as W
+
+
+def _L():
+    return _lib.load()
+
+
+def _stream(device) -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def pauli_masks(term: W.PauliTerm) -> tuple:
+    """(xmask, zmask): X sets the x bit, Z the z bit, Y both."""
+    x = z = 0
+    for q, p in term.ops:
+        bit = 1 << q
+        if p == "X":
+            x |= bit
+        elif p == "Z":
+            z |= bit
+        elif p == "Y":
+            x |= bit
+            z |= bit
+        else:
+            raise ValueError(f"unknown Pauli {p!r}")
+    return x, z
+
+
+class Observable:
+    """A Pauli sum marshalled once into the tqd_pauli_term layout."""
+
+    def __init__(self, terms):
+        if isinstance(terms, Observable):
+            terms = terms.terms
+        self.terms = list(terms)
+        self.arr = (_lib.PauliTerm * max(1, len(self.terms)))()
+        for j, t in enumerate(self.terms):
+            x, z = pauli_masks(t)
+            self.arr[j].xmask = x
+            self.arr[j].zmask = z
+            self.arr[j].coeff = float(t.coeff)
+
+    def __len__(self):
+        return len(self.terms)
+
+    @property
+    def ptr(self):
+        return C.cast(self.arr, C.c_void_p)
+
+
+def as_observable(obs) -> Observable:
+    return obs if isinstance(obs, Observable) else Observable(obs)
+
+
+class State:
+    """An n-qubit state over a contiguous CUDA tensor of 2^n complex amplitudes."""
+
+    def __init__(self, n: int, dtype=torch.complex64, device="cuda", tensor: torch.Tensor | None = None):
+        if tensor is None:
+            tensor = torch.empty(1 << n, dtype=dtype, device=device)
+        if not tensor.is_cuda:
+            raise ValueError("state tensor must be on a CUDA device")
+        if tensor.dtype not in (torch.complex64, torch.complex128):
+            raise ValueError("state tensor must be complex64 or complex128")
+        if tensor.numel() != (1 << n) or not tensor.is_contiguous():
+            raise ValueError("state tensor must be contiguous with 2^n elements")
+        self.n = n
+        self.tensor = tensor
+        self.device = tensor.device
+        self.dtype_code = _lib.C64 if tensor.dtype == torch.complex64 else _lib.C128
+        h = C.c_void_p()
+        _lib.check(_L().tqd_state_alloc(n, self.dtype_code, C.c_void_p(tensor.data_ptr()),
+                                        tensor.numel() * tensor.element_size(), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reset(self, basis_index: int = 0):
+        with torch.cuda.device(self.device):
+            _lib.check(_L().tqd_state_reset(self._h, basis_index, _stream(self.device)))
+        return self
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _L().tqd_state_free(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+class Circuit:
+    """A gate list planned by the library (plain gate-by-gate or fused passes)."""
+
+    def __init__(self, circuit: W.Circuit, mode: str = "fused", tile_qubits: int = 0, low_qubits: int = 0,
+                 device=None):
+        self.spec = circuit
+        self.n = circuit.n_qubits
+        self.n_params = circuit.n_params
+        self.mode = mode
+        gates = circuit.gates
+        arr = (_lib.Gate * max(1, len(gates)))()
+        table = []
+        for i, g in enumerate(gates):
+            a = arr[i]
+            a.kind = _lib.KIND_CODES[g.kind]
+            a.nwires = len(g.wires)
+            for j, w in enumerate(g.wires):
+                a.wires[j] = int(w)
+            a.param_idx = int(g.param)
+            a.fixed = float(g.angle)
+            a.mat_idx = -1
+            if g.kind in ("UNITARY1", "UNITARY2"):
+                a.mat_idx = len(table)
+                table.extend(np.asarray(g.matrix, dtype=np.complex128).reshape(-1).tolist())
+        mats = np.array([[v.real, v.imag] for v in table], dtype=np.float64).reshape(-1)
+        opts = _lib.PlanOpts()
+        opts.mode = _lib.PLAN_PLAIN if mode == "plain" else _lib.PLAN_FUSED
+        opts.tile_qubits = tile_qubits
+        opts.low_qubits = low_qubits
+        h = C.c_void_p()
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(dev):
+            _lib.check(_L().tqd_circuit_create(
+                self.n, C.cast(arr, C.c_void_p), len(gates), self.n_params,
+                mats.ctypes.data_as(C.c_void_p) if len(table) else None, len(table),
+                C.byref(opts), C.byref(h)))
+        self._h = h
+        self._mats = mats
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _lib.check(_L().tqd_circuit_info(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"passes": a.value, "launches_apply": b.value, "launches_backward": c.value}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _L().tqd_circuit_free(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+def _params_ptr(params: torch.Tensor | None, n_params: int):
+    if n_params == 0:
+        return None
+    if params is None or not params.is_cuda or params.dtype != torch.float64 or not params.is_contiguous():
+        raise ValueError("params must be a contiguous float64 CUDA tensor")
+    if params.numel() < n_params:
+        raise ValueError(f"params has {params.numel()} entries, circuit needs {n_params}")
+    return C.c_void_p(params.data_ptr())
+
+
+def apply(state: State, circuit: Circuit, params: torch.Tensor | None = None) -> State:
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_apply_circuit(state.handle, circuit.handle, _params_ptr(params, circuit.n_params),
+                                          _stream(state.device)))
+    return state
+
+
+def expval(state: State, obs, out: torch.Tensor | None = None) -> torch.Tensor:
+    obs = as_observable(obs)
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=state.device)
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_expval(state.handle, obs.ptr, len(obs), C.c_void_p(out.data_ptr()),
+                                   _stream(state.device)))
+    return out
+
+
+def expval_terms(state: State, obs, out: torch.Tensor | None = None) -> torch.Tensor:
+    obs = as_observable(obs)
+    if out is None:
+        out = torch.empty(len(obs), dtype=torch.float64, device=state.device)
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_expval_terms(state.handle, obs.ptr, len(obs),
+                                         C.c_void_p(out.data_ptr()) if len(obs) else None, _stream(state.device)))
+    return out
+
+
+def apply_observable(state: State, obs, weights: torch.Tensor | None = None, out: State | None = None) -> State:
+    obs = as_observable(obs)
+    if out is None:
+        out = State(state.n, state.tensor.dtype, state.device)
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_apply_observable(state.handle, obs.ptr, len(obs), _weights_ptr(weights, len(obs)),
+                                             out.handle, _stream(state.device)))
+    return out
+
+
+def _weights_ptr(weights, n_terms):
+    if weights is None:
+        return None
+    if not weights.is_cuda or weights.dtype != torch.float64 or not weights.is_contiguous() or \
+            weights.numel() < n_terms:
+        raise ValueError("weights must be a contiguous float64 CUDA tensor with one entry per term")
+    return C.c_void_p(weights.data_ptr())
+
+
+def backward(psi: State, lam: State, circuit: Circuit, params: torch.Tensor | None, obs,
+             grads: torch.Tensor | None, weights: torch.Tensor | None = None, scale: float = 1.0) -> torch.Tensor:
+    """Adjoint sweep: grads += d(scale * sum_j w_j c_j <P_j>)/dparams; psi is restored to
+    the circuit's input state."""
+    obs = as_observable(obs)
+    if grads is None:
+        grads = torch.zeros(max(circuit.n_params, 0), dtype=torch.float64, device=psi.device)
+    gptr = C.c_void_p(grads.data_ptr()) if circuit.n_params else None
+    with torch.cuda.device(psi.device):
+        _lib.check(_L().tqd_backward(psi.handle, lam.handle, circuit.handle, _params_ptr(params, circuit.n_params),
+                                     obs.ptr, len(obs), _weights_ptr(weights, len(obs)), float(scale), gptr,
+                                     _stream(psi.device)))
+    return grads
+
+
+# ------------------------------------------------------------------ autograd
+class _ExpvalFn(torch.autograd.Function):
+    """E(theta) = <psi_L|H|psi_L>.  Forward keeps only theta and psi_L; backward
+    recomputes earlier states by un-applying the circuit (Sec. 4.4)."""
+
+    @staticmethod
+    def forward(ctx, params, circuit, obs, dtype, basis_index):
+        psi = State(circuit.n, dtype, params.device).reset(basis_index)
+        apply(psi, circuit, params)
+        e = expval(psi, obs)
+        ctx.save_for_backward(params)
+        ctx.psi, ctx.circuit, ctx.obs = psi, circuit, obs
+        return e
+
+    @staticmethod
+    def backward(ctx, grad_e):
+        (params,) = ctx.saved_tensors
+        psi = ctx.psi
+        if psi is None:
+            raise RuntimeError("this expectation's backward already ran (the saved state is consumed)")
+        lam = State(psi.n, psi.tensor.dtype, psi.device)
+        w = grad_e.reshape(1).to(torch.float64).expand(len(ctx.obs)).contiguous()
+        grads = torch.zeros_like(params)
+        backward(psi, lam, ctx.circuit, params, ctx.obs, grads, weights=w)
+        ctx.psi = None
+        return grads, None, None, None, None
+
+
+class _MeasureFn(torch.autograd.Function):
+    """Per-term values <P_j> (e.g. <Z_i>), differentiable with a vector grad."""
+
+    @staticmethod
+    def forward(ctx, params, circuit, obs, dtype, basis_index):
+        psi = State(circuit.n, dtype, params.device).reset(basis_index)
+        apply(psi, circuit, params)
+        out = expval_terms(psi, obs)
+        ctx.save_for_backward(params)
+        ctx.psi, ctx.circuit, ctx.obs = psi, circuit, obs
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (params,) = ctx.saved_tensors
+        psi = ctx.psi
+        if psi is None:
+            raise RuntimeError("this measurement's backward already ran (the saved state is consumed)")
+        lam = State(psi.n, psi.tensor.dtype, psi.device)
+        # The per-term outputs carry no coefficient: weight_j = grad_j / coeff_j
+        # cancels the coefficient applied inside the library.
+        coeffs = torch.tensor([t.coeff for t in ctx.obs.terms], dtype=torch.float64, device=params.device)
+        w = (grad_out.to(torch.float64) / coeffs).contiguous()
+        grads = torch.zeros_like(params)
+        backward(psi, lam, ctx.circuit, params, ctx.obs, grads, weights=w)
+        ctx.psi = None
+        return grads, None, None, None, None
+
+
+def expval_fn(params: torch.Tensor, circuit: Circuit, obs, dtype=torch.complex64, basis_index: int = 0):
+    return _ExpvalFn.apply(params, circuit, as_observable(obs), dtype, basis_index)
+
+
+def measure_allz_fn(params: torch.Tensor, circuit: Circuit, dtype=torch.complex64, basis_index: int = 0):
+    obs = Observable(W.all_z_terms(circuit.n))
+    return _MeasureFn.apply(params, circuit, obs, dtype, basis_index)

@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element
+by element on the same seeded inputs (states, expectations, H psi, gradients),
+for both plans (gate-by-gate and fused) and both precisions."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2511_19291_gb300 import workloads as W
+from gpu_helpers import (AMP_TOL, DTYPES, E_TOL, G_REL, all_kinds_circuit, gpu_state, grad_close,
+                         params_tensor, sim, to_numpy)
+
+pytestmark = pytest.mark.gpu
+MODES = ["plain", "fused"]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,ng,seed", [(1, 12, 1), (2, 30, 2), (3, 60, 3), (4, 80, 4), (5, 120, 5),
+                                       (8, 200, 6), (11, 300, 7), (13, 300, 8), (14, 250, 9), (17, 120, 10)])
+def test_state_parity_all_gate_kinds(mode, dtype, n, ng, seed):
+    circ, params = all_kinds_circuit(1000 + seed, n, ng)
+    st, _, _ = gpu_state(circ, params, mode, dtype, basis=(seed * 7919) % (1 << n))
+    ref = oracle.run(circ, params, (seed * 7919) % (1 << n))
+    got = to_numpy(st)
+    tol = AMP_TOL[dtype] * math.sqrt(ng / 100 + 1)
+    np.testing.assert_allclose(got, ref, atol=tol, rtol=0)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,layers", [(4, 2), (12, 4), (13, 3), (15, 2)])
+def test_ansatz_state_parity(mode, n, layers):
+    circ = W.hea_ansatz(n, layers)
+    params = W.config_rng(1).angles(circ.n_params)
+    st, _, _ = gpu_state(circ, params, mode, "c64")
+    np.testing.assert_allclose(to_numpy(st), oracle.run(circ, params), atol=4e-6, rtol=0)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,seed", [(1, 1), (3, 2), (6, 3), (12, 4), (15, 5)])
+def test_expval_parity(dtype, n, seed):
+    S = sim()
+    rng = W.SplitMix64(2000 + seed)
+    circ, params = W.random_circuit(rng, n, 40 + 10 * n)
+    terms = W.random_pauli_terms(rng, n, 30) + (W.ising(n) if n > 1 else []) + W.sum_z(n)
+    st, _, _ = gpu_state(circ, params, "fused", dtype)
+    psi = oracle.run(circ, params)
+    e_ref, per_ref = oracle.expval(n, psi, terms)
+    e = S.expval(st, terms).item()
+    per = S.expval_terms(st, terms).cpu().numpy()
+    assert abs(e - e_ref) <= E_TOL[dtype] * max(1.0, W.observable_l1(terms) / 10)
+    np.testing.assert_allclose(per, per_ref, atol=E_TOL[dtype], rtol=0)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,seed", [(2, 1), (7, 2), (13, 3)])
+def test_apply_observable_parity(dtype, n, seed):
+    S = sim()
+    rng = W.SplitMix64(3000 + seed)
+    circ, params = W.random_circuit(rng, n, 60)
+    terms = W.random_pauli_terms(rng, n, 20) + W.ising(n)
+    st, _, _ = gpu_state(circ, params, "fused", dtype)
+    out = S.apply_observable(st, terms)
+    ref = oracle.apply_observable(n, oracle.run(circ, params), terms)
+    np.testing.assert_allclose(to_numpy(out), ref, atol=AMP_TOL[dtype] * 30, rtol=0)
+    w = np.linspace(-1.5, 2.0, len(terms))
+    outw = S.apply_observable(st, terms, weights=params_tensor(w))
+    terms_w = [W.PauliTerm(t.coeff * wi, t.ops) for t, wi in zip(terms, w)]
+    refw = oracle.apply_observable(n, oracle.run(circ, params), terms_w)
+    np.testing.assert_allclose(to_numpy(outw), refw, atol=AMP_TOL[dtype] * 60, rtol=0)
+
+
+def gpu_grad(circ, params, terms, mode, dtype, weights=None, scale=1.0):
+    S = sim()
+    st, c, p = gpu_state(circ, params, mode, dtype)
+    lam = S.State(circ.n_qubits, DTYPES[dtype])
+    g = torch.zeros(circ.n_params, dtype=torch.float64, device="cuda")
+    S.backward(st, lam, c, p, terms, g, weights=weights, scale=scale)
+    torch.cuda.synchronize()
+    return g.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,ng,seed", [(1, 10, 1), (2, 20, 2), (3, 40, 3), (5, 60, 4), (6, 80, 5), (9, 60, 6)])
+def test_gradient_parity_random(mode, dtype, n, ng, seed):
+    rng = W.SplitMix64(4000 + seed)
+    circ, params = W.random_circuit(rng, n, ng, n_params=max(2, ng // 3))
+    terms = W.random_pauli_terms(rng, n, 8) + W.sum_z(n)
+    ref = oracle.grad_param_shift(circ, params, terms)
+    g, st = gpu_grad(circ, params, terms, mode, dtype)
+    ok, worst = grad_close(g, ref, G_REL[dtype])
+    assert ok, f"worst relative error {worst}"
+    # the reverse sweep leaves the input state |0...0> behind
+    back = to_numpy(st)
+    e0 = np.zeros(1 << n, dtype=complex)
+    e0[0] = 1
+    np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 10 * math.sqrt(ng), rtol=0)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,layers", [(6, 3), (12, 2), (14, 2)])
+def test_gradient_parity_ansatz_ising(mode, n, layers):
+    circ = W.hea_ansatz(n, layers)
+    params = W.config_rng(3).angles(circ.n_params)
+    terms = W.ising(n)
+    ref = oracle.grad_param_shift(circ, params, terms)
+    for dtype in ("c64", "c128"):
+        g, _ = gpu_grad(circ, params, terms, mode, dtype)
+        ok, worst = grad_close(g, ref, G_REL[dtype])
+        assert ok, f"{dtype}: worst relative error {worst}"
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_gradient_weights_and_scale(mode):
+    n = 7
+    rng = W.SplitMix64(4500)
+    circ, params = W.random_circuit(rng, n, 70, n_params=20)
+    terms = W.random_pauli_terms(rng, n, 6)
+    w = np.array([0.5, -1.0, 2.0, 0.0, 1.5, -0.25])
+    scale = 0.75
+    ref = oracle.grad_param_shift(circ, params, [W.PauliTerm(t.coeff * wi * scale, t.ops) for t, wi in zip(terms, w)])
+    g, _ = gpu_grad(circ, params, terms, mode, "c128", weights=params_tensor(w), scale=scale)
+    ok, worst = grad_close(g, ref, 1e-10)
+    assert ok, worst
+
+
+def test_gradients_accumulate():
+    n = 5
+    circ = W.hea_ansatz(n, 2)
+    params = W.config_rng(3).angles(circ.n_params)
+    ref = oracle.grad_param_shift(circ, params, W.sum_z(n))
+    S = sim()
+    st, c, p = gpu_state(circ, params, "fused", "c128")
+    lam = S.State(n, torch.complex128)
+    g = torch.full((circ.n_params,), 1.0, dtype=torch.float64, device="cuda")
+    S.backward(st, lam, c, p, W.sum_z(n), g)
+    np.testing.assert_allclose(g.cpu().numpy(), ref + 1.0, atol=1e-11)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_autograd_function(mode):
+    S = sim()
+    n = 10
+    circ = W.hea_ansatz(n, 3)
+    params = W.config_rng(3).angles(circ.n_params)
+    c = S.Circuit(circ, mode=mode)
+    p = params_tensor(params).requires_grad_(True)
+    e = S.expval_fn(p, c, W.ising(n))
+    (2.5 * e).backward()
+    ref_e = oracle.energy(circ, params, W.ising(n))
+    ref_g = oracle.grad_param_shift(circ, params, W.ising(n))
+    assert abs(e.item() - ref_e) < 1e-5
+    ok, worst = grad_close(p.grad.cpu().numpy(), 2.5 * ref_g, 1e-4)
+    assert ok, worst
+
+
+def test_measure_allz_autograd():
+    S = sim()
+    n = 6
+    circ = W.ladder_ansatz(n, 3)
+    params = W.config_rng(2).angles(circ.n_params)
+    c = S.Circuit(circ)
+    p = params_tensor(params).requires_grad_(True)
+    z = S.measure_allz_fn(p, c, dtype=torch.complex128)
+    psi = oracle.run(circ, params)
+    _, ref = oracle.expval(n, psi, W.all_z_terms(n))
+    np.testing.assert_allclose(z.detach().cpu().numpy(), ref, atol=1e-12)
+    wts = torch.linspace(-1, 1, n, dtype=torch.float64, device="cuda")
+    (z * wts).sum().backward()
+    terms = [W.PauliTerm(float(wi), t.ops) for t, wi in zip(W.all_z_terms(n), wts.cpu().numpy())]
+    ok, worst = grad_close(p.grad.cpu().numpy(), oracle.grad_param_shift(circ, params, terms), 1e-10)
+    assert ok, worst
+
+
+def test_basic_example_allz():
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "basic_example.json")))
+    n = g["n_qubits"]
+    gates = [W.Gate(k, tuple(w), angle=a) for k, w, a in g["gates"]]
+    st, _, _ = gpu_state(W.Circuit(n, gates, 0), None, "fused", "c64")
+    z = sim().expval_terms(st, W.all_z_terms(n)).cpu().numpy()
+    np.testing.assert_allclose(z, g["expected_allZ"], atol=1e-6)
+
+
+def test_empty_circuit_and_empty_observable():
+    S = sim()
+    for n in (1, 5, 13):
+        st, _, _ = gpu_state(W.Circuit(n, [], 0), None, "fused", "c64", basis=1)
+        got = to_numpy(st)
+        ref = np.zeros(1 << n, dtype=complex)
+        ref[1] = 1
+        np.testing.assert_array_equal(got, ref)
+        assert S.expval(st, []).item() == 0.0
+        assert S.expval(st, [W.PauliTerm(1.0, ((0, "Z"),))]).item() == pytest.approx(-1.0)
+
+
+def test_small_workload_config():
+    """12 qubits, 4 layers, sum_i Z_i: complex64 against the complex128 oracle."""
+    S = sim()
+    w = W.workload_small()
+    st, _, _ = gpu_state(w.circuit, w.params, "fused", "c64")
+    e = S.expval(st, w.terms).item()
+    assert abs(e - oracle.energy(w.circuit, w.params, w.terms)) <= 1e-5
+
+
+def test_invalid_state_use_raises():
+    S = sim()
+    circ = W.hea_ansatz(4, 1)
+    c = S.Circuit(circ)
+    st = S.State(5)
+    with pytest.raises(Exception, match="qubits"):
+        S.apply(st, c, params_tensor(np.zeros(circ.n_params)))
+    with pytest.raises(Exception, match="qubit"):
+        S.expval(st, [W.PauliTerm(1.0, ((7, "Z"),))])
