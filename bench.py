@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable state-vector hot path on GB300.
+
+One step = one gradient evaluation of the 26-qubit, 20-layer hardware-efficient
+ansatz (1040 angles, complex64 amplitudes) with the open-chain Ising
+observable: reset |0...0>, apply the circuit, E = <H>, lambda = H psi, reverse
+sweep with the angle derivatives.  Inputs (angles) are resident in HBM during
+the timed region; the 512 MiB state is larger than L2, so no flush is needed.
+
+The JSON line reports grad-evals/s of the fused plan (value), the
+gate-by-gate plan measured on the same workload (plain), the dominant
+kernel's achieved HBM bandwidth against the measured peak (roofline), the
+same metric end to end with host buffers (e2e), and the CPU oracle timed on
+a bounded sample of the workload (cpu_baseline).
+
+Multi-GPU: the single-state path does not shard (replicas only): every rank
+runs its own replica; value = steps of all ranks / max time over ranks.
+
+``--impl reference`` times the CPU oracle on the same workload (bounded
+samples extrapolated to grad-evals/s); under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HBM GB/s vs peak per gate sweep; grad-evals/sec fused vs plain at ≤1e-5 error"
+UNIT = "grad-evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--plan", choices=["fused", "plain"], default="fused")
+    ap.add_argument("--plain-steps", type=int, default=2, help="steps of the gate-by-gate comparison (0 = skip)")
+    ap.add_argument("--n", type=int, default=26)
+    ap.add_argument("--layers", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-qubits", type=int, default=0)
+    ap.add_argument("--low-qubits", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    from paper_2511_19291_gb300 import workloads as W
+    if args.n == 26 and args.layers == 20:
+        return W.workload_main()
+    return W.workload_hea(2, args.n, args.layers, "ising")
+
+
+def config_of(args, w, plan):
+    return {
+        "workload": f"hea ansatz n={args.n} layers={args.layers} ({w.circuit.n_params} angles), "
+                    f"open-chain Ising H ({len(w.terms)} terms), forward + expval + adjoint gradient",
+        "n_qubits": args.n, "layers": args.layers, "n_params": w.circuit.n_params,
+        "gates": len(w.circuit.gates), "plan": plan, "amplitudes": "complex64",
+        "reductions": "fp64 beyond per-thread partials",
+        "l2": "inputs larger than L2 (state 2^n x 8 B; no flush needed)",
+        "parallelism": "replicas",
+    }
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def stored_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, valid only while the
+    library source is unchanged since the capture."""
+    try:
+        from paper_2511_19291_gb300 import build as B
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        if t.get("source_digest") != B._digest():
+            return None
+        return t.get("kernels", {}).get(kernel)
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(w, gate_sample=6, term_sample=2):
+    """Times the oracle on a bounded sample of the workload and extrapolates to
+    one parameter-shift gradient evaluation: (2P + 1) forward passes plus
+    expectations.  Single-threaded calls."""
+    import numpy as np
+    import oracle
+    n = w.circuit.n_qubits
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1
+    from paper_2511_19291_gb300 import workloads as W
+    sub = W.Circuit(n, w.circuit.gates[:gate_sample], w.circuit.n_params)
+    t0 = time.perf_counter()
+    psi = oracle.apply_gates(sub, w.params, psi)
+    t_gates = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.expval(n, psi, w.terms[:term_sample])
+    t_terms = time.perf_counter() - t0
+    per_gate = t_gates / gate_sample
+    per_term = t_terms / term_sample
+    t_eval = per_gate * len(w.circuit.gates) + per_term * len(w.terms)
+    t_grad = (2 * w.circuit.n_params + 1) * t_eval
+    sample = (f"{gate_sample} gates and {term_sample} terms of the {n}-qubit workload on 1 host thread "
+              f"({per_gate:.3f} s/gate, {per_term:.3f} s/term), extrapolated to one parameter-shift gradient "
+              f"= (2*{w.circuit.n_params}+1) x ({len(w.circuit.gates)} gates + {len(w.terms)} terms)")
+    return 1.0 / t_grad, sample, t_gates + t_terms
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args)
+    vals = []
+    total = 0.0
+    for i in range(args.warmup + args.steps):
+        v, sample, spent = oracle_sample(w, gate_sample=2, term_sample=1)
+        total += spent
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": config_of(args, w, "oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------- our path
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2511_19291_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2511_19291_gb300 import sim as S
+
+    w = workload(args)
+    n = w.circuit.n_qubits
+    obs = S.Observable(w.terms)
+    circ = S.Circuit(w.circuit, mode=args.plan, tile_qubits=args.tile_qubits, low_qubits=args.low_qubits,
+                     device=dev)
+    psi = S.State(n, torch.complex64, dev)
+    lam = S.State(n, torch.complex64, dev)
+    params = torch.tensor(w.params, dtype=torch.float64, device=dev)
+    grads = torch.zeros(w.circuit.n_params, dtype=torch.float64, device=dev)
+    e_out = torch.zeros((), dtype=torch.float64, device=dev)
+
+    def step(c):
+        psi.reset(0)
+        S.apply(psi, c, params)
+        S.expval(psi, obs, out=e_out)
+        S.backward(psi, lam, c, params, obs, grads)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(fn, k):
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k):
+            fn()
+        b.record()
+        barrier()
+        ms = a.elapsed_time(b)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # warm-up, and one profiled step to count launches
+    for _ in range(args.warmup):
+        step(circ)
+    S.profile_enable(True)
+    step(circ)
+    torch.cuda.synchronize(dev)
+    prof1 = S.profile_read()
+    launches_per_step = sum(p["launches"] for p in prof1)
+
+    # main timed region (per-kernel events recorded on the launching stream)
+    S.profile_enable(True)
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: step(circ), args.steps)
+    prof = S.profile_read()
+    S.profile_enable(False)
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+
+    # end to end: angles from pinned host memory in, E and gradient back out
+    params_host = torch.tensor(w.params, dtype=torch.float64).pin_memory()
+    e_host = torch.zeros((), dtype=torch.float64).pin_memory()
+    g_host = torch.zeros(w.circuit.n_params, dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        params.copy_(params_host, non_blocking=True)
+        step(circ)
+        e_host.copy_(e_out, non_blocking=True)
+        g_host.copy_(grads, non_blocking=True)
+
+    step_e2e()
+    ms_e2e = timed(step_e2e, args.steps)
+    e2e_value = world * args.steps / (ms_e2e / 1000.0)
+
+    # gate-by-gate comparison on the same workload
+    plain = None
+    if args.plain_steps > 0 and args.plan == "fused":
+        circ_plain = S.Circuit(w.circuit, mode="plain", device=dev)
+        step(circ_plain)
+        ms_plain = timed(lambda: step(circ_plain), args.plain_steps)
+        plain = {"value": world * args.plain_steps / (ms_plain / 1000.0), "unit": UNIT,
+                 "ms_per_step": ms_plain / args.plain_steps, "steps": args.plain_steps}
+
+    # sanity of the numbers being timed: E of this step against a fresh forward
+    psi.reset(0)
+    S.apply(psi, circ, params)
+    e_check = S.expval(psi, obs).item()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel class
+    peak, peak_src = peaks()
+    dom = max(prof, key=lambda p: p["ms"])
+    per_launch_ms = dom["ms"] / max(1, dom["launches"])
+    per_launch_bytes = dom["bytes"] / max(1, dom["launches"])
+    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
+    total_ms = sum(p["ms"] for p in prof)
+    roofline = {
+        "bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+        "traffic": stored_traffic(dom["name"]),
+        "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+        "share_of_step": dom["ms"] / total_ms if total_ms > 0 else None,
+    }
+    kernels = sorted(({"name": p["name"], "launches": p["launches"], "ms": round(p["ms"], 3),
+                       "gbs": round(p["bytes"] / (p["ms"] / 1000.0) / 1e9, 1) if p["ms"] > 0 and p["bytes"] > 0
+                       else None} for p in prof), key=lambda d: -d["ms"])
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, sample, _ = oracle_sample(w)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": config_of(args, w, args.plan),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(params_host.numel() * 8),
+                "d2h_bytes_per_step": int(8 + g_host.numel() * 8), "ms_per_step": ms_e2e / args.steps},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "plain": plain,
+        "fused_over_plain": (value / plain["value"]) if plain else None,
+        "clocks": clk.summary(),
+        "kernels": kernels,
+        "energy": e_check,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

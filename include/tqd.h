@@ -176,8 +176,31 @@ tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *ci
                         const double *dev_term_weights, double grad_scale, double *dev_grads,
                         void *stream);
 
+/* -------------------------------------------------------------- profiling */
+
+/* Per-kernel-class timing, summed over launches: CUDA events recorded on the
+ * launching stream around every kernel (the paper's Sec. 5 records walltime
+ * per step; this splits it by kernel).  bytes is the algorithmic traffic of
+ * those launches (amplitudes each launch must read and write). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+    double bytes;
+} tqd_profile_entry;
+
+/* Turn recording on (non-zero) or off, discarding earlier records.  Recording
+ * adds two event records per launch; it is off by default. */
+tqd_status tqd_profile_enable(int enable);
+
+/* Wait for the recorded events, write up to `capacity` entries (one per
+ * kernel class that launched) and their total count to *n_out, then discard
+ * the records. */
+tqd_status tqd_profile_read(tqd_profile_entry *out, int capacity, int *n_out);
+
 /* ------------------------------------------------------------------ misc */
 
+/* Message of the last failed call on this thread ("" if none). */
 const char *tqd_last_error(void);
 const char *tqd_version(void);
 

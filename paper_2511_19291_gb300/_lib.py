@@ -29,7 +29,7 @@ EXPORTS = (
     "tqd_state_alloc", "tqd_state_reset", "tqd_state_free",
     "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_apply_observable",
-    "tqd_backward", "tqd_last_error", "tqd_version",
+    "tqd_backward", "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
 )
 
 
@@ -57,6 +57,11 @@ class Gate(C.Structure):
 
 class PauliTerm(C.Structure):
     _fields_ = [("xmask", C.c_uint64), ("zmask", C.c_uint64), ("coeff", C.c_double)]
+
+
+class ProfileEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("bytes", C.c_double)]
 
 
 class PlanOpts(C.Structure):
@@ -96,9 +101,12 @@ def load(path: str | None = None):
         L.tqd_expval_terms.argtypes = [vp, vp, sz, vp, vp]
         L.tqd_apply_observable.argtypes = [vp, vp, sz, vp, vp, vp]
         L.tqd_backward.argtypes = [vp, vp, vp, vp, vp, sz, vp, dbl, vp, vp]
+        L.tqd_profile_enable.argtypes = [i32]
+        L.tqd_profile_read.argtypes = [vp, i32, C.POINTER(i32)]
         for name in ("tqd_state_alloc", "tqd_state_reset", "tqd_state_free", "tqd_circuit_create",
                      "tqd_circuit_free", "tqd_circuit_info", "tqd_apply_circuit", "tqd_expval",
-                     "tqd_expval_terms", "tqd_apply_observable", "tqd_backward"):
+                     "tqd_expval_terms", "tqd_apply_observable", "tqd_backward", "tqd_profile_enable",
+                     "tqd_profile_read"):
             getattr(L, name).restype = st
         L.tqd_last_error.restype = C.c_char_p
         L.tqd_last_error.argtypes = []

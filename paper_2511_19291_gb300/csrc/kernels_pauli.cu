@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "prof.h"
 
 namespace tqd {
 
@@ -273,10 +274,12 @@ static cudaError_t expval_t(tqd_state *st, const std::vector<PauliGroup> &groups
                 TermPack tp;
                 const size_t cnt = std::min((size_t)MAXT, g.terms.size() - from);
                 fill_pack(tp, g.xmask, g.terms, from, cnt, true);
+                ProfScope ps(PK_EXPVAL, (double)N * sizeof(V), s);
                 k_expval_total<V><<<grid, PT, 0, s>>>((const V *)st->amps, n, tp, parts + slot * pblk);
                 ++slot;
             }
         }
+        ProfScope ps(PK_REDUCE, 0.0, s);
         k_sum_rows<<<(int)launches, PT, 0, s>>>(parts, pblk, grid, sums);
         k_sum_all<<<1, 32, 0, s>>>(sums, (int)launches, dev_out);
         return cudaGetLastError();
@@ -289,9 +292,11 @@ static cudaError_t expval_t(tqd_state *st, const std::vector<PauliGroup> &groups
         for (size_t from = 0; from < g.terms.size(); from += MAXT1) {
             TermPack tp;
             fill_pack(tp, g.xmask, g.terms, from, std::min((size_t)MAXT1, g.terms.size() - from), false);
+            ProfScope ps(PK_EXPVAL_TERMS, (double)N * sizeof(V), s);
             k_expval_terms<V><<<grid, PT, 0, s>>>((const V *)st->amps, n, tp, parts, pblk);
         }
     }
+    ProfScope ps(PK_REDUCE, 0.0, s);
     k_sum_rows<<<n_terms, PT, 0, s>>>(parts, pblk, grid, dev_out);
     return cudaGetLastError();
 }
@@ -314,6 +319,7 @@ static cudaError_t apply_obs_t(const tqd_state *psi, const std::vector<PauliGrou
         for (size_t from = 0; from < g.terms.size(); from += MAXT) {
             TermPack tp;
             fill_pack(tp, g.xmask, g.terms, from, std::min((size_t)MAXT, g.terms.size() - from), true);
+            ProfScope ps(PK_APPLY_OBS, (double)N * sizeof(V) * (accumulate ? 3 : 2), s);
             k_apply_obs<V><<<grid, PT, 0, s>>>((const V *)psi->amps, (V *)out->amps, n, tp, weights, scale,
                                                accumulate);
             accumulate = 1;

@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "prof.h"
 
 namespace tqd {
 
@@ -96,6 +97,7 @@ __global__ void k_prep(const GateDev *__restrict__ gates, int ng, const double *
 cudaError_t launch_prep(const tqd_circuit *c, const double *dev_params, cudaStream_t s) {
     const int ng = (int)c->gates.size();
     if (ng == 0) return cudaSuccess;
+    ProfScope ps(PK_PREP, 0.0, s);
     k_prep<<<(ng + 127) / 128, 128, 0, s>>>(c->d_gates, ng, dev_params, c->d_table, c->d_mats64, c->d_mats32);
     return cudaGetLastError();
 }
@@ -117,6 +119,7 @@ __global__ void k_reset(V *__restrict__ a, uint64_t N, uint64_t j) {
 cudaError_t launch_reset(tqd_state *st, uint64_t j, cudaStream_t s) {
     const uint64_t N = (uint64_t)1 << st->n;
     const int grid = stream_grid((N + 1) / 2, TPB);
+    ProfScope ps(PK_RESET, (double)N * (st->dtype == TQD_C64 ? 8 : 16), s);
     if (st->dtype == TQD_C64) k_reset<float2><<<grid, TPB, 0, s>>>((float2 *)st->amps, N, j);
     else k_reset<double2><<<grid, TPB, 0, s>>>((double2 *)st->amps, N, j);
     return cudaGetLastError();
@@ -333,35 +336,47 @@ __global__ void k_small(V *__restrict__ a, int n, int k, int w0, int w1, const R
 template <typename V>
 static cudaError_t plain_gate_t(V *a, int n, const GateH &g, const RT<V> *mat, bool dag, cudaStream_t s) {
     const int k = gate_arity(g.kind);
+    const double A = (double)sizeof(V) * ((uint64_t)1 << n);  // bytes of one full read (or write)
     if (n < 4) {
+        ProfScope ps(PK_SMALL, 2 * A, s);
         k_small<V><<<1, 64, 0, s>>>(a, n, k, g.w[0], k == 2 ? g.w[1] : 0, mat, dag);
         return cudaGetLastError();
     }
     const uint64_t N = (uint64_t)1 << n;
     switch (g.kind) {
-    case TQD_H: case TQD_X: case TQD_Y: case TQD_RX: case TQD_RY: case TQD_UNITARY1:
+    case TQD_H: case TQD_X: case TQD_Y: case TQD_RX: case TQD_RY: case TQD_UNITARY1: {
+        ProfScope ps(PK_DENSE1, 2 * A, s);
         k_dense1<V><<<stream_grid(N / 4, TPB), TPB, 0, s>>>(a, n, g.w[0], mat, dag);
         break;
-    case TQD_Z: case TQD_S: case TQD_T: case TQD_PHASE:
+    }
+    case TQD_Z: case TQD_S: case TQD_T: case TQD_PHASE: {
+        ProfScope ps(PK_DIAG1, A, s);
         k_diag1<V><<<stream_grid(g.w[0] >= 1 ? N / 4 : N / 2, TPB), TPB, 0, s>>>(a, n, g.w[0], mat, dag, 1);
         break;
-    case TQD_RZ:
+    }
+    case TQD_RZ: {
+        ProfScope ps(PK_DIAG1, 2 * A, s);
         k_diag1<V><<<stream_grid(N / 2, TPB), TPB, 0, s>>>(a, n, g.w[0], mat, dag, 0);
         break;
+    }
     case TQD_CNOT: case TQD_SWAP: {
         const int lo = g.w[0] < g.w[1] ? g.w[0] : g.w[1];
+        ProfScope ps(PK_PERM2, A, s);
         k_perm2<V><<<stream_grid(lo >= 1 ? N / 8 : N / 4, TPB), TPB, 0, s>>>(a, n, g.w[0], g.w[1],
                                                                                g.kind == TQD_CNOT ? 0 : 1);
         break;
     }
     case TQD_CZ: case TQD_CPHASE: {
         const int lo = g.w[0] < g.w[1] ? g.w[0] : g.w[1];
+        ProfScope ps(PK_PHASE11, A / 2, s);
         k_phase11<V><<<stream_grid(lo >= 1 ? N / 8 : N / 4, TPB), TPB, 0, s>>>(a, n, g.w[0], g.w[1], mat, dag);
         break;
     }
-    case TQD_UNITARY2:
+    case TQD_UNITARY2: {
+        ProfScope ps(PK_DENSE2, 2 * A, s);
         k_dense2<V><<<stream_grid(N / 4, TPB), TPB, 0, s>>>(a, n, g.w[0], g.w[1], mat, dag);
         break;
+    }
     default:
         return cudaErrorInvalidValue;
     }
@@ -515,19 +530,23 @@ static cudaError_t plain_adjoint_t(V *psi, V *lam, int n, const GateH &g, const 
     const bool grad = partials != nullptr && g.param >= 0 && gate_parametric(g.kind);
     const int gen = grad ? gate_gen(g.kind) : GEN_NONE;
     const uint64_t N = (uint64_t)1 << n;
+    const double A = (double)sizeof(V) * N;
     if (k == 1 && n >= 4) {
         int grid = stream_grid(N / 4, TPB);
         if (grid > pblk) grid = pblk;
+        ProfScope ps(PK_ADJ1, 4 * A, s);
         k_adj1<V><<<grid, TPB, 0, s>>>(psi, lam, n, g.w[0], mat, gen, grad ? partials : nullptr);
         return cudaGetLastError();
     }
     if ((g.kind == TQD_CPHASE || g.kind == TQD_CZ) && n >= 4) {
         int grid = stream_grid(N / 4, TPB);
         if (grid > pblk) grid = pblk;
+        ProfScope ps(PK_ADJ_PHASE11, A, s);
         k_adj_phase11<V><<<grid, TPB, 0, s>>>(psi, lam, n, g.w[0], g.w[1], mat, gen, grad ? partials : nullptr);
         return cudaGetLastError();
     }
     if (n < 4) {
+        ProfScope ps(PK_ADJ_SMALL, 4 * A, s);
         k_adj_small<V><<<1, 64, 0, s>>>(psi, lam, n, k, g.w[0], k == 2 ? g.w[1] : 0, mat, gen,
                                          grad ? partials : nullptr);
         return cudaGetLastError();
@@ -571,6 +590,7 @@ __global__ void k_param_sum(const int *__restrict__ ptr, const int *__restrict__
 
 cudaError_t launch_grad_finalize(const tqd_circuit *c, int nblk, double *dev_grads, cudaStream_t s) {
     if (c->n_slots == 0 || c->n_params == 0) return cudaSuccess;
+    ProfScope ps(PK_REDUCE, 0.0, s);
     k_slot_sum<<<c->n_slots, TPB, 0, s>>>(c->d_partials, c->pblk, nblk, c->d_slot_sums);
     k_param_sum<<<(c->n_params + 127) / 128, 128, 0, s>>>(c->d_param_ptr, c->d_param_slots, c->d_slot_sums,
                                                           c->n_params, dev_grads);

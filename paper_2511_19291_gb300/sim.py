@@ -306,3 +306,19 @@ def expval_fn(params: torch.Tensor, circuit: Circuit, obs, dtype=torch.complex64
 def measure_allz_fn(params: torch.Tensor, circuit: Circuit, dtype=torch.complex64, basis_index: int = 0):
     obs = Observable(W.all_z_terms(circuit.n))
     return _MeasureFn.apply(params, circuit, obs, dtype, basis_index)
+
+
+# ------------------------------------------------------------------ profiling
+def profile_enable(on: bool = True):
+    _lib.check(_L().tqd_profile_enable(1 if on else 0))
+
+
+def profile_read() -> list:
+    """Per-kernel-class launches, total device ms and algorithmic bytes since
+    the last enable/read (waits for the recorded events)."""
+    cap = 64
+    arr = (_lib.ProfileEntry * cap)()
+    n = C.c_int()
+    _lib.check(_L().tqd_profile_read(C.cast(arr, C.c_void_p), cap, C.byref(n)))
+    return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "ms": float(arr[i].total_ms),
+             "bytes": float(arr[i].bytes)} for i in range(min(n.value, cap))]
