@@ -176,6 +176,29 @@ tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *ci
                         const double *dev_term_weights, double grad_scale, double *dev_grads,
                         void *stream);
 
+/* Same result as tqd_expval, for callers that may not allocate device memory
+ * while they run: a service that reserved its whole memory budget at
+ * start-up, a latency-sensitive loop where cudaMalloc/cudaFree would stall the
+ * device, or a framework that owns the device allocator.  (The paper has no
+ * counterpart; this is a library convenience.)
+ *
+ * The reduction's per-block partial sums go to a fixed scratch array inside
+ * the library, TQD_NOALLOC_SCRATCH_DOUBLES doubles (1 MiB) per GPU, reserved
+ * from library load until process exit.  This call makes no cudaMalloc,
+ * cudaFree or other allocating call.  Requests whose partials do not fit are
+ * rejected with TQD_ERR_INVALID_ARG: they need (number of 64-term chunks of
+ * distinct x masks) x (blocks + 1) doubles, blocks <= 8 x the SM count; on a
+ * 152-SM GB300 about 100 chunks fit.  Every slot a call reads is written
+ * earlier in the same call, so nothing has to be cleared between calls.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array:
+ * calls whose GPU work overlaps (different streams or host threads) race. */
+#define TQD_NOALLOC_SCRATCH_DOUBLES 131072
+tqd_status tqd_expval_noalloc(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms,
+                              double *dev_out, void *stream);
+
 /* -------------------------------------------------------------- profiling */
 
 /* Per-kernel-class timing, summed over launches: CUDA events recorded on the

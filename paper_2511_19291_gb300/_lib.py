@@ -28,7 +28,7 @@ PLAN_PLAIN, PLAN_FUSED = 0, 1
 EXPORTS = (
     "tqd_state_alloc", "tqd_state_reset", "tqd_state_free",
     "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_apply_circuit",
-    "tqd_expval", "tqd_expval_terms", "tqd_apply_observable",
+    "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
     "tqd_backward", "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
 )
 
@@ -99,13 +99,15 @@ def load(path: str | None = None):
         L.tqd_apply_circuit.argtypes = [vp, vp, vp, vp]
         L.tqd_expval.argtypes = [vp, vp, sz, vp, vp]
         L.tqd_expval_terms.argtypes = [vp, vp, sz, vp, vp]
+        L.tqd_expval_noalloc.argtypes = [vp, vp, sz, vp, vp]
         L.tqd_apply_observable.argtypes = [vp, vp, sz, vp, vp, vp]
         L.tqd_backward.argtypes = [vp, vp, vp, vp, vp, sz, vp, dbl, vp, vp]
         L.tqd_profile_enable.argtypes = [i32]
         L.tqd_profile_read.argtypes = [vp, i32, C.POINTER(i32)]
         for name in ("tqd_state_alloc", "tqd_state_reset", "tqd_state_free", "tqd_circuit_create",
                      "tqd_circuit_free", "tqd_circuit_info", "tqd_apply_circuit", "tqd_expval",
-                     "tqd_expval_terms", "tqd_apply_observable", "tqd_backward", "tqd_profile_enable",
+                     "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable", "tqd_backward",
+                     "tqd_profile_enable",
                      "tqd_profile_read"):
             getattr(L, name).restype = st
         L.tqd_last_error.restype = C.c_char_p
