@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "tile.h"
 #include "tqd.h"
 
 namespace tqd {
@@ -112,4 +113,7 @@ struct tqd_circuit {
     int launches_apply;
     int launches_backward;
     int n_passes;
+    bool fused;                  // tile passes (n >= 12) instead of the gate-by-gate plan
+    std::vector<tqd::TilePlanPass> tile_passes;
+    int *d_err;                  // device error word (bounded waits that gave up)
 };

@@ -5,6 +5,7 @@
 
 #include "launch.h"
 #include "plan.h"
+#include "tile_plan.h"
 
 namespace tqd {
 
@@ -36,6 +37,8 @@ tqd_status build_circuit(tqd_circuit *c) {
     c->d_slot_sums = nullptr;
     c->d_param_ptr = nullptr;
     c->d_param_slots = nullptr;
+    c->d_err = nullptr;
+    c->fused = false;
 
     // gradient slots: one per parametric gate that reads the parameter vector
     c->grad_slot.assign(ng, -1);
@@ -86,6 +89,24 @@ tqd_status build_circuit(tqd_circuit *c) {
     if ((e = upload(&c->d_param_ptr, ptr)) != cudaSuccess) return fail(e);
     if ((e = upload(&c->d_param_slots, slots)) != cudaSuccess) return fail(e);
 
+    if ((e = cudaMalloc((void **)&c->d_err, sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return fail(e);
+
+    // fused plan: tile passes, when the state holds at least one full tile
+    if (c->opts.mode == TQD_PLAN_FUSED && c->n >= TILE_K && ng > 0) {
+        std::vector<TilePlanPass> passes = plan_tile_passes(c);
+        bool ok = !passes.empty();
+        for (auto &p : passes) ok = ok && encode_tile_pass(c, p);
+        if (ok) {
+            c->tile_passes = std::move(passes);
+            c->fused = true;
+            c->n_passes = (int)c->tile_passes.size();
+            c->launches_apply = c->n_passes + 1;
+            c->launches_backward = c->n_passes + 1 + (c->n_slots > 0 ? 2 : 0);  // + the H psi launches
+            return TQD_OK;
+        }
+    }
+
     // plain plan: one launch per gate (two for 2-qubit permutations in reverse)
     c->n_passes = ng;
     c->launches_apply = ng + (ng > 0 ? 1 : 0);
@@ -108,11 +129,19 @@ void release_circuit(tqd_circuit *c) {
     cudaFree(c->d_slot_sums);
     cudaFree(c->d_param_ptr);
     cudaFree(c->d_param_slots);
+    cudaFree(c->d_err);
 }
 
 cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s) {
     cudaError_t e = launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
+    if (c->fused) {
+        for (int p = 0; p < (int)c->tile_passes.size(); ++p) {
+            e = launch_tile_pass(psi, nullptr, c, p, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (int g = 0; g < (int)c->gates.size(); ++g) {
         e = launch_plain_gate(psi, c, g, false, s);
         if (e != cudaSuccess) return e;
@@ -127,6 +156,13 @@ cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, c
     if (e != cudaSuccess) return e;
     e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s);
     if (e != cudaSuccess) return e;
+    if (c->fused) {
+        for (int p = (int)c->tile_passes.size() - 1; p >= 0; --p) {
+            e = launch_tile_pass(psi, lam, c, p, s);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_grad_finalize(c, tile_grid(c, psi->dtype == TQD_C64 ? 0 : 1, true), dev_grads, s);
+    }
     const int nblk = plain_adjoint_blocks(c->n);
     for (int g = (int)c->gates.size() - 1; g >= 0; --g) {
         const int slot = c->grad_slot[g];

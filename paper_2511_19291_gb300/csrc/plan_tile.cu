@@ -1,0 +1,390 @@
+// plan_tile.cu -- host planner of the fused tile passes.
+//
+// 1. Passes.  Starting at the first gate not yet done, the pass's qubit set Q
+//    is qubits 0..3 plus the first other qubits touched in gate order (up to
+//    12).  Gates are then absorbed in order: a gate joins the pass when all
+//    its wires are in Q and no earlier gate left out of the pass touches any
+//    of them.  Every gate left out therefore commutes with every absorbed gate
+//    after it, so executing the pass before the rest preserves the circuit.
+// 2. TMA box.  Q's qubits above 3 are grouped into runs; the tensor map has at
+//    most 5 dimensions, so runs that do not fit become "extra" bits, copied by
+//    2^extra TMA operations per tile.
+// 3. Stages.  List scheduling over the pass's gates: a stage fixes 4 register
+//    bits, then takes every gate whose predecessors are scheduled and whose
+//    dense qubits are register bits.  Thread-index bits are assigned so that a
+//    half-warp's shared-memory accesses fall in different banks under the
+//    128-byte swizzle.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "launch.h"
+#include "tile.h"
+#include "tile_plan.h"
+
+namespace tqd {
+
+namespace {
+
+// Register bits a gate needs in its stage (local bits).
+void dense_needs(const GateH &g, const int *loc, int *out, int &cnt) {
+    cnt = 0;
+    switch (g.kind) {
+    case TQD_H: case TQD_X: case TQD_Y: case TQD_RX: case TQD_RY: case TQD_UNITARY1:
+        out[cnt++] = loc[g.w[0]];
+        break;
+    case TQD_CNOT:
+        out[cnt++] = loc[g.w[1]];
+        break;
+    case TQD_SWAP: case TQD_UNITARY2:
+        out[cnt++] = loc[g.w[0]];
+        out[cnt++] = loc[g.w[1]];
+        break;
+    default:
+        break;  // diagonal gates: any bit
+    }
+}
+
+uint8_t op_type_of(int kind) {
+    switch (kind) {
+    case TQD_H: case TQD_X: case TQD_Y: case TQD_RX: case TQD_RY: case TQD_UNITARY1: return TOP_G1;
+    case TQD_Z: case TQD_S: case TQD_T: case TQD_RZ: case TQD_PHASE: return TOP_D1;
+    case TQD_CNOT: return TOP_CX;
+    case TQD_SWAP: return TOP_SW;
+    case TQD_UNITARY2: return TOP_G2;
+    default: return TOP_D2;  // CZ, CPHASE
+    }
+}
+
+// Segments of [from, n): maximal runs of equal membership, in-runs capped at 8.
+struct Seg {
+    int lo, len;
+    bool in;
+};
+std::vector<Seg> segments(const std::vector<char> &box, int from, int n) {
+    std::vector<Seg> out;
+    int b = from;
+    while (b < n) {
+        const bool in = box[b] != 0;
+        int e = b;
+        while (e < n && (box[e] != 0) == in && (!in || e - b < 8)) ++e;
+        out.push_back(Seg{b, e - b, in});
+        b = e;
+    }
+    return out;
+}
+
+// Swizzled shared-memory offset of local index l (units of amplitudes).
+uint32_t swz_host(uint32_t l, int amp_bytes) {
+    return amp_bytes == 8 ? (l ^ (((l >> 4) & 7u) << 1)) : (l ^ ((l >> 3) & 7u));
+}
+
+}  // namespace
+
+bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L) {
+    // box bits start as all of Q; extras are taken from the top runs until the
+    // stricter (complex128, 3-bit inner dimension) layout has <= 5 dimensions.
+    std::vector<char> box(inQ);
+    L.extra.clear();
+    for (int iter = 0; iter < 16; ++iter) {
+        const std::vector<Seg> s128 = segments(box, TILE_LOW - 1, n);
+        const int dims = 1 + (int)s128.size();
+        if (dims <= TILE_MAX_DIMS) break;
+        // move the highest in-run of the box to the extras
+        int hi = -1;
+        for (int i = (int)s128.size() - 1; i >= 0; --i)
+            if (s128[i].in) { hi = i; break; }
+        if (hi < 0) return false;
+        for (int b = s128[hi].lo; b < s128[hi].lo + s128[hi].len; ++b) {
+            box[b] = 0;
+            L.extra.push_back(b);
+        }
+    }
+    std::sort(L.extra.begin(), L.extra.end());
+    if ((int)L.extra.size() > 4) return false;
+    // local order: box bits ascending, then extra bits ascending
+    L.qubit_of_local.clear();
+    for (int b = 0; b < n; ++b)
+        if (box[b]) L.qubit_of_local.push_back(b);
+    for (int b : L.extra) L.qubit_of_local.push_back(b);
+    if ((int)L.qubit_of_local.size() != TILE_K) return false;
+    for (int dt = 0; dt < 2; ++dt) {
+        const int low = dt == 0 ? TILE_LOW : TILE_LOW - 1;
+        const std::vector<Seg> s = segments(box, low, n);
+        L.rank[dt] = 1 + (int)s.size();
+        if (L.rank[dt] > TILE_MAX_DIMS) return false;
+        L.dim_lo[dt][0] = 0;
+        L.dim_len[dt][0] = low;
+        L.dim_in[dt][0] = 1;
+        for (size_t i = 0; i < s.size(); ++i) {
+            L.dim_lo[dt][i + 1] = s[i].lo;
+            L.dim_len[dt][i + 1] = s[i].len;
+            L.dim_in[dt][i + 1] = s[i].in ? 1 : 0;
+        }
+    }
+    L.out.clear();
+    for (int b = 0; b < n; ++b)
+        if (!inQ[b]) L.out.push_back(b);
+    return true;
+}
+
+std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c) {
+    const int n = c->n;
+    const int L = (int)c->gates.size();
+    std::vector<TilePlanPass> passes;
+    std::vector<char> done(L, 0);
+    int first = 0;
+    while (first < L) {
+        // --- qubit set: low qubits, then the qubits of gates in order, each
+        // addition accepted only if the TMA box still fits
+        std::vector<char> inQ(n, 0);
+        int qn = 0;
+        for (int q = 0; q < TILE_LOW; ++q) { inQ[q] = 1; ++qn; }
+        TileLayout lay;
+        auto try_add = [&](const int *ws, int cnt) {
+            int newq = 0;
+            for (int a = 0; a < cnt; ++a) newq += inQ[ws[a]] ? 0 : 1;
+            if (newq == 0) return true;
+            if (qn + newq > TILE_K) return false;
+            std::vector<char> t(inQ);
+            for (int a = 0; a < cnt; ++a) t[ws[a]] = 1;
+            // the layout needs exactly K bits: check with the set padded by the
+            // lowest free qubits above the highest run (contiguous padding adds
+            // no segments below it)
+            std::vector<char> pad(t);
+            int have = qn + newq;
+            for (int q = TILE_LOW; q < n && have < TILE_K; ++q)
+                if (!pad[q] && pad[q - 1]) { pad[q] = 1; ++have; }
+            for (int q = TILE_LOW; q < n && have < TILE_K; ++q)
+                if (!pad[q]) { pad[q] = 1; ++have; }
+            TileLayout tl;
+            if (!tile_layout(n, pad, tl)) return false;
+            inQ.swap(t);
+            qn += newq;
+            return true;
+        };
+        int scanned = 0;
+        for (int g = first; g < L && qn < TILE_K && scanned < 4096; ++g) {
+            if (done[g]) continue;
+            ++scanned;
+            const GateH &gh = c->gates[g];
+            if (!try_add(gh.w, gh.nw) && g == first) break;
+        }
+        // fill: qubits that extend an existing run first, then any
+        for (int pass2 = 0; pass2 < 2 && qn < TILE_K; ++pass2)
+            for (int q = TILE_LOW; q < n && qn < TILE_K; ++q)
+                if (!inQ[q] && (pass2 == 1 || inQ[q - 1] || (q + 1 < n && inQ[q + 1]))) try_add(&q, 1);
+        if (qn < TILE_K || !tile_layout(n, inQ, lay)) return {};
+        {
+            const GateH &g0 = c->gates[first];
+            for (int a = 0; a < g0.nw; ++a)
+                if (!inQ[g0.w[a]]) return {};
+        }
+        // --- absorb gates
+        TilePlanPass P;
+        P.layout = lay;
+        std::vector<char> blocked(n, 0);
+        int blocked_in_q = 0;
+        for (int g = first; g < L; ++g) {
+            if (done[g]) continue;
+            const GateH &gh = c->gates[g];
+            bool ok = (int)P.gates.size() < TILE_MAX_OPS;
+            for (int a = 0; a < gh.nw && ok; ++a) ok = inQ[gh.w[a]] && !blocked[gh.w[a]];
+            if (ok) {
+                P.gates.push_back(g);
+                done[g] = 1;
+            } else {
+                for (int a = 0; a < gh.nw; ++a) {
+                    if (!blocked[gh.w[a]]) {
+                        blocked[gh.w[a]] = 1;
+                        if (inQ[gh.w[a]]) ++blocked_in_q;
+                    }
+                }
+                if (blocked_in_q == TILE_K) break;
+            }
+        }
+        passes.push_back(P);
+        while (first < L && done[first]) ++first;
+    }
+    return passes;
+}
+
+// Stage scheduling + op encoding for one pass.
+bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
+    const int n = c->n;
+    const TileLayout &lay = P.layout;
+    std::vector<int> loc(n, -1);
+    for (int i = 0; i < TILE_K; ++i) loc[lay.qubit_of_local[i]] = i;
+    const int m = (int)P.gates.size();
+    // dependencies inside the pass (shared local bits)
+    std::vector<std::vector<int>> preds(m);
+    {
+        std::vector<int> last(TILE_K, -1);
+        for (int i = 0; i < m; ++i) {
+            const GateH &g = c->gates[P.gates[i]];
+            for (int a = 0; a < g.nw; ++a) {
+                const int lb = loc[g.w[a]];
+                if (last[lb] >= 0) preds[i].push_back(last[lb]);
+                last[lb] = i;
+            }
+        }
+    }
+    std::vector<char> sched(m, 0);
+    int nsched = 0;
+    std::vector<int> order;  // execution order (indices into P.gates)
+    struct StageH {
+        int reg[TILE_R];
+        int begin, end;
+    };
+    std::vector<StageH> stages;
+    auto ready = [&](int i) {
+        for (int p : preds[i])
+            if (!sched[p]) return false;
+        return true;
+    };
+    while (nsched < m) {
+        // register set from the ready gates in order
+        std::vector<int> rs;
+        for (int i = 0; i < m && (int)rs.size() < TILE_R; ++i) {
+            if (sched[i] || !ready(i)) continue;
+            int need[2], cnt;
+            dense_needs(c->gates[P.gates[i]], loc.data(), need, cnt);
+            std::vector<int> u(rs);
+            for (int k = 0; k < cnt; ++k)
+                if (std::find(u.begin(), u.end(), need[k]) == u.end()) u.push_back(need[k]);
+            if ((int)u.size() <= TILE_R) rs = u;
+        }
+        // take every gate that becomes executable with this register set
+        StageH st;
+        st.begin = (int)order.size();
+        bool progress = true;
+        while (progress) {
+            progress = false;
+            for (int i = 0; i < m; ++i) {
+                if (sched[i] || !ready(i)) continue;
+                int need[2], cnt;
+                dense_needs(c->gates[P.gates[i]], loc.data(), need, cnt);
+                bool fits = true;
+                for (int k = 0; k < cnt; ++k)
+                    fits = fits && std::find(rs.begin(), rs.end(), need[k]) != rs.end();
+                if (!fits) continue;
+                sched[i] = 1;
+                ++nsched;
+                order.push_back(i);
+                progress = true;
+            }
+        }
+        st.end = (int)order.size();
+        if (st.end == st.begin) return false;  // cannot happen: the first ready gate always fits
+        // pad the register set with the highest free local bits (they do not
+        // help bank spreading as lane bits)
+        for (int b = TILE_K - 1; b >= 0 && (int)rs.size() < TILE_R; --b)
+            if (std::find(rs.begin(), rs.end(), b) == rs.end()) rs.push_back(b);
+        std::sort(rs.begin(), rs.end());
+        for (int r = 0; r < TILE_R; ++r) st.reg[r] = rs[r];
+        stages.push_back(st);
+    }
+    if ((int)stages.size() > TILE_MAX_STAGES) return false;
+
+    // --- encode for both dtypes
+    for (int dt = 0; dt < 2; ++dt) {
+        TilePassDev &D = P.dev[dt];
+        memset(&D, 0, sizeof(D));
+        D.n = n;
+        D.n_tiles_log2 = n - TILE_K;
+        D.n_extra = (int)lay.extra.size();
+        D.rank = lay.rank[dt];
+        for (int d = 0; d < TILE_MAX_DIMS; ++d) {
+            D.dim_lo[d] = d < D.rank ? lay.dim_lo[dt][d] : 0;
+            D.dim_len[d] = d < D.rank ? lay.dim_len[dt][d] : 0;
+        }
+        for (size_t i = 0; i < lay.out.size(); ++i) D.out_bits[i] = lay.out[i];
+        for (size_t i = 0; i < lay.extra.size(); ++i) D.extra_bits[i] = lay.extra[i];
+        D.n_stages = (int)stages.size();
+        D.n_ops = m;
+        int pool = 0, ngrad = 0;
+        const int amp_bytes = dt == 0 ? 8 : 16;
+        for (size_t s = 0; s < stages.size(); ++s) {
+            const StageH &sh = stages[s];
+            TileStage &ts = D.stages[s];
+            bool is_reg[TILE_K] = {false};
+            for (int r = 0; r < TILE_R; ++r) {
+                ts.reg[r] = (uint8_t)sh.reg[r];
+                is_reg[sh.reg[r]] = true;
+            }
+            // thread bits: one representative of each bank class first
+            std::vector<int> free_bits;
+            for (int b = 0; b < TILE_K; ++b)
+                if (!is_reg[b]) free_bits.push_back(b);
+            std::vector<int> lanes;
+            const int classes64[4][2] = {{0, -1}, {1, 4}, {2, 5}, {3, 6}};
+            const int classes128[3][2] = {{0, 3}, {1, 4}, {2, 5}};
+            const int ncls = dt == 0 ? 4 : 3;
+            for (int k = 0; k < ncls; ++k) {
+                for (int t = 0; t < 2; ++t) {
+                    const int b = dt == 0 ? classes64[k][t] : classes128[k][t];
+                    if (b >= 0 && !is_reg[b] &&
+                        std::find(lanes.begin(), lanes.end(), b) == lanes.end()) {
+                        lanes.push_back(b);
+                        break;
+                    }
+                }
+            }
+            for (int b : free_bits)
+                if (std::find(lanes.begin(), lanes.end(), b) == lanes.end()) lanes.push_back(b);
+            for (int u = 0; u < TILE_T; ++u) ts.thr[u] = (uint8_t)lanes[u];
+            for (int j = 0; j < (1 << TILE_R); ++j) {
+                uint32_t o = 0;
+                for (int r = 0; r < TILE_R; ++r)
+                    if ((j >> r) & 1) o |= 1u << sh.reg[r];
+                ts.roff[j] = (uint16_t)swz_host(o, amp_bytes);
+            }
+            ts.op_begin = (uint16_t)sh.begin;
+            ts.op_end = (uint16_t)sh.end;
+            auto pos = [&](int lb) -> uint8_t {
+                for (int r = 0; r < TILE_R; ++r)
+                    if (ts.reg[r] == lb) return (uint8_t)r;
+                for (int u = 0; u < TILE_T; ++u)
+                    if (ts.thr[u] == lb) return (uint8_t)(0x80 | u);
+                return 0xff;
+            };
+            for (int k = sh.begin; k < sh.end; ++k) {
+                const int gi = P.gates[order[k]];
+                const GateH &g = c->gates[gi];
+                TileOp &op = D.ops[k];
+                op.type = op_type_of(g.kind);
+                op.a = pos(loc[g.w[0]]);
+                op.b = g.nw > 1 ? pos(loc[g.w[1]]) : 0;
+                const int slot = c->grad_slot[gi];
+                op.gen = slot >= 0 ? (uint8_t)gate_gen(g.kind) : 0;
+                op.gslot = -1;
+                if (slot >= 0) {
+                    op.gslot = (int16_t)ngrad;
+                    D.grad_gate_slot[ngrad] = slot;
+                    ++ngrad;
+                }
+                int len = 0;
+                switch (op.type) {
+                case TOP_G1: case TOP_D1: len = 8; break;
+                case TOP_G2: len = 32; break;
+                case TOP_D2: len = 2; break;
+                default: len = 0; break;
+                }
+                op.moff = len ? (int16_t)pool : (int16_t)-1;
+                pool += len;
+                D.op_gate[k] = gi;
+                if (op.a == 0xff || op.b == 0xff) return false;
+                if ((op.type == TOP_G1 || op.type == TOP_SW || op.type == TOP_G2) && (op.a & 0x80)) return false;
+                if ((op.type == TOP_CX || op.type == TOP_SW || op.type == TOP_G2) && (op.b & 0x80)) return false;
+            }
+        }
+        D.n_grad = ngrad;
+        D.pool_len = pool;
+    }
+    P.order.clear();
+    for (int k = 0; k < m; ++k) P.order.push_back(P.gates[order[k]]);
+    return true;
+}
+
+}  // namespace tqd

@@ -1,0 +1,99 @@
+// tile.h -- fused tile passes: structures shared by the host planner and the
+// tile kernel (internal).
+//
+// A pass holds K = 12 qubits Q (always the low qubits 0..3 plus up to 8
+// others).  Every tile of the state -- the 2^K amplitudes that share the
+// values of the qubits outside Q -- is brought into shared memory by TMA,
+// every gate of the pass is applied there, and the tile is written back: one
+// HBM read and write of the state per pass instead of one per gate.
+//
+// Inside the tile, local bit i stands for qubit q[i].  The 256 threads of a
+// block each hold 2^R = 16 amplitudes in registers.  A pass is split into
+// stages; in a stage, R chosen local bits are "register bits" (the bits of
+// the register index j) and the other 8 are "thread bits" (bits of the
+// thread index).  Dense gates need their qubits on register bits; diagonal
+// gates and CNOT controls work on any bit.  Between stages the tile goes
+// through shared memory, so each stage may pick new register bits.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+namespace tqd {
+
+constexpr int TILE_K = 12;        // qubits per tile
+constexpr int TILE_R = 4;         // register bits (amplitudes per thread = 16)
+constexpr int TILE_T = 8;         // thread bits (256 threads)
+constexpr int TILE_THREADS = 1 << TILE_T;
+constexpr int TILE_LOW = 4;       // qubits 0..3 are in every tile (128-byte runs for c64)
+constexpr int TILE_MAX_STAGES = 40;
+constexpr int TILE_MAX_OPS = 240;
+constexpr int TILE_MAX_DIMS = 5;  // TMA tensor rank limit
+
+// Op types.  Positions are resolved per stage: `pos` < 0x80 is a register
+// position (bit of the register index), `pos` >= 0x80 is thread-index bit
+// (pos & 0x7f).
+enum TileOpType : uint8_t {
+    TOP_G1 = 0,  // dense 2x2 on register position a
+    TOP_D1 = 1,  // diagonal diag(m00, m11) on position a (register or thread)
+    TOP_CX = 2,  // NOT on register position b when position a (register or thread) is 1
+    TOP_SW = 3,  // swap register positions a, b
+    TOP_G2 = 4,  // dense 4x4, wires[0] on register position a (MSB), wires[1] on b
+    TOP_D2 = 5,  // phase m33 when positions a and b are both 1 (CZ, CPHASE)
+};
+
+struct TileOp {
+    uint8_t type;
+    uint8_t a, b;
+    uint8_t gen;     // generator class for the angle derivative (Gen), 0 = none
+    int16_t moff;    // offset of the matrix in the block's pool (floats/doubles), -1 = none
+    int16_t gslot;   // index among this pass's gradient ops, -1 = none
+};
+
+struct TileStage {
+    uint8_t reg[TILE_R];      // local bit of register-index bit r
+    uint8_t thr[TILE_T];      // local bit of thread-index bit u
+    uint16_t op_begin, op_end;
+    uint16_t roff[1 << TILE_R];  // swizzled shared-memory offset of register j (amplitudes)
+};
+
+// Everything a tile kernel needs for one pass (a kernel parameter).
+struct TilePassDev {
+    int n;                 // qubits of the state
+    int n_tiles_log2;      // n - K
+    int n_extra;           // top local bits not covered by the TMA box (2^n_extra copies per tile)
+    int rank;              // tensor-map rank
+    int dim_lo[TILE_MAX_DIMS];    // lowest qubit of each tensor dimension
+    int dim_len[TILE_MAX_DIMS];   // qubits in each tensor dimension
+    int out_bits[40];      // qubits outside Q, ascending (tile index bit i -> qubit out_bits[i])
+    int extra_bits[8];     // qubits of the extra local bits, ascending
+    int n_stages;
+    int n_ops;
+    int n_grad;
+    int pool_len;          // matrix pool length (scalars)
+    TileStage stages[TILE_MAX_STAGES];
+    TileOp ops[TILE_MAX_OPS];
+    int32_t op_gate[TILE_MAX_OPS];        // circuit gate index of each op (matrix row)
+    int32_t grad_gate_slot[TILE_MAX_OPS]; // circuit gradient slot of each gradient op
+};
+
+// Host-side plan of one pass.
+struct TileLayout {
+    std::vector<int> qubit_of_local;  // local bit -> qubit (box bits ascending, then extras)
+    std::vector<int> extra;           // Q qubits copied by separate TMA operations
+    std::vector<int> out;             // qubits outside Q, ascending
+    int rank[2];                      // tensor-map rank for c64 / c128
+    int dim_lo[2][TILE_MAX_DIMS];
+    int dim_len[2][TILE_MAX_DIMS];
+    int dim_in[2][TILE_MAX_DIMS];     // 1 = dimension inside the box
+};
+
+struct TilePlanPass {
+    TileLayout layout;
+    std::vector<int> gates;  // absorbed gates, circuit order
+    std::vector<int> order;  // absorbed gates, execution order (stage schedule)
+    TilePassDev dev[2];      // kernel descriptor for c64 / c128
+};
+
+}  // namespace tqd

@@ -1,0 +1,22 @@
+// tile_plan.h -- host-side plan of the fused tile passes (internal).
+#pragma once
+
+#include <vector>
+
+#include "internal.h"
+#include "tile.h"
+
+namespace tqd {
+
+bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L);
+// Empty result: the circuit cannot be planned into tiles (the caller falls
+// back to the gate-by-gate plan).
+std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c);
+bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P);
+
+// Launch one pass (forward: lam == nullptr; reverse sweep with gradients
+// into the circuit's partials when lam != nullptr).
+cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s);
+int tile_grid(const tqd_circuit *c, int dtype, bool adj);
+
+}  // namespace tqd
