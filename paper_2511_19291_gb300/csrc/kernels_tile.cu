@@ -198,10 +198,65 @@ template <typename V> __device__ __forceinline__ V pool_c(const RT<V> *pool, int
     return mkc<V>(pool[off], pool[off + 1]);
 }
 
+template <int P, typename V> __device__ __forceinline__ void rg1r(V (&a)[NR], RT<V> m00, RT<V> m01, RT<V> m10,
+                                                                 RT<V> m11) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        if (j & (1 << P)) continue;
+        const V x0 = a[j], x1 = a[j | (1 << P)];
+        a[j] = mkc<V>(fma(m00, x0.x, m01 * x1.x), fma(m00, x0.y, m01 * x1.y));
+        a[j | (1 << P)] = mkc<V>(fma(m10, x0.x, m11 * x1.x), fma(m10, x0.y, m11 * x1.y));
+    }
+}
+
+// Per-thread factor of a diagonal run: the product of its gates whose
+// positions are all thread bits.  *any tells whether there is one.
+template <typename V>
+__device__ __forceinline__ V dg_thread_factor(const TileOp &op, const TileSub *subs, const RT<V> *pool, uint32_t tid,
+                                              bool &any) {
+    V f = mkc<V>(1, 0);
+    any = false;
+    for (int i = op.sub0; i < op.sub0 + op.nsub; ++i) {
+        const TileSub sb = subs[i];
+        if (!(sb.a & 0x80)) continue;
+        any = true;
+        const int ba = (tid >> (sb.a & 0x7f)) & 1u;
+        if (sb.type == TOP_D1) {
+            f = cmul(f, pool_c<V>(pool, sb.moff + (ba ? 6 : 0)));
+        } else if (ba && ((tid >> (sb.b & 0x7f)) & 1u)) {
+            f = cmul(f, pool_c<V>(pool, sb.moff));
+        }
+    }
+    return f;
+}
+
 // Apply one op (forward, or its inverse when DAG) to the 16 amplitudes.
 template <typename V, bool DAG>
-__device__ __forceinline__ void apply_op(const TileOp &op, V (&a)[NR], const RT<V> *pool, uint32_t tid) {
+__device__ __forceinline__ void apply_op(const TileOp &op, V (&a)[NR], const RT<V> *pool, uint32_t tid,
+                                         const TileSub *subs, const V *dgt) {
     switch (op.type) {
+    case TOP_G1R: {
+        RT<V> m00 = pool[op.moff], m01 = pool[op.moff + 2], m10 = pool[op.moff + 4], m11 = pool[op.moff + 6];
+        if (DAG) { const RT<V> t = m01; m01 = m10; m10 = t; }
+        with_pos(op.a, [&](auto P_) { rg1r<decltype(P_)::value>(a, m00, m01, m10, m11); });
+        break;
+    }
+    case TOP_DG: {
+        bool any;
+        const V f = dg_thread_factor<V>(op, subs, pool, tid, any);
+        const V *t = dgt + op.moff * NR;
+        if (any) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const V ph = cmul(t[j], f);
+                a[j] = cmul(a[j], DAG ? conjv(ph) : ph);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) a[j] = cmul(a[j], DAG ? conjv(t[j]) : t[j]);
+        }
+        break;
+    }
     case TOP_G1: {
         M2<V> m;
         m.a = pool_c<V>(pool, op.moff);
@@ -283,11 +338,36 @@ __device__ __forceinline__ RT<V> grad_g1(int gen, const V (&a)[NR], const V (&b)
     return s;
 }
 
+// Share of one diagonal gate's derivative given w_j = Im(conj(lambda_j) psi_j)
+// (unchanged by diagonal gates, so one w serves a whole run).
+template <typename V>
+__device__ __forceinline__ RT<V> grad_diag(uint8_t type, uint8_t pa, uint8_t pb, uint8_t gen, const RT<V> (&w)[NR],
+                                           uint32_t tid) {
+    using T = RT<V>;
+    T s = 0;
+    auto bit_of = [&](uint8_t pos, int j) -> int {
+        return (pos & 0x80) ? (int)((tid >> (pos & 0x7f)) & 1u) : ((j >> pos) & 1);
+    };
+    if (type == TOP_D1) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const int bit = bit_of(pa, j);
+            if (gen == GEN_Z) s += bit ? -w[j] : w[j];
+            else if (bit) s += w[j];  // GEN_P1
+        }
+        return gen == GEN_P1 ? T(-2) * s : s;
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+        if (bit_of(pa, j) && bit_of(pb, j)) s += w[j];
+    return T(-2) * s;
+}
+
 template <typename V>
 __device__ __forceinline__ RT<V> grad_op(const TileOp &op, const V (&a)[NR], const V (&b)[NR], uint32_t tid) {
     using T = RT<V>;
     T s = 0;
-    if (op.type == TOP_G1) {
+    if (op.type == TOP_G1 || op.type == TOP_G1R) {
         with_pos(op.a, [&](auto P_) { s = grad_g1<decltype(P_)::value>(op.gen, a, b); });
         return s;
     }
@@ -295,24 +375,7 @@ __device__ __forceinline__ RT<V> grad_op(const TileOp &op, const V (&a)[NR], con
     T w[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);
-    auto bit_of = [&](uint8_t pos, int j) -> int {
-        return (pos & 0x80) ? (int)((tid >> (pos & 0x7f)) & 1u) : ((j >> pos) & 1);
-    };
-    if (op.type == TOP_D1) {
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            const int bit = bit_of(op.a, j);
-            if (op.gen == GEN_Z) s += bit ? -w[j] : w[j];
-            else if (bit) s += w[j];  // GEN_P1
-        }
-        if (op.gen == GEN_P1) s *= T(-2);
-        return s;
-    }
-    // TOP_D2, GEN_P11
-#pragma unroll
-    for (int j = 0; j < NR; ++j)
-        if (bit_of(op.a, j) && bit_of(op.b, j)) s += w[j];
-    return T(-2) * s;
+    return grad_diag<V>(op.type, op.a, op.b, op.gen, w, tid);
 }
 
 template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
@@ -324,7 +387,7 @@ template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
 // Matrix scalars copied into the pool for an op: (source offset, length).
 __device__ __forceinline__ void op_pool_span(uint8_t type, int &src, int &len) {
     switch (type) {
-    case TOP_G1: case TOP_D1: src = 0; len = 8; break;
+    case TOP_G1: case TOP_G1R: case TOP_D1: src = 0; len = 8; break;
     case TOP_G2: src = 0; len = 32; break;
     case TOP_D2: src = 30; len = 2; break;
     default: src = 0; len = 0; break;
@@ -332,22 +395,24 @@ __device__ __forceinline__ void op_pool_span(uint8_t type, int &src, int &len) {
 }
 
 struct TileSmem {
-    uint32_t tiles, pool, gacc, total;
+    uint32_t tiles, pool, gacc, dgt, tbt, total;
 };
 
 template <typename V, bool ADJ>
-__host__ __device__ inline TileSmem tile_smem(int pool_len, int n_grad) {
+__host__ __device__ inline TileSmem tile_smem(int pool_len, int n_grad, int n_dg, int n_stages) {
     TileSmem s;
     s.tiles = (ADJ ? 2u : 1u) * (1u << TILE_K) * (uint32_t)sizeof(V);
     s.pool = (uint32_t)((pool_len * sizeof(RT<V>) + 15) & ~15u);
     s.gacc = (uint32_t)(n_grad * (TILE_THREADS / 32) * sizeof(KSum<RT<V>>));
     s.gacc = (s.gacc + 15) & ~15u;
-    s.total = 1024 + s.tiles + s.pool + s.gacc + 16;
+    s.dgt = (uint32_t)(n_dg * NR * sizeof(V));
+    s.tbt = (uint32_t)((n_stages * (32 + TILE_THREADS / 32) * sizeof(uint16_t) + 15) & ~15u);
+    s.total = 1024 + s.tiles + s.pool + s.gacc + s.dgt + s.tbt + 16;
     return s;
 }
 
 template <typename V, bool ADJ>
-__global__ void __launch_bounds__(TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, sizeof(V) == 8 ? (ADJ ? 2 : 3) : 1)
     k_tile(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam,
            const __grid_constant__ TilePassDev P, const RT<V> *__restrict__ mats, double *__restrict__ partials,
            int pblk, int *__restrict__ err) {
@@ -355,21 +420,34 @@ __global__ void __launch_bounds__(TILE_THREADS)
     extern __shared__ unsigned char smem_raw[];
     const uint32_t pad = (1024u - (sptr(smem_raw) & 1023u)) & 1023u;
     unsigned char *sm = smem_raw + pad;
-    const TileSmem L = tile_smem<V, ADJ>(P.pool_len, P.n_grad);
+    const TileSmem L = tile_smem<V, ADJ>(P.pool_len, P.n_grad, P.n_dg, P.n_stages);
     V *tile_a = reinterpret_cast<V *>(sm);
     V *tile_b = tile_a + (1 << TILE_K);
     T *pool = reinterpret_cast<T *>(sm + L.tiles);
     KSum<T> *gacc = reinterpret_cast<KSum<T> *>(sm + L.tiles + L.pool);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.tiles + L.pool + L.gacc);
+    V *dgt = reinterpret_cast<V *>(sm + L.tiles + L.pool + L.gacc);
+    uint16_t *tbt = reinterpret_cast<uint16_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt);
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    constexpr int TBS = 32 + TILE_THREADS / 32;
 
+    // matrices of every op and diagonal sub-op, per-stage lane/warp offsets
     for (int k = 0; k < P.n_ops; ++k) {
         const TileOp op = P.ops[k];
-        if (op.moff < 0) continue;
+        if (op.moff < 0 || op.type == TOP_DG) continue;
         int src, len;
         op_pool_span(op.type, src, len);
         for (int i = tid; i < len; i += blockDim.x) pool[op.moff + i] = mats[(size_t)P.op_gate[k] * MAT_STRIDE + src + i];
+    }
+    for (int k = 0; k < P.n_subs; ++k) {
+        const TileSub sb = P.subs[k];
+        const int src = sb.type == TOP_D1 ? 0 : 30, len = sb.type == TOP_D1 ? 8 : 2;
+        for (int i = tid; i < len; i += blockDim.x) pool[sb.moff + i] = mats[(size_t)P.sub_gate[k] * MAT_STRIDE + src + i];
+    }
+    for (int i = tid; i < P.n_stages * TBS; i += blockDim.x) {
+        const int st = i / TBS, e = i % TBS;
+        tbt[i] = e < 32 ? P.stages[st].tlo[e] : P.stages[st].thi[e - 32];
     }
     if (ADJ) {
         for (int i = tid; i < P.n_grad * (TILE_THREADS / 32); i += blockDim.x) gacc[i] = KSum<T>();
@@ -377,6 +455,21 @@ __global__ void __launch_bounds__(TILE_THREADS)
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_fence_init();
+    }
+    __syncthreads();
+    // phase tables of the diagonal runs: entry j = product of the run's gates
+    // whose positions are all register bits, evaluated at register index j
+    for (int i = tid; i < P.n_dg * NR; i += blockDim.x) {
+        const int d = i / NR, j = i % NR;
+        const TileOp op = P.ops[P.dg_op[d]];
+        V t = mkc<V>(1, 0);
+        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+            const TileSub sb = P.subs[q];
+            if (sb.a & 0x80) continue;
+            if (sb.type == TOP_D1) t = cmul(t, pool_c<V>(pool, sb.moff + (((j >> sb.a) & 1) ? 6 : 0)));
+            else if (((j >> sb.a) & 1) && ((j >> sb.b) & 1)) t = cmul(t, pool_c<V>(pool, sb.moff));
+        }
+        dgt[i] = t;
     }
     __syncthreads();
 
@@ -387,8 +480,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
 
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         uint64_t g0 = 0;
-        for (int i = 0; i < P.n_tiles_log2; ++i) g0 |= ((tile >> i) & 1ull) << P.out_bits[i];
         if (tid == 0) {
+            for (int i = 0; i < P.n_tiles_log2; ++i) g0 |= ((tile >> i) & 1ull) << P.out_bits[i];
             mbar_expect_tx(bar, tile_bytes * (ADJ ? 2u : 1u));
             for (int e = 0; e < (1 << P.n_extra); ++e) {
                 uint64_t g = g0;
@@ -415,10 +508,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
         for (int si = 0; si < P.n_stages; ++si) {
             const int s = ADJ ? P.n_stages - 1 - si : si;
             const TileStage &st = P.stages[s];
-            uint32_t tb = 0;
-#pragma unroll
-            for (int u = 0; u < TILE_T; ++u) tb |= ((tid >> u) & 1u) << st.thr[u];
-            const uint32_t tbs = swz<V>(tb);
+            const uint32_t tbs = swz<V>((uint32_t)tbt[s * TBS + lane] | (uint32_t)tbt[s * TBS + 32 + warp]);
             V a[NR];
             V b[ADJ ? NR : 1];
 #pragma unroll
@@ -427,16 +517,26 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 if constexpr (ADJ) b[j] = tile_b[tbs ^ st.roff[j]];
             }
             if constexpr (!ADJ) {
-                for (int k = st.op_begin; k < st.op_end; ++k) apply_op<V, false>(P.ops[k], a, pool, tid);
+                for (int k = st.op_begin; k < st.op_end; ++k) apply_op<V, false>(P.ops[k], a, pool, tid, P.subs, dgt);
             } else {
                 for (int k = (int)st.op_end - 1; k >= (int)st.op_begin; --k) {
                     const TileOp op = P.ops[k];
-                    if (op.gslot >= 0) {
+                    if (op.type == TOP_DG) {
+                        T w[NR];
+#pragma unroll
+                        for (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);
+                        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+                            const TileSub sb = P.subs[q];
+                            if (sb.gslot < 0) continue;
+                            const T part = warp_sum_t<T>(grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, tid));
+                            if (lane == 0) gacc[sb.gslot * (TILE_THREADS / 32) + warp].add(part);
+                        }
+                    } else if (op.gslot >= 0) {
                         const T part = warp_sum_t<T>(grad_op<V>(op, a, b, tid));
                         if (lane == 0) gacc[op.gslot * (TILE_THREADS / 32) + warp].add(part);
                     }
-                    apply_op<V, true>(op, a, pool, tid);
-                    apply_op<V, true>(op, b, pool, tid);
+                    apply_op<V, true>(op, a, pool, tid, P.subs, dgt);
+                    apply_op<V, true>(op, b, pool, tid, P.subs, dgt);
                 }
             }
 #pragma unroll
@@ -533,7 +633,7 @@ template <typename V, bool ADJ>
 static uint32_t max_smem(const tqd_circuit *c, int dt) {
     uint32_t m = 0;
     for (const auto &p : c->tile_passes) {
-        const TileSmem s = tile_smem<V, ADJ>(p.dev[dt].pool_len, p.dev[dt].n_grad);
+        const TileSmem s = tile_smem<V, ADJ>(p.dev[dt].pool_len, p.dev[dt].n_grad, p.dev[dt].n_dg, p.dev[dt].n_stages);
         if (s.total > m) m = s.total;
     }
     return m;
@@ -568,7 +668,7 @@ static cudaError_t launch_t(tqd_state *psi, tqd_state *lam, const tqd_circuit *c
         mb = ma;
     }
     const TilePassDev &D = pp.dev[dt];
-    const TileSmem sm = tile_smem<V, ADJ>(D.pool_len, D.n_grad);
+    const TileSmem sm = tile_smem<V, ADJ>(D.pool_len, D.n_grad, D.n_dg, D.n_stages);
     const int grid = grid_for<V, ADJ>(c, dt);
     const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
     ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);

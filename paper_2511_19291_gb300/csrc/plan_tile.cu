@@ -9,9 +9,9 @@
 // 2. TMA box.  Q's qubits above 3 are grouped into runs; the tensor map has at
 //    most 5 dimensions, so runs that do not fit become "extra" bits, copied by
 //    2^extra TMA operations per tile.
-// 3. Stages.  List scheduling over the pass's gates: a stage fixes 4 register
-//    bits, then takes every gate whose predecessors are scheduled and whose
-//    dense qubits are register bits.  Thread-index bits are assigned so that a
+// 3. Stages.  A stage fixes 4 register bits and takes, in gate order, every
+//    gate whose predecessors are scheduled or taken by the same stage and
+//    whose dense qubits fit in the register set.  Thread-index bits are assigned so that a
 //    half-warp's shared-memory accesses fall in different banks under the
 //    128-byte swizzle.
 #include <string.h>
@@ -238,42 +238,34 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
         int begin, end;
     };
     std::vector<StageH> stages;
-    auto ready = [&](int i) {
-        for (int p : preds[i])
-            if (!sched[p]) return false;
-        return true;
-    };
     while (nsched < m) {
-        // register set from the ready gates in order
+        // Closure in gate order: a gate joins the stage when each of its
+        // predecessors is scheduled or joined earlier in this stage and its
+        // dense qubits fit in the stage's register set together with those
+        // of the gates already joined.  Joined gates run in gate order.
         std::vector<int> rs;
-        for (int i = 0; i < m && (int)rs.size() < TILE_R; ++i) {
-            if (sched[i] || !ready(i)) continue;
+        std::vector<char> fit(m, 0);
+        for (int i = 0; i < m; ++i) {
+            if (sched[i]) continue;
+            bool preds_ok = true;
+            for (int p : preds[i]) preds_ok = preds_ok && (sched[p] || fit[p]);
+            if (!preds_ok) continue;
             int need[2], cnt;
             dense_needs(c->gates[P.gates[i]], loc.data(), need, cnt);
             std::vector<int> u(rs);
             for (int k = 0; k < cnt; ++k)
                 if (std::find(u.begin(), u.end(), need[k]) == u.end()) u.push_back(need[k]);
-            if ((int)u.size() <= TILE_R) rs = u;
+            if ((int)u.size() > TILE_R) continue;
+            rs = u;
+            fit[i] = 1;
         }
-        // take every gate that becomes executable with this register set
         StageH st;
         st.begin = (int)order.size();
-        bool progress = true;
-        while (progress) {
-            progress = false;
-            for (int i = 0; i < m; ++i) {
-                if (sched[i] || !ready(i)) continue;
-                int need[2], cnt;
-                dense_needs(c->gates[P.gates[i]], loc.data(), need, cnt);
-                bool fits = true;
-                for (int k = 0; k < cnt; ++k)
-                    fits = fits && std::find(rs.begin(), rs.end(), need[k]) != rs.end();
-                if (!fits) continue;
-                sched[i] = 1;
-                ++nsched;
-                order.push_back(i);
-                progress = true;
-            }
+        for (int i = 0; i < m; ++i) {
+            if (!fit[i]) continue;
+            sched[i] = 1;
+            ++nsched;
+            order.push_back(i);
         }
         st.end = (int)order.size();
         if (st.end == st.begin) return false;  // cannot happen: the first ready gate always fits
@@ -302,8 +294,8 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
         for (size_t i = 0; i < lay.out.size(); ++i) D.out_bits[i] = lay.out[i];
         for (size_t i = 0; i < lay.extra.size(); ++i) D.extra_bits[i] = lay.extra[i];
         D.n_stages = (int)stages.size();
-        D.n_ops = m;
-        int pool = 0, ngrad = 0;
+        int pool = 0, ngrad = 0, nops = 0, nsubs = 0;
+        D.n_dg = 0;
         const int amp_bytes = dt == 0 ? 8 : 16;
         for (size_t s = 0; s < stages.size(); ++s) {
             const StageH &sh = stages[s];
@@ -340,8 +332,18 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                     if ((j >> r) & 1) o |= 1u << sh.reg[r];
                 ts.roff[j] = (uint16_t)swz_host(o, amp_bytes);
             }
-            ts.op_begin = (uint16_t)sh.begin;
-            ts.op_end = (uint16_t)sh.end;
+            for (int l = 0; l < 32; ++l) {
+                uint32_t o = 0;
+                for (int u = 0; u < 5; ++u)
+                    if ((l >> u) & 1) o |= 1u << ts.thr[u];
+                ts.tlo[l] = (uint16_t)o;
+            }
+            for (int w = 0; w < TILE_THREADS / 32; ++w) {
+                uint32_t o = 0;
+                for (int u = 5; u < TILE_T; ++u)
+                    if ((w >> (u - 5)) & 1) o |= 1u << ts.thr[u];
+                ts.thi[w] = (uint16_t)o;
+            }
             auto pos = [&](int lb) -> uint8_t {
                 for (int r = 0; r < TILE_R; ++r)
                     if (ts.reg[r] == lb) return (uint8_t)r;
@@ -349,38 +351,97 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                     if (ts.thr[u] == lb) return (uint8_t)(0x80 | u);
                 return 0xff;
             };
-            for (int k = sh.begin; k < sh.end; ++k) {
-                const int gi = P.gates[order[k]];
-                const GateH &g = c->gates[gi];
-                TileOp &op = D.ops[k];
-                op.type = op_type_of(g.kind);
-                op.a = pos(loc[g.w[0]]);
-                op.b = g.nw > 1 ? pos(loc[g.w[1]]) : 0;
+            auto grad_of = [&](int gi, uint8_t &gen, int16_t &gslot) -> bool {
                 const int slot = c->grad_slot[gi];
-                op.gen = slot >= 0 ? (uint8_t)gate_gen(g.kind) : 0;
-                op.gslot = -1;
+                gen = slot >= 0 ? (uint8_t)gate_gen(c->gates[gi].kind) : 0;
+                gslot = -1;
                 if (slot >= 0) {
-                    op.gslot = (int16_t)ngrad;
+                    if (ngrad >= TILE_MAX_OPS) return false;
+                    gslot = (int16_t)ngrad;
                     D.grad_gate_slot[ngrad] = slot;
                     ++ngrad;
                 }
+                return true;
+            };
+            // a diagonal gate that can join a run: 1-qubit, or 2-qubit with both
+            // positions on register bits or both on thread bits
+            auto runnable = [&](int gi) {
+                const GateH &g = c->gates[gi];
+                if (!gate_diagonal(g.kind)) return false;
+                if (g.nw == 1) return true;
+                const uint8_t pa = pos(loc[g.w[0]]), pb = pos(loc[g.w[1]]);
+                return ((pa & 0x80) != 0) == ((pb & 0x80) != 0);
+            };
+            ts.op_begin = (uint16_t)nops;
+            int k = sh.begin;
+            while (k < sh.end) {
+                const int gi0 = P.gates[order[k]];
+                int run_end = k;
+                while (run_end < sh.end && runnable(P.gates[order[run_end]])) ++run_end;
+                if (nops >= TILE_MAX_OPS) return false;
+                TileOp &op = D.ops[nops];
+                memset(&op, 0, sizeof(op));
+                op.moff = -1;
+                op.gslot = -1;
+                op.sub0 = -1;
+                if (run_end - k >= 2) {
+                    // diagonal run
+                    if (D.n_dg >= TILE_MAX_DG || nsubs + (run_end - k) > TILE_MAX_SUBS) return false;
+                    op.type = TOP_DG;
+                    op.moff = (int16_t)D.n_dg;
+                    op.sub0 = (int16_t)nsubs;
+                    op.nsub = (int16_t)(run_end - k);
+                    D.dg_op[D.n_dg++] = (int16_t)nops;
+                    for (int q = k; q < run_end; ++q) {
+                        const int gi = P.gates[order[q]];
+                        const GateH &g = c->gates[gi];
+                        TileSub &sb = D.subs[nsubs];
+                        sb.type = g.nw == 1 ? TOP_D1 : TOP_D2;
+                        sb.a = pos(loc[g.w[0]]);
+                        sb.b = g.nw > 1 ? pos(loc[g.w[1]]) : 0;
+                        if (!grad_of(gi, sb.gen, sb.gslot)) return false;
+                        const int len = sb.type == TOP_D1 ? 8 : 2;
+                        sb.moff = (int16_t)pool;
+                        pool += len;
+                        D.sub_gate[nsubs] = gi;
+                        ++nsubs;
+                    }
+                    D.op_gate[nops] = gi0;
+                    ++nops;
+                    k = run_end;
+                    continue;
+                }
+                const GateH &g = c->gates[gi0];
+                op.type = op_type_of(g.kind);
+                if (op.type == TOP_G1 && (g.kind == TQD_RY || g.kind == TQD_H || g.kind == TQD_X)) op.type = TOP_G1R;
+                op.a = pos(loc[g.w[0]]);
+                op.b = g.nw > 1 ? pos(loc[g.w[1]]) : 0;
+                if (!grad_of(gi0, op.gen, op.gslot)) return false;
                 int len = 0;
                 switch (op.type) {
-                case TOP_G1: case TOP_D1: len = 8; break;
+                case TOP_G1: case TOP_G1R: case TOP_D1: len = 8; break;
                 case TOP_G2: len = 32; break;
                 case TOP_D2: len = 2; break;
                 default: len = 0; break;
                 }
                 op.moff = len ? (int16_t)pool : (int16_t)-1;
                 pool += len;
-                D.op_gate[k] = gi;
+                D.op_gate[nops] = gi0;
                 if (op.a == 0xff || op.b == 0xff) return false;
-                if ((op.type == TOP_G1 || op.type == TOP_SW || op.type == TOP_G2) && (op.a & 0x80)) return false;
+                if ((op.type == TOP_G1 || op.type == TOP_G1R || op.type == TOP_SW || op.type == TOP_G2) &&
+                    (op.a & 0x80))
+                    return false;
                 if ((op.type == TOP_CX || op.type == TOP_SW || op.type == TOP_G2) && (op.b & 0x80)) return false;
+                ++nops;
+                ++k;
             }
+            ts.op_end = (uint16_t)nops;
         }
+        D.n_ops = nops;
+        D.n_subs = nsubs;
         D.n_grad = ngrad;
         D.pool_len = pool;
+        if (pool > 32000) return false;
     }
     P.order.clear();
     for (int k = 0; k < m; ++k) P.order.push_back(P.gates[order[k]]);

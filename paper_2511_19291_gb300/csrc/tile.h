@@ -41,21 +41,39 @@ enum TileOpType : uint8_t {
     TOP_SW = 3,  // swap register positions a, b
     TOP_G2 = 4,  // dense 4x4, wires[0] on register position a (MSB), wires[1] on b
     TOP_D2 = 5,  // phase m33 when positions a and b are both 1 (CZ, CPHASE)
+    TOP_G1R = 6, // real 2x2 (RY, H) on register position a
+    TOP_DG = 7,  // run of diagonal gates: subs[sub0 .. sub0 + nsub), one phase per amplitude
 };
 
 struct TileOp {
     uint8_t type;
     uint8_t a, b;
     uint8_t gen;     // generator class for the angle derivative (Gen), 0 = none
-    int16_t moff;    // offset of the matrix in the block's pool (floats/doubles), -1 = none
+    int16_t moff;    // matrix offset in the pool (scalars), or the DG table index; -1 = none
     int16_t gslot;   // index among this pass's gradient ops, -1 = none
+    int16_t sub0;    // TOP_DG: first sub-op
+    int16_t nsub;    // TOP_DG: number of sub-ops
 };
+
+// One diagonal gate inside a TOP_DG run (type TOP_D1 or TOP_D2).
+struct TileSub {
+    uint8_t type;
+    uint8_t a, b;
+    uint8_t gen;
+    int16_t moff;    // d0, d1 (D1: scalars 0..7 of the 2x2) or ph (D2) in the pool
+    int16_t gslot;
+};
+
+constexpr int TILE_MAX_SUBS = 160;
+constexpr int TILE_MAX_DG = 64;
 
 struct TileStage {
     uint8_t reg[TILE_R];      // local bit of register-index bit r
     uint8_t thr[TILE_T];      // local bit of thread-index bit u
     uint16_t op_begin, op_end;
     uint16_t roff[1 << TILE_R];  // swizzled shared-memory offset of register j (amplitudes)
+    uint16_t tlo[32];         // local-index bits contributed by lane l
+    uint16_t thi[TILE_THREADS / 32];  // local-index bits contributed by warp w
 };
 
 // Everything a tile kernel needs for one pass (a kernel parameter).
@@ -72,9 +90,14 @@ struct TilePassDev {
     int n_ops;
     int n_grad;
     int pool_len;          // matrix pool length (scalars)
+    int n_subs;
+    int n_dg;              // diagonal runs (each has a 16-entry phase table)
     TileStage stages[TILE_MAX_STAGES];
     TileOp ops[TILE_MAX_OPS];
+    TileSub subs[TILE_MAX_SUBS];
     int32_t op_gate[TILE_MAX_OPS];        // circuit gate index of each op (matrix row)
+    int32_t sub_gate[TILE_MAX_SUBS];      // circuit gate index of each diagonal sub-op
+    int16_t dg_op[TILE_MAX_DG];           // op index of each diagonal run
     int32_t grad_gate_slot[TILE_MAX_OPS]; // circuit gradient slot of each gradient op
 };
 
