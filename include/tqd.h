@@ -134,6 +134,13 @@ tqd_status tqd_circuit_free(tqd_circuit *circuit);
 tqd_status tqd_circuit_info(const tqd_circuit *circuit, int *n_passes, int *n_launches_apply,
                             int *n_launches_backward);
 
+/* Synchronizes the device and reads the circuit's device error word:
+ * *device_error = 0 when every launch of this circuit completed normally,
+ * 1 when a bounded wait for a tile copy gave up (that launch's results are
+ * invalid), 2 when a kernel built with TQD_CHECKED found an index out of
+ * range.  Returns TQD_ERR_TIMEOUT for 1, TQD_ERR_NUMERIC for 2. */
+tqd_status tqd_circuit_check(const tqd_circuit *circuit, int *device_error);
+
 /* psi <- G_L ... G_1 psi (Sec. 4.1; gate semantics of Algorithm 1).
  * dev_params: device array of n_params doubles (may be NULL when n_params
  * is 0).  The state must have the circuit's qubit count. */

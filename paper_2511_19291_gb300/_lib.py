@@ -27,7 +27,7 @@ PLAN_PLAIN, PLAN_FUSED = 0, 1
 # Every symbol include/tqd.h declares (checked by the ABI test).
 EXPORTS = (
     "tqd_state_alloc", "tqd_state_reset", "tqd_state_free",
-    "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_apply_circuit",
+    "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
     "tqd_backward", "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
 )
@@ -96,6 +96,7 @@ def load(path: str | None = None):
         L.tqd_circuit_create.argtypes = [i32, vp, sz, i32, vp, sz, vp, C.POINTER(vp)]
         L.tqd_circuit_free.argtypes = [vp]
         L.tqd_circuit_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.tqd_circuit_check.argtypes = [vp, C.POINTER(i32)]
         L.tqd_apply_circuit.argtypes = [vp, vp, vp, vp]
         L.tqd_expval.argtypes = [vp, vp, sz, vp, vp]
         L.tqd_expval_terms.argtypes = [vp, vp, sz, vp, vp]
@@ -105,7 +106,7 @@ def load(path: str | None = None):
         L.tqd_profile_enable.argtypes = [i32]
         L.tqd_profile_read.argtypes = [vp, i32, C.POINTER(i32)]
         for name in ("tqd_state_alloc", "tqd_state_reset", "tqd_state_free", "tqd_circuit_create",
-                     "tqd_circuit_free", "tqd_circuit_info", "tqd_apply_circuit", "tqd_expval",
+                     "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit", "tqd_expval",
                      "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable", "tqd_backward",
                      "tqd_profile_enable",
                      "tqd_profile_read"):

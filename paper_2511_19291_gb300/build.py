@@ -33,6 +33,9 @@ def nvcc() -> str:
 def _flags(verbose_ptxas: bool) -> list:
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC,
                 "--expt-relaxed-constexpr", "-DNDEBUG"]
+    if os.environ.get("TQD_CHECKED") == "1":
+        # kernels check their shared-memory indices and record failures
+        f += ["-DTQD_CHECKED"]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]
     return f
@@ -40,6 +43,7 @@ def _flags(verbose_ptxas: bool) -> list:
 
 def _digest() -> str:
     h = hashlib.sha256()
+    h.update(b"checked" if os.environ.get("TQD_CHECKED") == "1" else b"release")
     for p in sorted(glob.glob(os.path.join(CSRC, "*")) + [os.path.join(INCLUDE, "tqd.h"), __file__]):
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())

@@ -233,6 +233,23 @@ tqd_status tqd_circuit_info(const tqd_circuit *c, int *n_passes, int *n_launches
     return TQD_OK;
 }
 
+tqd_status tqd_circuit_check(const tqd_circuit *c, int *device_error) {
+    CHECK_ARG(c != nullptr && device_error != nullptr, "tqd_circuit_check: NULL argument");
+    GUARD(c->device);
+    int v = 0;
+    CHECK_CUDA(cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    *device_error = v;
+    if (v == 1) {
+        tqd::set_error("tqd_circuit_check: a bounded wait for a tile copy gave up");
+        return TQD_ERR_TIMEOUT;
+    }
+    if (v != 0) {
+        tqd::set_error("tqd_circuit_check: a checked kernel found an index out of range (code %d)", v);
+        return TQD_ERR_NUMERIC;
+    }
+    return TQD_OK;
+}
+
 tqd_status tqd_apply_circuit(tqd_state *state, const tqd_circuit *c, const double *dev_params, void *stream) {
     CHECK_ARG(state != nullptr && c != nullptr, "tqd_apply_circuit: NULL state or circuit");
     CHECK_ARG(state->n == c->n, "tqd_apply_circuit: state has %d qubits, circuit %d", state->n, c->n);

@@ -115,5 +115,6 @@ struct tqd_circuit {
     int n_passes;
     bool fused;                  // tile passes (n >= 12) instead of the gate-by-gate plan
     std::vector<tqd::TilePlanPass> tile_passes;
-    int *d_err;                  // device error word (bounded waits that gave up)
+    tqd::TilePassDev *d_tile_desc;  // [pass][c64, c128] descriptors in device memory
+    int *d_err;                  // device error word (bounded waits that gave up, failed checks)
 };

@@ -209,6 +209,9 @@ template <int P, typename V> __device__ __forceinline__ void rg1r(V (&a)[NR], RT
     }
 }
 
+template <typename V, bool DAG>
+__device__ __forceinline__ void apply_op_rest(const TileOp &op, V (&a)[NR], const RT<V> *pool, uint32_t tid);
+
 // Per-thread factor of a diagonal run: the product of its gates whose
 // positions are all thread bits.  *any tells whether there is one.
 template <typename V>
@@ -230,33 +233,46 @@ __device__ __forceinline__ V dg_thread_factor(const TileOp &op, const TileSub *s
     return f;
 }
 
-// Apply one op (forward, or its inverse when DAG) to the 16 amplitudes.
-template <typename V, bool DAG>
-__device__ __forceinline__ void apply_op(const TileOp &op, V (&a)[NR], const RT<V> *pool, uint32_t tid,
+// Apply one op (forward, or its inverse when DAG) to the 16 amplitudes of a,
+// and of b too when TWO (the reverse sweep carries psi and lambda).
+template <typename V, bool DAG, bool TWO>
+__device__ __forceinline__ void apply_op(const TileOp &op, V (&a)[NR], V (&b)[NR], const RT<V> *pool, uint32_t tid,
                                          const TileSub *subs, const V *dgt) {
     switch (op.type) {
     case TOP_G1R: {
         RT<V> m00 = pool[op.moff], m01 = pool[op.moff + 2], m10 = pool[op.moff + 4], m11 = pool[op.moff + 6];
         if (DAG) { const RT<V> t = m01; m01 = m10; m10 = t; }
-        with_pos(op.a, [&](auto P_) { rg1r<decltype(P_)::value>(a, m00, m01, m10, m11); });
-        break;
+        with_pos(op.a, [&](auto P_) {
+            rg1r<decltype(P_)::value>(a, m00, m01, m10, m11);
+            if (TWO) rg1r<decltype(P_)::value>(b, m00, m01, m10, m11);
+        });
+        return;
     }
     case TOP_DG: {
         bool any;
         const V f = dg_thread_factor<V>(op, subs, pool, tid, any);
         const V *t = dgt + op.moff * NR;
-        if (any) {
 #pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const V ph = cmul(t[j], f);
-                a[j] = cmul(a[j], DAG ? conjv(ph) : ph);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < NR; ++j) a[j] = cmul(a[j], DAG ? conjv(t[j]) : t[j]);
+        for (int j = 0; j < NR; ++j) {
+            V ph = t[j];
+            if (any) ph = cmul(ph, f);
+            if (DAG) ph = conjv(ph);
+            a[j] = cmul(a[j], ph);
+            if (TWO) b[j] = cmul(b[j], ph);
         }
+        return;
+    }
+    default:
         break;
     }
+    apply_op_rest<V, DAG>(op, a, pool, tid);
+    if (TWO) apply_op_rest<V, DAG>(op, b, pool, tid);
+}
+
+// The remaining op types, one register array at a time.
+template <typename V, bool DAG>
+__device__ __forceinline__ void apply_op_rest(const TileOp &op, V (&a)[NR], const RT<V> *pool, uint32_t tid) {
+    switch (op.type) {
     case TOP_G1: {
         M2<V> m;
         m.a = pool_c<V>(pool, op.moff);
@@ -395,62 +411,99 @@ __device__ __forceinline__ void op_pool_span(uint8_t type, int &src, int &len) {
 }
 
 struct TileSmem {
-    uint32_t tiles, pool, gacc, dgt, tbt, total;
+    uint32_t tiles, pool, gacc, dgt, tbt, stages, ops, subs, total;
 };
 
 template <typename V, bool ADJ>
-__host__ __device__ inline TileSmem tile_smem(int pool_len, int n_grad, int n_dg, int n_stages) {
+__host__ __device__ inline TileSmem tile_smem(const TileHead &h) {
+    const int pool_len = h.pool_len, n_grad = h.n_grad, n_dg = h.n_dg, n_stages = h.n_stages;
     TileSmem s;
     s.tiles = (ADJ ? 2u : 1u) * (1u << TILE_K) * (uint32_t)sizeof(V);
     s.pool = (uint32_t)((pool_len * sizeof(RT<V>) + 15) & ~15u);
-    s.gacc = (uint32_t)(n_grad * (TILE_THREADS / 32) * sizeof(KSum<RT<V>>));
+    s.gacc = ADJ ? (uint32_t)(n_grad * TILE_THREADS * sizeof(RT<V>)) : 0u;
     s.gacc = (s.gacc + 15) & ~15u;
     s.dgt = (uint32_t)(n_dg * NR * sizeof(V));
-    s.tbt = (uint32_t)((n_stages * (32 + TILE_THREADS / 32) * sizeof(uint16_t) + 15) & ~15u);
-    s.total = 1024 + s.tiles + s.pool + s.gacc + s.dgt + s.tbt + 16;
+    s.tbt = (uint32_t)((n_stages * TILE_TB * sizeof(uint16_t) + 15) & ~15u);
+    s.stages = (uint32_t)(n_stages * sizeof(TileStage));
+    s.ops = (uint32_t)((h.n_ops * sizeof(TileOp) + 15) & ~15u);
+    s.subs = (uint32_t)((h.n_subs * sizeof(TileSub) + 15) & ~15u);
+    s.total = 1024 + s.tiles + s.pool + s.gacc + s.dgt + s.tbt + s.stages + s.ops + s.subs + 16;
     return s;
+}
+
+// Bounds checks of the shared-memory indices, compiled in with TQD_CHECKED:
+// a bad index is recorded in the error word (code 2) and the access skipped.
+#ifdef TQD_CHECKED
+#define TQD_IDX_OK(idx, lim) ((idx) < (lim) ? true : (atomicCAS(err, 0, 2), false))
+#else
+#define TQD_IDX_OK(idx, lim) true
+#endif
+
+// Copy `bytes` (a multiple of 4) from global to shared memory.
+__device__ __forceinline__ void copy_words(void *dst, const void *src, uint32_t bytes) {
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = s[i];
 }
 
 template <typename V, bool ADJ>
 __global__ void __launch_bounds__(TILE_THREADS, sizeof(V) == 8 ? (ADJ ? 2 : 3) : 1)
     k_tile(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam,
-           const __grid_constant__ TilePassDev P, const RT<V> *__restrict__ mats, double *__restrict__ partials,
+           const TilePassDev *__restrict__ Pg, const RT<V> *__restrict__ mats, double *__restrict__ partials,
            int pblk, int *__restrict__ err) {
     using T = RT<V>;
     extern __shared__ unsigned char smem_raw[];
+    __shared__ TileHead P;
+    copy_words(&P, &Pg->h, sizeof(TileHead));
+    __syncthreads();
     const uint32_t pad = (1024u - (sptr(smem_raw) & 1023u)) & 1023u;
     unsigned char *sm = smem_raw + pad;
-    const TileSmem L = tile_smem<V, ADJ>(P.pool_len, P.n_grad, P.n_dg, P.n_stages);
+    const TileSmem L = tile_smem<V, ADJ>(P);
     V *tile_a = reinterpret_cast<V *>(sm);
     V *tile_b = tile_a + (1 << TILE_K);
     T *pool = reinterpret_cast<T *>(sm + L.tiles);
-    KSum<T> *gacc = reinterpret_cast<KSum<T> *>(sm + L.tiles + L.pool);
+    T *gacc = reinterpret_cast<T *>(sm + L.tiles + L.pool);  // [grad op][thread]
     V *dgt = reinterpret_cast<V *>(sm + L.tiles + L.pool + L.gacc);
     uint16_t *tbt = reinterpret_cast<uint16_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt);
+    TileStage *stages = reinterpret_cast<TileStage *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt);
+    TileOp *ops = reinterpret_cast<TileOp *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages);
+    TileSub *subs = reinterpret_cast<TileSub *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops);
+    uint64_t *bar =
+        reinterpret_cast<uint64_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops + L.subs);
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    constexpr int TBS = 32 + TILE_THREADS / 32;
+    constexpr int TBS = TILE_TB;
+    constexpr int NW = TILE_THREADS / 32;
+
+    copy_words(stages, Pg->stages, P.n_stages * sizeof(TileStage));
+    copy_words(ops, Pg->ops, P.n_ops * sizeof(TileOp));
+    copy_words(subs, Pg->subs, P.n_subs * sizeof(TileSub));
+    __syncthreads();
 
     // matrices of every op and diagonal sub-op, per-stage lane/warp offsets
     for (int k = 0; k < P.n_ops; ++k) {
-        const TileOp op = P.ops[k];
+        const TileOp op = ops[k];
         if (op.moff < 0 || op.type == TOP_DG) continue;
         int src, len;
         op_pool_span(op.type, src, len);
-        for (int i = tid; i < len; i += blockDim.x) pool[op.moff + i] = mats[(size_t)P.op_gate[k] * MAT_STRIDE + src + i];
+        for (int i = tid; i < len; i += blockDim.x)
+            if (TQD_IDX_OK((uint32_t)(op.moff + i), (uint32_t)P.pool_len))
+                pool[op.moff + i] = mats[(size_t)Pg->op_gate[k] * MAT_STRIDE + src + i];
     }
     for (int k = 0; k < P.n_subs; ++k) {
-        const TileSub sb = P.subs[k];
+        const TileSub sb = subs[k];
         const int src = sb.type == TOP_D1 ? 0 : 30, len = sb.type == TOP_D1 ? 8 : 2;
-        for (int i = tid; i < len; i += blockDim.x) pool[sb.moff + i] = mats[(size_t)P.sub_gate[k] * MAT_STRIDE + src + i];
+        for (int i = tid; i < len; i += blockDim.x)
+            if (TQD_IDX_OK((uint32_t)(sb.moff + i), (uint32_t)P.pool_len))
+                pool[sb.moff + i] = mats[(size_t)Pg->sub_gate[k] * MAT_STRIDE + src + i];
     }
     for (int i = tid; i < P.n_stages * TBS; i += blockDim.x) {
         const int st = i / TBS, e = i % TBS;
-        tbt[i] = e < 32 ? P.stages[st].tlo[e] : P.stages[st].thi[e - 32];
+        const TileStage &S = stages[st];
+        tbt[i] = e < 32 ? S.ld_lo[e] : e < 32 + NW ? S.ld_hi[e - 32] : e < 64 + NW ? S.st_lo[e - 32 - NW] : S.st_hi[e - 64 - NW];
     }
     if (ADJ) {
-        for (int i = tid; i < P.n_grad * (TILE_THREADS / 32); i += blockDim.x) gacc[i] = KSum<T>();
+        for (int i = tid; i < P.n_grad * TILE_THREADS; i += blockDim.x) gacc[i] = T(0);
     }
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -461,10 +514,10 @@ __global__ void __launch_bounds__(TILE_THREADS, sizeof(V) == 8 ? (ADJ ? 2 : 3) :
     // whose positions are all register bits, evaluated at register index j
     for (int i = tid; i < P.n_dg * NR; i += blockDim.x) {
         const int d = i / NR, j = i % NR;
-        const TileOp op = P.ops[P.dg_op[d]];
+        const TileOp op = ops[Pg->dg_op[d]];
         V t = mkc<V>(1, 0);
         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
-            const TileSub sb = P.subs[q];
+            const TileSub sb = subs[q];
             if (sb.a & 0x80) continue;
             if (sb.type == TOP_D1) t = cmul(t, pool_c<V>(pool, sb.moff + (((j >> sb.a) & 1) ? 6 : 0)));
             else if (((j >> sb.a) & 1) && ((j >> sb.b) & 1)) t = cmul(t, pool_c<V>(pool, sb.moff));
@@ -507,42 +560,51 @@ __global__ void __launch_bounds__(TILE_THREADS, sizeof(V) == 8 ? (ADJ ? 2 : 3) :
 
         for (int si = 0; si < P.n_stages; ++si) {
             const int s = ADJ ? P.n_stages - 1 - si : si;
-            const TileStage &st = P.stages[s];
-            const uint32_t tbs = swz<V>((uint32_t)tbt[s * TBS + lane] | (uint32_t)tbt[s * TBS + 32 + warp]);
+            const TileStage &st = stages[s];
+            // forward: load through F, store through G; reverse: the other way
+            const uint16_t *tl = tbt + s * TBS;
+            const uint32_t base_ld = ADJ ? (uint32_t)(tl[32 + NW + lane] ^ tl[64 + NW + warp]) : (uint32_t)(tl[lane] ^ tl[32 + warp]);
+            const uint32_t base_st = ADJ ? (uint32_t)(tl[lane] ^ tl[32 + warp]) : (uint32_t)(tl[32 + NW + lane] ^ tl[64 + NW + warp]);
+            const uint16_t *roff_ld = ADJ ? st.st_roff : st.ld_roff;
+            const uint16_t *roff_st = ADJ ? st.ld_roff : st.st_roff;
             V a[NR];
-            V b[ADJ ? NR : 1];
+            V b[NR];
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                a[j] = tile_a[tbs ^ st.roff[j]];
-                if constexpr (ADJ) b[j] = tile_b[tbs ^ st.roff[j]];
+                const uint32_t ad = base_ld ^ roff_ld[j];
+                if (TQD_IDX_OK(ad, (uint32_t)(1 << TILE_K))) {
+                    a[j] = tile_a[ad];
+                    if constexpr (ADJ) b[j] = tile_b[ad];
+                }
             }
             if constexpr (!ADJ) {
-                for (int k = st.op_begin; k < st.op_end; ++k) apply_op<V, false>(P.ops[k], a, pool, tid, P.subs, dgt);
+                for (int k = st.op_begin; k < st.op_end; ++k)
+                    apply_op<V, false, false>(ops[k], a, b, pool, tid, subs, dgt);
             } else {
                 for (int k = (int)st.op_end - 1; k >= (int)st.op_begin; --k) {
-                    const TileOp op = P.ops[k];
+                    const TileOp op = ops[k];
                     if (op.type == TOP_DG) {
                         T w[NR];
 #pragma unroll
                         for (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);
                         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
-                            const TileSub sb = P.subs[q];
+                            const TileSub sb = subs[q];
                             if (sb.gslot < 0) continue;
-                            const T part = warp_sum_t<T>(grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, tid));
-                            if (lane == 0) gacc[sb.gslot * (TILE_THREADS / 32) + warp].add(part);
+                            gacc[sb.gslot * TILE_THREADS + tid] += grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, tid);
                         }
                     } else if (op.gslot >= 0) {
-                        const T part = warp_sum_t<T>(grad_op<V>(op, a, b, tid));
-                        if (lane == 0) gacc[op.gslot * (TILE_THREADS / 32) + warp].add(part);
+                        gacc[op.gslot * TILE_THREADS + tid] += grad_op<V>(op, a, b, tid);
                     }
-                    apply_op<V, true>(op, a, pool, tid, P.subs, dgt);
-                    apply_op<V, true>(op, b, pool, tid, P.subs, dgt);
+                    apply_op<V, true, true>(op, a, b, pool, tid, subs, dgt);
                 }
             }
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                tile_a[tbs ^ st.roff[j]] = a[j];
-                if constexpr (ADJ) tile_b[tbs ^ st.roff[j]] = b[j];
+                const uint32_t ad = base_st ^ roff_st[j];
+                if (TQD_IDX_OK(ad, (uint32_t)(1 << TILE_K))) {
+                    tile_a[ad] = a[j];
+                    if constexpr (ADJ) tile_b[ad] = b[j];
+                }
             }
             __syncthreads();
         }
@@ -568,10 +630,13 @@ __global__ void __launch_bounds__(TILE_THREADS, sizeof(V) == 8 ? (ADJ ? 2 : 3) :
     if (tid == 0) bulk_wait0();
     if constexpr (ADJ) {
         __syncthreads();
-        for (int k = tid; k < P.n_grad; k += blockDim.x) {
+        // per-thread partial sums (state precision, about 16 amplitudes x
+        // the block's tiles each) are added in FP64, one warp per gradient op
+        for (int k = warp; k < P.n_grad; k += NW) {
             double t = 0;
-            for (int w = 0; w < TILE_THREADS / 32; ++w) t += gacc[k * (TILE_THREADS / 32) + w].value();
-            partials[(size_t)P.grad_gate_slot[k] * pblk + blockIdx.x] = t;
+            for (int i = lane; i < TILE_THREADS; i += 32) t += (double)gacc[k * TILE_THREADS + i];
+            t = warp_sum(t);
+            if (lane == 0) partials[(size_t)Pg->grad_gate_slot[k] * pblk + blockIdx.x] = t;
         }
     }
 }
@@ -633,7 +698,7 @@ template <typename V, bool ADJ>
 static uint32_t max_smem(const tqd_circuit *c, int dt) {
     uint32_t m = 0;
     for (const auto &p : c->tile_passes) {
-        const TileSmem s = tile_smem<V, ADJ>(p.dev[dt].pool_len, p.dev[dt].n_grad, p.dev[dt].n_dg, p.dev[dt].n_stages);
+        const TileSmem s = tile_smem<V, ADJ>(p.dev[dt].h);
         if (s.total > m) m = s.total;
     }
     return m;
@@ -667,13 +732,13 @@ static cudaError_t launch_t(tqd_state *psi, tqd_state *lam, const tqd_circuit *c
     } else {
         mb = ma;
     }
-    const TilePassDev &D = pp.dev[dt];
-    const TileSmem sm = tile_smem<V, ADJ>(D.pool_len, D.n_grad, D.n_dg, D.n_stages);
+    const TileSmem sm = tile_smem<V, ADJ>(pp.dev[dt].h);
     const int grid = grid_for<V, ADJ>(c, dt);
     const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
     ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
     const RT<V> *mats = dt == 0 ? (const RT<V> *)c->d_mats32 : (const RT<V> *)c->d_mats64;
-    k_tile<V, ADJ><<<grid, TILE_THREADS, sm.total, s>>>(ma, mb, D, mats, c->d_partials, c->pblk, c->d_err);
+    k_tile<V, ADJ><<<grid, TILE_THREADS, sm.total, s>>>(ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials,
+                                                        c->pblk, c->d_err);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ tqd_status build_circuit(tqd_circuit *c) {
     c->d_param_ptr = nullptr;
     c->d_param_slots = nullptr;
     c->d_err = nullptr;
+    c->d_tile_desc = nullptr;
     c->fused = false;
 
     // gradient slots: one per parametric gate that reads the parameter vector
@@ -98,6 +99,12 @@ tqd_status build_circuit(tqd_circuit *c) {
         bool ok = !passes.empty();
         for (auto &p : passes) ok = ok && encode_tile_pass(c, p);
         if (ok) {
+            std::vector<TilePassDev> desc;
+            for (auto &p : passes) {
+                desc.push_back(p.dev[0]);
+                desc.push_back(p.dev[1]);
+            }
+            if ((e = upload(&c->d_tile_desc, desc)) != cudaSuccess) return fail(e);
             c->tile_passes = std::move(passes);
             c->fused = true;
             c->n_passes = (int)c->tile_passes.size();
@@ -130,6 +137,7 @@ void release_circuit(tqd_circuit *c) {
     cudaFree(c->d_param_ptr);
     cudaFree(c->d_param_slots);
     cudaFree(c->d_err);
+    cudaFree(c->d_tile_desc);
 }
 
 cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s) {

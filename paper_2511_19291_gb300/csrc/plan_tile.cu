@@ -80,6 +80,45 @@ uint32_t swz_host(uint32_t l, int amp_bytes) {
     return amp_bytes == 8 ? (l ^ (((l >> 4) & 7u) << 1)) : (l ^ ((l >> 3) & 7u));
 }
 
+// Affine map over GF(2) on 12-bit local indices: x -> L x ^ v.
+struct Aff {
+    uint32_t col[TILE_K];
+    uint32_t v;
+    Aff() : v(0) {
+        for (int i = 0; i < TILE_K; ++i) col[i] = 1u << i;
+    }
+    uint32_t lin(uint32_t x) const {
+        uint32_t r = 0;
+        for (int i = 0; i < TILE_K; ++i)
+            if ((x >> i) & 1) r ^= col[i];
+        return r;
+    }
+    uint32_t operator()(uint32_t x) const { return lin(x) ^ v; }
+};
+// (f o h)(x) = f(h(x))
+Aff compose(const Aff &f, const Aff &h) {
+    Aff r;
+    for (int i = 0; i < TILE_K; ++i) r.col[i] = f.lin(h.col[i]);
+    r.v = f(h.v);
+    return r;
+}
+bool is_perm_gate(int kind) { return kind == TQD_CNOT || kind == TQD_SWAP || kind == TQD_X; }
+// The permutation of local indices a CNOT / SWAP / X performs (each is its own inverse).
+Aff perm_map(const GateH &g, const int *loc) {
+    Aff m;
+    if (g.kind == TQD_CNOT) {
+        const int c = loc[g.w[0]], t = loc[g.w[1]];
+        m.col[c] ^= 1u << t;
+    } else if (g.kind == TQD_SWAP) {
+        const int p = loc[g.w[0]], q = loc[g.w[1]];
+        m.col[p] = 1u << q;
+        m.col[q] = 1u << p;
+    } else {
+        m.v = 1u << loc[g.w[0]];
+    }
+    return m;
+}
+
 }  // namespace
 
 bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L) {
@@ -185,15 +224,17 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c) {
         TilePlanPass P;
         P.layout = lay;
         std::vector<char> blocked(n, 0);
-        int blocked_in_q = 0;
+        int blocked_in_q = 0, ngrad = 0;
         for (int g = first; g < L; ++g) {
             if (done[g]) continue;
             const GateH &gh = c->gates[g];
-            bool ok = (int)P.gates.size() < TILE_MAX_OPS;
+            const bool is_grad = c->grad_slot[g] >= 0;
+            bool ok = (int)P.gates.size() < TILE_MAX_OPS && (!is_grad || ngrad < TILE_MAX_GRAD);
             for (int a = 0; a < gh.nw && ok; ++a) ok = inQ[gh.w[a]] && !blocked[gh.w[a]];
             if (ok) {
                 P.gates.push_back(g);
                 done[g] = 1;
+                if (is_grad) ++ngrad;
             } else {
                 for (int a = 0; a < gh.nw; ++a) {
                     if (!blocked[gh.w[a]]) {
@@ -283,19 +324,19 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
     for (int dt = 0; dt < 2; ++dt) {
         TilePassDev &D = P.dev[dt];
         memset(&D, 0, sizeof(D));
-        D.n = n;
-        D.n_tiles_log2 = n - TILE_K;
-        D.n_extra = (int)lay.extra.size();
-        D.rank = lay.rank[dt];
+        D.h.n = n;
+        D.h.n_tiles_log2 = n - TILE_K;
+        D.h.n_extra = (int)lay.extra.size();
+        D.h.rank = lay.rank[dt];
         for (int d = 0; d < TILE_MAX_DIMS; ++d) {
-            D.dim_lo[d] = d < D.rank ? lay.dim_lo[dt][d] : 0;
-            D.dim_len[d] = d < D.rank ? lay.dim_len[dt][d] : 0;
+            D.h.dim_lo[d] = d < D.h.rank ? lay.dim_lo[dt][d] : 0;
+            D.h.dim_len[d] = d < D.h.rank ? lay.dim_len[dt][d] : 0;
         }
-        for (size_t i = 0; i < lay.out.size(); ++i) D.out_bits[i] = lay.out[i];
-        for (size_t i = 0; i < lay.extra.size(); ++i) D.extra_bits[i] = lay.extra[i];
-        D.n_stages = (int)stages.size();
+        for (size_t i = 0; i < lay.out.size(); ++i) D.h.out_bits[i] = lay.out[i];
+        for (size_t i = 0; i < lay.extra.size(); ++i) D.h.extra_bits[i] = lay.extra[i];
+        D.h.n_stages = (int)stages.size();
         int pool = 0, ngrad = 0, nops = 0, nsubs = 0;
-        D.n_dg = 0;
+        D.h.n_dg = 0;
         const int amp_bytes = dt == 0 ? 8 : 16;
         for (size_t s = 0; s < stages.size(); ++s) {
             const StageH &sh = stages[s];
@@ -326,23 +367,36 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
             for (int b : free_bits)
                 if (std::find(lanes.begin(), lanes.end(), b) == lanes.end()) lanes.push_back(b);
             for (int u = 0; u < TILE_T; ++u) ts.thr[u] = (uint8_t)lanes[u];
+            // permutation gates at the start / end of the stage become the
+            // load map F = f1 o f2 o ... and the store map G = ... o g2 o g1
+            int lead_end = sh.begin;
+            while (lead_end < sh.end && is_perm_gate(c->gates[P.gates[order[lead_end]]].kind)) ++lead_end;
+            int trail_begin = sh.end;
+            while (trail_begin > lead_end && is_perm_gate(c->gates[P.gates[order[trail_begin - 1]]].kind))
+                --trail_begin;
+            Aff F, G;
+            for (int q = sh.begin; q < lead_end; ++q) F = compose(F, perm_map(c->gates[P.gates[order[q]]], loc.data()));
+            for (int q = trail_begin; q < sh.end; ++q) G = compose(perm_map(c->gates[P.gates[order[q]]], loc.data()), G);
             for (int j = 0; j < (1 << TILE_R); ++j) {
                 uint32_t o = 0;
                 for (int r = 0; r < TILE_R; ++r)
                     if ((j >> r) & 1) o |= 1u << sh.reg[r];
-                ts.roff[j] = (uint16_t)swz_host(o, amp_bytes);
+                ts.ld_roff[j] = (uint16_t)swz_host(F(o), amp_bytes);
+                ts.st_roff[j] = (uint16_t)swz_host(G(o), amp_bytes);
             }
             for (int l = 0; l < 32; ++l) {
                 uint32_t o = 0;
                 for (int u = 0; u < 5; ++u)
                     if ((l >> u) & 1) o |= 1u << ts.thr[u];
-                ts.tlo[l] = (uint16_t)o;
+                ts.ld_lo[l] = (uint16_t)swz_host(F.lin(o), amp_bytes);
+                ts.st_lo[l] = (uint16_t)swz_host(G.lin(o), amp_bytes);
             }
             for (int w = 0; w < TILE_THREADS / 32; ++w) {
                 uint32_t o = 0;
                 for (int u = 5; u < TILE_T; ++u)
                     if ((w >> (u - 5)) & 1) o |= 1u << ts.thr[u];
-                ts.thi[w] = (uint16_t)o;
+                ts.ld_hi[w] = (uint16_t)swz_host(F.lin(o), amp_bytes);
+                ts.st_hi[w] = (uint16_t)swz_host(G.lin(o), amp_bytes);
             }
             auto pos = [&](int lb) -> uint8_t {
                 for (int r = 0; r < TILE_R; ++r)
@@ -373,11 +427,11 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                 return ((pa & 0x80) != 0) == ((pb & 0x80) != 0);
             };
             ts.op_begin = (uint16_t)nops;
-            int k = sh.begin;
-            while (k < sh.end) {
+            int k = lead_end;
+            while (k < trail_begin) {
                 const int gi0 = P.gates[order[k]];
                 int run_end = k;
-                while (run_end < sh.end && runnable(P.gates[order[run_end]])) ++run_end;
+                while (run_end < trail_begin && runnable(P.gates[order[run_end]])) ++run_end;
                 if (nops >= TILE_MAX_OPS) return false;
                 TileOp &op = D.ops[nops];
                 memset(&op, 0, sizeof(op));
@@ -386,12 +440,12 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                 op.sub0 = -1;
                 if (run_end - k >= 2) {
                     // diagonal run
-                    if (D.n_dg >= TILE_MAX_DG || nsubs + (run_end - k) > TILE_MAX_SUBS) return false;
+                    if (D.h.n_dg >= TILE_MAX_DG || nsubs + (run_end - k) > TILE_MAX_SUBS) return false;
                     op.type = TOP_DG;
-                    op.moff = (int16_t)D.n_dg;
+                    op.moff = (int16_t)D.h.n_dg;
                     op.sub0 = (int16_t)nsubs;
                     op.nsub = (int16_t)(run_end - k);
-                    D.dg_op[D.n_dg++] = (int16_t)nops;
+                    D.dg_op[D.h.n_dg++] = (int16_t)nops;
                     for (int q = k; q < run_end; ++q) {
                         const int gi = P.gates[order[q]];
                         const GateH &g = c->gates[gi];
@@ -437,10 +491,10 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
             }
             ts.op_end = (uint16_t)nops;
         }
-        D.n_ops = nops;
-        D.n_subs = nsubs;
-        D.n_grad = ngrad;
-        D.pool_len = pool;
+        D.h.n_ops = nops;
+        D.h.n_subs = nsubs;
+        D.h.n_grad = ngrad;
+        D.h.pool_len = pool;
         if (pool > 32000) return false;
     }
     P.order.clear();

@@ -67,17 +67,26 @@ struct TileSub {
 constexpr int TILE_MAX_SUBS = 160;
 constexpr int TILE_MAX_DG = 64;
 
+// Shared-memory addresses of a stage.  Register j of thread (lane, warp)
+// holds local index y = tlo[lane] ^ thi[warp] ^ roff[j].  Permutation gates
+// (CNOT, SWAP, X) at the start of a stage are folded into the load address
+// F(y) and those at its end into the store address G(y); F and G are affine
+// maps over GF(2), so each address is an XOR of three table entries (already
+// swizzled).  The reverse sweep loads with G and stores with F.
 struct TileStage {
     uint8_t reg[TILE_R];      // local bit of register-index bit r
     uint8_t thr[TILE_T];      // local bit of thread-index bit u
     uint16_t op_begin, op_end;
-    uint16_t roff[1 << TILE_R];  // swizzled shared-memory offset of register j (amplitudes)
-    uint16_t tlo[32];         // local-index bits contributed by lane l
-    uint16_t thi[TILE_THREADS / 32];  // local-index bits contributed by warp w
+    uint16_t ld_roff[1 << TILE_R];
+    uint16_t st_roff[1 << TILE_R];
+    uint16_t ld_lo[32], ld_hi[TILE_THREADS / 32];
+    uint16_t st_lo[32], st_hi[TILE_THREADS / 32];
 };
+constexpr int TILE_TB = 2 * (32 + TILE_THREADS / 32);  // per-stage lane/warp table entries
+constexpr int TILE_MAX_GRAD = 32;                        // gradient ops per pass
 
-// Everything a tile kernel needs for one pass (a kernel parameter).
-struct TilePassDev {
+// Scalar part of a pass descriptor.
+struct TileHead {
     int n;                 // qubits of the state
     int n_tiles_log2;      // n - K
     int n_extra;           // top local bits not covered by the TMA box (2^n_extra copies per tile)
@@ -92,13 +101,21 @@ struct TilePassDev {
     int pool_len;          // matrix pool length (scalars)
     int n_subs;
     int n_dg;              // diagonal runs (each has a 16-entry phase table)
+    int pad[4];
+};
+
+// Everything a tile kernel needs for one pass.  It lives in device memory
+// (uploaded once per circuit); each block copies the parts it uses into
+// shared memory.
+struct TilePassDev {
+    TileHead h;
     TileStage stages[TILE_MAX_STAGES];
     TileOp ops[TILE_MAX_OPS];
     TileSub subs[TILE_MAX_SUBS];
     int32_t op_gate[TILE_MAX_OPS];        // circuit gate index of each op (matrix row)
     int32_t sub_gate[TILE_MAX_SUBS];      // circuit gate index of each diagonal sub-op
-    int16_t dg_op[TILE_MAX_DG];           // op index of each diagonal run
     int32_t grad_gate_slot[TILE_MAX_OPS]; // circuit gradient slot of each gradient op
+    int16_t dg_op[TILE_MAX_DG];           // op index of each diagonal run
 };
 
 // Host-side plan of one pass.

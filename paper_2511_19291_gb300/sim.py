@@ -161,6 +161,13 @@ class Circuit:
         _lib.check(_L().tqd_circuit_info(self._h, C.byref(a), C.byref(b), C.byref(c)))
         return {"passes": a.value, "launches_apply": b.value, "launches_backward": c.value}
 
+    def check(self) -> int:
+        """Synchronize and return the device error word (0 = all launches of
+        this circuit completed normally); raises on a non-zero word."""
+        v = C.c_int()
+        _lib.check(_L().tqd_circuit_check(self._h, C.byref(v)))
+        return v.value
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
