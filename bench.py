@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-qubits", type=int, default=0)
     ap.add_argument("--low-qubits", type=int, default=0)
+    ap.add_argument("--sweep-n", type=int, default=30, help="qubits of the plain gate-sweep measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -143,10 +144,14 @@ def stored_traffic(kernel):
     """DRAM bytes per launch from a committed ncu summary, valid only while the
     library source is unchanged since the capture."""
     try:
-        from paper_2511_19291_gb300 import build as B
+        import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        if t.get("source_digest") != B._digest():
+        h = hashlib.sha256()
+        for rel in t.get("source_files", []):
+            with open(os.path.join(ROOT, rel), "rb") as g:
+                h.update(g.read())
+        if t.get("source_digest") != h.hexdigest():
             return None
         return t.get("kernels", {}).get(kernel)
     except Exception:
@@ -204,6 +209,42 @@ def run_reference(args):
     }
     print(json.dumps(line))
     return 0
+
+
+# -------------------------------------------------- plain sweep measurement
+def sweep_bench(S, torch, dev, n, barrier, reps=5):
+    """Achieved HBM bandwidth of single gate sweeps (gate-by-gate kernels) on
+    an n-qubit complex64 state: RY (dense), RZ (diagonal) and CNOT at several
+    targets; algorithmic bytes from the library's own accounting."""
+    from paper_2511_19291_gb300 import workloads as W
+    st = S.State(n, torch.complex64, dev).reset(0)
+    targets = sorted({0, 1, 4, n // 2, n - 2, n - 1})
+    rows = []
+    for kind in ("RY", "RZ", "CNOT"):
+        for t in targets:
+            if kind == "CNOT":
+                g = W.Gate("CNOT", ((t + 1) % n, t))
+            else:
+                g = W.Gate(kind, (t,), angle=0.37)
+            c = S.Circuit(W.Circuit(n, [g] * reps, 0), mode="plain", device=dev)
+            S.apply(st, c)
+            barrier()
+            S.profile_enable(True)
+            S.apply(st, c)
+            torch.cuda.synchronize(dev)
+            prof = {p["name"]: p for p in S.profile_read()}
+            S.profile_enable(False)
+            k = {"RY": "dense1", "RZ": "diag1", "CNOT": "perm2"}[kind]
+            p = prof[k]
+            rows.append({"gate": kind, "target": t, "gbs": round(p["bytes"] / (p["ms"] / 1000.0) / 1e9, 1),
+                         "us": round(1000.0 * p["ms"] / p["launches"], 1)})
+    del st
+    torch.cuda.empty_cache()
+    peak, src = peaks()
+    best = max(r["gbs"] for r in rows)
+    worst = min(r["gbs"] for r in rows)
+    return {"n_qubits": n, "rows": rows, "min_frac": worst / peak, "max_frac": best / peak,
+            "peak": peak, "peak_source": f"{src} hbm_gbs"}
 
 
 # ------------------------------------------------------------- our path
@@ -305,6 +346,11 @@ def main():
         plain = {"value": world * args.plain_steps / (ms_plain / 1000.0), "unit": UNIT,
                  "ms_per_step": ms_plain / args.plain_steps, "steps": args.plain_steps}
 
+    # plain gate sweeps at 30 qubits: one full-state kernel per gate, GB/s per (gate, target)
+    sweep = None
+    if args.sweep_n > 0:
+        sweep = sweep_bench(S, torch, dev, args.sweep_n, barrier)
+
     # sanity of the numbers being timed: E of this step against a fresh forward
     psi.reset(0)
     S.apply(psi, circ, params)
@@ -351,6 +397,7 @@ def main():
         "cpu_baseline": cpu,
         "plain": plain,
         "fused_over_plain": (value / plain["value"]) if plain else None,
+        "sweep": sweep,
         "clocks": clk.summary(),
         "kernels": kernels,
         "energy": e_check,
