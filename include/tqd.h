@@ -206,6 +206,51 @@ tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *ci
 tqd_status tqd_expval_noalloc(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms,
                               double *dev_out, void *stream);
 
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent circuits of uneven width and depth (the batch dimension of
+ * Sec. 4, every circuit with its own state) evaluated together: forward,
+ * E_c = <H_c>, and the adjoint gradient of every E_c, all from one CUDA-graph
+ * launch.  Circuits of complex64 width up to `small_max_qubits` run whole in
+ * one block's shared memory (psi and lambda resident) from a persistent
+ * work-queue kernel; wider circuits run their fused tile passes on
+ * `streams` concurrent streams inside the same graph. */
+typedef struct tqd_batch tqd_batch;
+
+typedef struct {
+    uint32_t small_max_qubits; /* 0 = default (13) or the autotuned value */
+    uint32_t small_threads;    /* block size of the small-circuit kernel; 0 = default / autotuned */
+    uint32_t streams;          /* concurrent streams for the wider circuits; 0 = default (16) */
+    uint32_t autotune;         /* non-zero: time the candidates once at creation and keep the best */
+    uint32_t plain;            /* non-zero: every circuit gate by gate, one launch per gate (baseline) */
+    uint32_t reserved[3];      /* must be zero */
+} tqd_batch_opts;
+
+/* circuits: n_circuits planned circuits (complex64 widths 1..26); terms[c],
+ * n_terms[c]: circuit c's observable (host arrays, copied).  The batch owns
+ * its states and its device buffers for angles, energies and gradients (see
+ * tqd_batch_buffers); the circuits must outlive the batch. */
+tqd_status tqd_batch_create(int n_circuits, const tqd_circuit *const *circuits,
+                            const tqd_pauli_term *const *terms, const size_t *n_terms,
+                            const tqd_batch_opts *opts, tqd_batch **out);
+
+/* Device buffers owned by the batch: params (sum of the circuits' n_params
+ * doubles, circuit c's angles at param_offset[c]), energies (n_circuits
+ * doubles), grads (same layout as params, overwritten by every run).  Any
+ * pointer may be NULL.  param_offset (host, n_circuits entries) may be NULL. */
+tqd_status tqd_batch_buffers(tqd_batch *batch, double **dev_params, double **dev_energies, double **dev_grads,
+                             size_t *param_offset);
+
+/* One forward + expectation + adjoint gradient of every circuit, as one
+ * CUDA-graph launch on `stream`; the first call on a batch captures the graph
+ * (and warms the workspaces up), later calls replay it. */
+tqd_status tqd_batch_run(tqd_batch *batch, void *stream);
+
+tqd_status tqd_batch_info(const tqd_batch *batch, int *n_small, int *n_large, int *small_max_qubits,
+                          int *small_threads, int *graph_nodes);
+
+tqd_status tqd_batch_free(tqd_batch *batch);
+
 /* -------------------------------------------------------------- profiling */
 
 /* Per-kernel-class timing, summed over launches: CUDA events recorded on the

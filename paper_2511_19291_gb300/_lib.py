@@ -29,7 +29,8 @@ EXPORTS = (
     "tqd_state_alloc", "tqd_state_reset", "tqd_state_free",
     "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
-    "tqd_backward", "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
+    "tqd_backward", "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info", "tqd_batch_free",
+    "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
 )
 
 
@@ -62,6 +63,11 @@ class PauliTerm(C.Structure):
 class ProfileEntry(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
                 ("bytes", C.c_double)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("small_max_qubits", C.c_uint32), ("small_threads", C.c_uint32), ("streams", C.c_uint32),
+                ("autotune", C.c_uint32), ("plain", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 class PlanOpts(C.Structure):
@@ -103,12 +109,18 @@ def load(path: str | None = None):
         L.tqd_expval_noalloc.argtypes = [vp, vp, sz, vp, vp]
         L.tqd_apply_observable.argtypes = [vp, vp, sz, vp, vp, vp]
         L.tqd_backward.argtypes = [vp, vp, vp, vp, vp, sz, vp, dbl, vp, vp]
+        L.tqd_batch_create.argtypes = [i32, vp, vp, vp, vp, C.POINTER(vp)]
+        L.tqd_batch_buffers.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
+        L.tqd_batch_run.argtypes = [vp, vp]
+        L.tqd_batch_info.argtypes = [vp] + [C.POINTER(i32)] * 5
+        L.tqd_batch_free.argtypes = [vp]
         L.tqd_profile_enable.argtypes = [i32]
         L.tqd_profile_read.argtypes = [vp, i32, C.POINTER(i32)]
         for name in ("tqd_state_alloc", "tqd_state_reset", "tqd_state_free", "tqd_circuit_create",
                      "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit", "tqd_expval",
                      "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable", "tqd_backward",
-                     "tqd_profile_enable",
+                     "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info",
+                     "tqd_batch_free", "tqd_profile_enable",
                      "tqd_profile_read"):
             getattr(L, name).restype = st
         L.tqd_last_error.restype = C.c_char_p

@@ -102,6 +102,13 @@ cudaError_t launch_prep(const tqd_circuit *c, const double *dev_params, cudaStre
     return cudaGetLastError();
 }
 
+cudaError_t launch_prep_raw(const GateDev *gates, int ng, const double *dev_params, const double *table,
+                            double *m64, float *m32, cudaStream_t s) {
+    if (ng == 0) return cudaSuccess;
+    k_prep<<<(ng + 127) / 128, 128, 0, s>>>(gates, ng, dev_params, table, m64, m32);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ reset
 template <typename V>
 __global__ void k_reset(V *__restrict__ a, uint64_t N, uint64_t j) {
@@ -229,12 +236,28 @@ __global__ void __launch_bounds__(TPB) k_perm2(V *__restrict__ a, int n, int p, 
             st2(a + (b | off1), x0, y0);
         }
     } else {
+        // one wire is qubit 0: work on 16-byte pairs (b, b+1) and (b|H, b|H+1)
+        const uint64_t H = (uint64_t)1 << hi;
         const uint64_t units = (uint64_t)1 << (n - 2);
         for (; i < units; i += S) {
-            const uint64_t b = insert00(i, lo, hi);
-            const V x = a[b | off0], y = a[b | off1];
-            a[b | off0] = y;
-            a[b | off1] = x;
+            const uint64_t b = insert0(2 * i, hi);
+            if (kind == 0 && q == 0) {
+                // CNOT with target 0: swap the two amplitudes of the pair at b|control
+                V x, y;
+                ld2(a + (b | H), x, y);
+                st2(a + (b | H), y, x);
+            } else {
+                V x0, x1, y0, y1;
+                ld2(a + b, x0, x1);
+                ld2(a + (b | H), y0, y1);
+                if (kind == 0) {  // CNOT with control 0: swap (b+1) <-> (b|T)+1
+                    st2(a + b, x0, y1);
+                    st2(a + (b | H), y0, x1);
+                } else {          // SWAP(0, hi): swap (b+1) <-> (b|H)
+                    st2(a + b, x0, y0);
+                    st2(a + (b | H), x1, y1);
+                }
+            }
         }
     }
 }
@@ -258,10 +281,14 @@ __global__ void __launch_bounds__(TPB) k_phase11(V *__restrict__ a, int n, int p
             st2(a + b, cmul(x, ph), cmul(y, ph));
         }
     } else {
+        // one wire is qubit 0: the odd amplitude of the 16-byte pair at b|H
+        const uint64_t H = (uint64_t)1 << hi;
         const uint64_t units = (uint64_t)1 << (n - 2);
         for (; i < units; i += S) {
-            const uint64_t b = insert00(i, lo, hi) | PQ;
-            a[b] = cmul(a[b], ph);
+            const uint64_t b = insert0(2 * i, hi) | H;
+            V x, y;
+            ld2(a + b, x, y);
+            st2(a + b, x, cmul(y, ph));
         }
     }
 }

@@ -14,6 +14,10 @@ int stream_grid(uint64_t units, int threads);
 // Per-gate matrices from the angles (double and float copies).
 cudaError_t launch_prep(const tqd_circuit *c, const double *dev_params, cudaStream_t s);
 
+// Matrices for an explicit gate-record array (used by batches).
+cudaError_t launch_prep_raw(const GateDev *gates, int ng, const double *dev_params, const double *table,
+                            double *m64, float *m32, cudaStream_t s);
+
 // psi = e_j.
 cudaError_t launch_reset(tqd_state *st, uint64_t j, cudaStream_t s);
 

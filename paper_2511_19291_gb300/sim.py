@@ -329,3 +329,78 @@ def profile_read() -> list:
     _lib.check(_L().tqd_profile_read(C.cast(arr, C.c_void_p), cap, C.byref(n)))
     return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches), "ms": float(arr[i].total_ms),
              "bytes": float(arr[i].bytes)} for i in range(min(n.value, cap))]
+
+
+# -------------------------------------------------------------------- batches
+class _DevView:
+    """Zero-copy torch view of a float64 device buffer owned by the library."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+class Batch:
+    """Many independent circuits evaluated together (forward, E_c and the
+    adjoint gradient of every E_c) by one CUDA-graph launch per run.
+
+    ``circuits``: planned ``Circuit`` objects (distinct, complex64);
+    ``observables``: one Pauli-term list per circuit.  After ``set_params``,
+    ``run()`` fills ``energies`` and ``grads`` (device views; circuit c's
+    angles and gradient at ``offsets[c]``)."""
+
+    def __init__(self, circuits, observables, small_max_qubits=0, small_threads=0, streams=0, autotune=False,
+                 plain=False):
+        self.circuits = list(circuits)
+        self.obs = [as_observable(o) for o in observables]
+        n = len(self.circuits)
+        handles = (C.c_void_p * n)(*[c.handle.value for c in self.circuits])
+        tptrs = (C.c_void_p * n)(*[o.ptr.value for o in self.obs])
+        counts = (C.c_size_t * n)(*[len(o) for o in self.obs])
+        opts = _lib.BatchOpts()
+        opts.small_max_qubits = small_max_qubits
+        opts.small_threads = small_threads
+        opts.streams = streams
+        opts.autotune = 1 if autotune else 0
+        opts.plain = 1 if plain else 0
+        h = C.c_void_p()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        _lib.check(_L().tqd_batch_create(n, C.cast(handles, C.c_void_p), C.cast(tptrs, C.c_void_p),
+                                         C.cast(counts, C.c_void_p), C.byref(opts), C.byref(h)))
+        self._h = h
+        p, e, g = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        offs = (C.c_size_t * n)()
+        _lib.check(_L().tqd_batch_buffers(h, C.byref(p), C.byref(e), C.byref(g), C.cast(offs, C.c_void_p)))
+        self.offsets = [int(x) for x in offs]
+        self.n_params_total = sum(c.n_params for c in self.circuits)
+        np_ = max(1, self.n_params_total)
+        self.params = torch.as_tensor(_DevView(p.value, np_), device=self.device)
+        self.energies = torch.as_tensor(_DevView(e.value, n), device=self.device)
+        self.grads = torch.as_tensor(_DevView(g.value, np_), device=self.device)
+
+    def set_params(self, arrays):
+        flat = np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1)[: c.n_params]
+                               for a, c in zip(arrays, self.circuits)]) if self.n_params_total else np.zeros(0)
+        if flat.size:
+            self.params[: flat.size].copy_(torch.from_numpy(flat))
+
+    def run(self):
+        with torch.cuda.device(self.device):
+            _lib.check(_L().tqd_batch_run(self._h, _stream(self.device)))
+
+    def grads_of(self, c):
+        return self.grads[self.offsets[c]: self.offsets[c] + self.circuits[c].n_params]
+
+    def info(self) -> dict:
+        v = [C.c_int() for _ in range(5)]
+        _lib.check(_L().tqd_batch_info(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(["small", "large", "small_max_qubits", "small_threads", "graph_nodes"], [x.value for x in v]))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _L().tqd_batch_free(h)
+            except Exception:
+                pass
+            self._h = None

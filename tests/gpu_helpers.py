@@ -35,12 +35,16 @@ def to_numpy(state):
     return state.tensor.detach().cpu().numpy().astype(np.complex128)
 
 
-def grad_close(g, ref, rel):
-    """|g - ref| <= rel * max(|ref|, 1e-2 * max|ref|) componentwise."""
+def grad_close(g, ref, rel, hnorm=None):
+    """|g - ref| <= rel * max(|ref|, 1e-2 * max|ref|) componentwise; with
+    hnorm = ||H||_1 a component also passes when |g - ref| <= 1e-6 * ||H||_1
+    (complex64 error stated against the observable's scale)."""
     g = np.asarray(g)
     ref = np.asarray(ref)
     floor = 1e-2 * (np.max(np.abs(ref)) if ref.size else 0.0)
     bound = rel * np.maximum(np.abs(ref), floor) + 1e-300
+    if hnorm is not None:
+        bound = np.maximum(bound, 1e-6 * hnorm)
     bad = np.abs(g - ref) > bound
     return not bad.any(), np.max(np.abs(g - ref) / bound) if ref.size else 0.0
 
