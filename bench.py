@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--tile-qubits", type=int, default=0)
     ap.add_argument("--low-qubits", type=int, default=0)
     ap.add_argument("--sweep-n", type=int, default=30, help="qubits of the plain gate-sweep measurement (0 = skip)")
+    ap.add_argument("--batch-count", type=int, default=512, help="circuits of the batched measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -247,6 +248,37 @@ def sweep_bench(S, torch, dev, n, barrier, reps=5):
             "peak": peak, "peak_source": f"{src} hbm_gbs"}
 
 
+# ------------------------------------------------------- batched measurement
+def batch_bench(S, torch, dev, count, barrier, reps=3):
+    """512 ragged circuits (widths 10..20, depths 2..12, sum_i Z_i): forward +
+    adjoint gradient of every circuit per run.  Fused: one CUDA-graph launch
+    (autotuned); plain: every gate its own launch, issued by the host."""
+    from paper_2511_19291_gb300 import workloads as W
+    wl = W.batched_workload(count=count)
+    out = {"circuits": count, "widths": "10..20", "depths": "2..12", "observable": "sum_i Z_i"}
+    for mode in ("fused", "plain"):
+        circs = [S.Circuit(w.circuit, mode=mode, device=dev) for w in wl]
+        b = S.Batch(circs, [w.terms for w in wl], autotune=(mode == "fused"), plain=(mode == "plain"))
+        b.set_params([w.params for w in wl])
+        b.run()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        k = reps if mode == "fused" else 1
+        a.record()
+        for _ in range(k):
+            b.run()
+        e.record()
+        barrier()
+        ms = a.elapsed_time(e) / k
+        out[mode] = {"grad_evals_per_s": count / (ms / 1000.0), "ms_per_batch": ms, "runs": k}
+        if mode == "fused":
+            out[mode].update(b.info())
+        del b, circs
+    out["fused_over_plain"] = out["fused"]["grad_evals_per_s"] / out["plain"]["grad_evals_per_s"]
+    return out
+
+
 # ------------------------------------------------------------- our path
 def main():
     args = parse()
@@ -351,6 +383,10 @@ def main():
     if args.sweep_n > 0:
         sweep = sweep_bench(S, torch, dev, args.sweep_n, barrier)
 
+    batched = None
+    if args.batch_count > 0:
+        batched = batch_bench(S, torch, dev, args.batch_count, barrier)
+
     # sanity of the numbers being timed: E of this step against a fresh forward
     psi.reset(0)
     S.apply(psi, circ, params)
@@ -398,6 +434,7 @@ def main():
         "plain": plain,
         "fused_over_plain": (value / plain["value"]) if plain else None,
         "sweep": sweep,
+        "batched": batched,
         "clocks": clk.summary(),
         "kernels": kernels,
         "energy": e_check,
