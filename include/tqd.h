@@ -86,7 +86,10 @@ typedef struct {
 
 typedef enum {
     TQD_PLAN_PLAIN = 0, /* one full-state sweep per gate (gate-by-gate path) */
-    TQD_PLAN_FUSED = 1  /* fused passes: low-qubit and mixed tiles, diagonal runs */
+    TQD_PLAN_FUSED = 1, /* fused passes: low-qubit and mixed tiles, diagonal runs */
+    TQD_PLAN_TC = 2     /* as FUSED, and runs of >= 16 gates on qubits 0..5 become one fused
+                           64 x 64 unitary applied on the tensor cores (complex64 forward;
+                           split-precision TF32 products) */
 } tqd_plan_mode;
 
 typedef struct {

@@ -22,7 +22,7 @@ KIND_CODES = {
     "UNITARY1": 14, "UNITARY2": 15,
 }
 C64, C128 = 0, 1
-PLAN_PLAIN, PLAN_FUSED = 0, 1
+PLAN_PLAIN, PLAN_FUSED, PLAN_TC = 0, 1, 2
 
 # Every symbol include/tqd.h declares (checked by the ABI test).
 EXPORTS = (

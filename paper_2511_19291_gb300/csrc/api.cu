@@ -155,7 +155,8 @@ tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gate
     o.mode = TQD_PLAN_FUSED;
     if (opts) {
         o = *opts;
-        CHECK_ARG(o.mode == TQD_PLAN_PLAIN || o.mode == TQD_PLAN_FUSED, "tqd_circuit_create: unknown plan mode");
+        CHECK_ARG(o.mode == TQD_PLAN_PLAIN || o.mode == TQD_PLAN_FUSED || o.mode == TQD_PLAN_TC,
+                  "tqd_circuit_create: unknown plan mode");
         for (int i = 0; i < 5; ++i) CHECK_ARG(o.reserved[i] == 0, "tqd_circuit_create: reserved opts not zero");
     }
     std::vector<GateH> gs(n_gates);

@@ -115,6 +115,7 @@ struct tqd_circuit {
     int n_passes;
     bool fused;                  // tile passes (n >= 12) instead of the gate-by-gate plan
     std::vector<tqd::TilePlanPass> tile_passes;
+    std::vector<void *> tc_blocks;   // tqd::TcBlock*, forward of passes whose gates all act on qubits 0..5
     tqd::TilePassDev *d_tile_desc;  // [pass][c64, c128] descriptors in device memory
     int *d_err;                  // device error word (bounded waits that gave up, failed checks)
 };

@@ -1,10 +1,13 @@
 // plan.cu -- circuit planning (host) and the forward / backward executors.
 #include <string.h>
 
+#include <new>
+
 #include <vector>
 
 #include "launch.h"
 #include "plan.h"
+#include "tc.h"
 #include "tile_plan.h"
 
 namespace tqd {
@@ -94,7 +97,7 @@ tqd_status build_circuit(tqd_circuit *c) {
     if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return fail(e);
 
     // fused plan: tile passes, when the state holds at least one full tile
-    if (c->opts.mode == TQD_PLAN_FUSED && c->n >= TILE_K && ng > 0) {
+    if ((c->opts.mode == TQD_PLAN_FUSED || c->opts.mode == TQD_PLAN_TC) && c->n >= TILE_K && ng > 0) {
         std::vector<TilePlanPass> passes = plan_tile_passes(c);
         bool ok = !passes.empty();
         for (auto &p : passes) ok = ok && encode_tile_pass(c, p);
@@ -105,6 +108,29 @@ tqd_status build_circuit(tqd_circuit *c) {
                 desc.push_back(p.dev[1]);
             }
             if ((e = upload(&c->d_tile_desc, desc)) != cudaSuccess) return fail(e);
+            // tensor-core blocks: gate list and operand buffers per marked pass
+            for (auto &p : passes) {
+                if (p.tc < 0) continue;
+                std::vector<TcGate> tg;
+                for (int g : p.gates) {
+                    const GateH &h = c->gates[g];
+                    TcGate t;
+                    t.gate = g;
+                    t.nw = (uint8_t)h.nw;
+                    t.w0 = (uint8_t)h.w[0];
+                    t.w1 = (uint8_t)(h.nw > 1 ? h.w[1] : 0);
+                    t.pad = 0;
+                    tg.push_back(t);
+                }
+                TcBlock *b = new (std::nothrow) TcBlock();
+                if (!b) return fail(cudaErrorMemoryAllocation);
+                c->tc_blocks.push_back(b);
+                b->n_gates = (int)tg.size();
+                if ((e = upload(&b->d_gates, tg)) != cudaSuccess) return fail(e);
+                if ((e = cudaMalloc((void **)&b->d_ahi, 128 * 128 * sizeof(float))) != cudaSuccess) return fail(e);
+                if ((e = cudaMalloc((void **)&b->d_alo, 128 * 128 * sizeof(float))) != cudaSuccess) return fail(e);
+                p.tc = (int)c->tc_blocks.size() - 1;
+            }
             c->tile_passes = std::move(passes);
             c->fused = true;
             c->n_passes = (int)c->tile_passes.size();
@@ -138,6 +164,14 @@ void release_circuit(tqd_circuit *c) {
     cudaFree(c->d_param_slots);
     cudaFree(c->d_err);
     cudaFree(c->d_tile_desc);
+    for (void *v : c->tc_blocks) {
+        TcBlock *b = (TcBlock *)v;
+        cudaFree(b->d_gates);
+        cudaFree(b->d_ahi);
+        cudaFree(b->d_alo);
+        delete b;
+    }
+    c->tc_blocks.clear();
 }
 
 cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s) {
@@ -145,7 +179,11 @@ cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_
     if (e != cudaSuccess) return e;
     if (c->fused) {
         for (int p = 0; p < (int)c->tile_passes.size(); ++p) {
-            e = launch_tile_pass(psi, nullptr, c, p, s);
+            const TilePlanPass &pp = c->tile_passes[p];
+            if (pp.tc >= 0 && psi->dtype == TQD_C64)
+                e = launch_tc_block(psi, c, *(const TcBlock *)c->tc_blocks[pp.tc], s);
+            else
+                e = launch_tile_pass(psi, nullptr, c, p, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;

@@ -25,6 +25,9 @@
 
 namespace tqd {
 
+constexpr int TC_QUBITS = 6;       // qubits of a tensor-core block
+constexpr int TC_MIN_GATES = 16;   // shortest run worth a block
+
 namespace {
 
 // Register bits a gate needs in its stage (local bits).
@@ -175,6 +178,41 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c) {
     std::vector<char> done(L, 0);
     int first = 0;
     while (first < L) {
+        // --- tensor-core block: a long run of gates on qubits 0..5
+        if (c->opts.mode == TQD_PLAN_TC) {
+            std::vector<int> blk;
+            std::vector<char> blocked(n, 0);
+            int nb = 0;
+            for (int g = first; g < L && nb < TC_QUBITS && (int)blk.size() < TILE_MAX_OPS; ++g) {
+                if (done[g]) continue;
+                const GateH &gh = c->gates[g];
+                bool ok = c->grad_slot[g] < 0 || true;
+                for (int a = 0; a < gh.nw && ok; ++a) ok = gh.w[a] < TC_QUBITS && !blocked[gh.w[a]];
+                if (ok) {
+                    blk.push_back(g);
+                } else {
+                    for (int a = 0; a < gh.nw; ++a)
+                        if (!blocked[gh.w[a]]) {
+                            blocked[gh.w[a]] = 1;
+                            if (gh.w[a] < TC_QUBITS) ++nb;
+                        }
+                }
+            }
+            int ngrad = 0;
+            for (int g : blk) ngrad += c->grad_slot[g] >= 0 ? 1 : 0;
+            if ((int)blk.size() >= TC_MIN_GATES && ngrad <= TILE_MAX_GRAD) {
+                std::vector<char> inQ(n, 0);
+                for (int q = 0; q < TILE_K; ++q) inQ[q] = 1;
+                TilePlanPass P;
+                if (!tile_layout(n, inQ, P.layout)) return {};
+                P.gates = blk;
+                P.tc = 0;  // marked; the circuit builder assigns the block
+                for (int g : blk) done[g] = 1;
+                passes.push_back(P);
+                while (first < L && done[first]) ++first;
+                continue;
+            }
+        }
         // --- qubit set: low qubits, then the qubits of gates in order, each
         // addition accepted only if the TMA box still fits
         std::vector<char> inQ(n, 0);

@@ -1,0 +1,30 @@
+// tc.h -- fused 6-qubit blocks on the tensor cores (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace tqd {
+
+// One gate of a block: wires are qubits 0..5 (local index bits).
+struct TcGate {
+    int32_t gate;  // circuit gate index (row of the per-gate matrices)
+    uint8_t nw, w0, w1, pad;
+};
+
+// Device buffers of one block: its gates and the 128 x 128 real embedding of
+// the fused unitary, TF32 hi / lo halves in the tensor-core operand layout.
+struct TcBlock {
+    TcGate *d_gates;
+    int n_gates;
+    float *d_ahi;
+    float *d_alo;
+};
+
+// Builds the block's fused unitary from the current angles and applies it to
+// every 64-amplitude column of psi (complex64, n >= 12).
+cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock &blk, cudaStream_t s);
+
+}  // namespace tqd

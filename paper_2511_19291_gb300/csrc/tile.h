@@ -134,6 +134,7 @@ struct TilePlanPass {
     std::vector<int> gates;  // absorbed gates, circuit order
     std::vector<int> order;  // absorbed gates, execution order (stage schedule)
     TilePassDev dev[2];      // kernel descriptor for c64 / c128
+    int tc = -1;             // index of the tensor-core block that replaces this pass's forward (c64), or -1
 };
 
 }  // namespace tqd

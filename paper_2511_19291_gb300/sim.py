@@ -139,7 +139,7 @@ class Circuit:
                 table.extend(np.asarray(g.matrix, dtype=np.complex128).reshape(-1).tolist())
         mats = np.array([[v.real, v.imag] for v in table], dtype=np.float64).reshape(-1)
         opts = _lib.PlanOpts()
-        opts.mode = _lib.PLAN_PLAIN if mode == "plain" else _lib.PLAN_FUSED
+        opts.mode = {"plain": _lib.PLAN_PLAIN, "fused": _lib.PLAN_FUSED, "tc": _lib.PLAN_TC}[mode]
         opts.tile_qubits = tile_qubits
         opts.low_qubits = low_qubits
         h = C.c_void_p()

@@ -215,3 +215,48 @@ def test_invalid_state_use_raises():
         S.apply(st, c, params_tensor(np.zeros(circ.n_params)))
     with pytest.raises(Exception, match="qubit"):
         S.expval(st, [W.PauliTerm(1.0, ((7, "Z"),))])
+
+
+def tc_circuit(seed, n, blocks):
+    """Runs of 40 random gates (every kind) on qubits 0..5, each followed by RY
+    on the other qubits and two CNOTs that leave the block."""
+    rng = W.SplitMix64(seed)
+    gates, n_params = [], 0
+    for _ in range(blocks):
+        c6, _ = W.random_circuit(rng, 6, 40, n_params=8)
+        for g in c6.gates:
+            gates.append(W.Gate(g.kind, g.wires, g.param + n_params if g.param >= 0 else -1, g.angle, g.matrix))
+        n_params += 8
+        for q in range(6, n):
+            gates.append(W.Gate("RY", (q,), param=n_params))
+            n_params += 1
+        gates.append(W.Gate("CNOT", (5, 6)))
+        gates.append(W.Gate("CNOT", (n - 1, 0)))
+    return W.Circuit(n, gates, n_params), rng.angles(n_params)
+
+
+@pytest.mark.parametrize("n,blocks,seed", [(12, 2, 1), (14, 3, 2), (17, 2, 3)])
+def test_tensor_core_blocks(n, blocks, seed):
+    """Fused 6-qubit blocks on the tensor cores (split-precision TF32) in the
+    forward pass; the reverse sweep runs the same gates through tile passes."""
+    S = sim()
+    circ, params = tc_circuit(8000 + seed, n, blocks)
+    terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(seed), n, 5)
+    S.profile_enable(True)
+    st, c, p = gpu_state(circ, params, "tc", "c64")
+    torch.cuda.synchronize()
+    prof = {q["name"]: q for q in S.profile_read()}
+    S.profile_enable(False)
+    assert prof.get("tc_block", {}).get("launches", 0) >= 1
+    ref = oracle.run(circ, params)
+    np.testing.assert_allclose(to_numpy(st), ref, atol=1e-5, rtol=0)
+    e_ref, g_ref = oracle.grad_stored(circ, params, terms)
+    assert abs(S.expval(st, terms).item() - e_ref) < 1e-5
+    lam = S.State(n, torch.complex64)
+    g = torch.zeros(circ.n_params, dtype=torch.float64, device="cuda")
+    S.backward(st, lam, c, p, terms, g)
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4, hnorm=W.observable_l1(terms))
+    assert ok, worst
+    # complex128 states take the tile path for the same plan
+    st2, _, _ = gpu_state(circ, params, "tc", "c128")
+    np.testing.assert_allclose(to_numpy(st2), ref, atol=1e-12, rtol=0)
