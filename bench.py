@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--low-qubits", type=int, default=0)
     ap.add_argument("--sweep-n", type=int, default=30, help="qubits of the plain gate-sweep measurement (0 = skip)")
     ap.add_argument("--batch-count", type=int, default=512, help="circuits of the batched measurement (0 = skip)")
+    ap.add_argument("--tc-gates", type=int, default=200, help="gates of the tensor-core block measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -279,6 +280,47 @@ def batch_bench(S, torch, dev, count, barrier, reps=3):
     return out
 
 
+# ------------------------------------------------ tensor-core block measurement
+def tc_bench(S, torch, dev, n, n_gates, barrier, reps=5):
+    """One run of `n_gates` gates on qubits 0..5 of an n-qubit complex64 state:
+    the fused 64 x 64 block on the tensor cores against the same gates in one
+    tile pass.  Achieved bandwidth counts one read and one write of the state."""
+    from paper_2511_19291_gb300 import workloads as W
+    rng = W.SplitMix64(2511)
+    gates = []
+    for i in range(n_gates):
+        r = i % 3
+        if r == 0:
+            gates.append(W.Gate("RY", (i % 6,), angle=rng.angle()))
+        elif r == 1:
+            gates.append(W.Gate("RZ", ((i + 2) % 6,), angle=rng.angle()))
+        else:
+            gates.append(W.Gate("CNOT", (i % 6, (i + 1) % 6)))
+    circ = W.Circuit(n, gates, 0)
+    st = S.State(n, torch.complex64, dev).reset(0)
+    out = {"n_qubits": n, "gates": n_gates}
+    for mode, kern in (("tc", "tc_block"), ("fused", "tile_fwd")):
+        c = S.Circuit(circ, mode=mode, device=dev)
+        S.apply(st, c)
+        barrier()
+        S.profile_enable(True)
+        for _ in range(reps):
+            S.apply(st, c)
+        torch.cuda.synchronize(dev)
+        prof = {p["name"]: p for p in S.profile_read()}
+        S.profile_enable(False)
+        p = prof[kern]
+        ms = p["ms"] / p["launches"]
+        out[mode] = {"kernel": kern, "ms_per_pass": ms, "gbs": 2.0 * 8 * (1 << n) / (ms / 1000.0) / 1e9,
+                     "passes_per_apply": p["launches"] // reps}
+    peak, src = peaks()
+    out["tc"]["frac_of_hbm"] = out["tc"]["gbs"] / peak
+    out["tc_over_tile"] = out["fused"]["ms_per_pass"] * out["fused"]["passes_per_apply"] / \
+        (out["tc"]["ms_per_pass"] * out["tc"]["passes_per_apply"])
+    del st
+    return out
+
+
 # ------------------------------------------------------------- our path
 def main():
     args = parse()
@@ -383,6 +425,10 @@ def main():
     if args.sweep_n > 0:
         sweep = sweep_bench(S, torch, dev, args.sweep_n, barrier)
 
+    tcb = None
+    if args.tc_gates > 0:
+        tcb = tc_bench(S, torch, dev, args.n, args.tc_gates, barrier)
+
     batched = None
     if args.batch_count > 0:
         batched = batch_bench(S, torch, dev, args.batch_count, barrier)
@@ -435,6 +481,7 @@ def main():
         "fused_over_plain": (value / plain["value"]) if plain else None,
         "sweep": sweep,
         "batched": batched,
+        "tc_block": tcb,
         "clocks": clk.summary(),
         "kernels": kernels,
         "energy": e_check,
