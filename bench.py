@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-qubits", type=int, default=0)
     ap.add_argument("--low-qubits", type=int, default=0)
+    ap.add_argument("--buffers", type=int, default=0, choices=[0, 1, 2],
+                    help="tile buffers per block in the fused passes (0 = library default)")
+    ap.add_argument("--jit", type=int, default=0, choices=[0, 1, 2],
+                    help="fused passes: 1 generic kernel, 2 pass-specialised kernels, 0 library default")
     ap.add_argument("--sweep-n", type=int, default=30, help="qubits of the plain gate-sweep measurement (0 = skip)")
     ap.add_argument("--batch-count", type=int, default=512, help="circuits of the batched measurement (0 = skip)")
     ap.add_argument("--tc-gates", type=int, default=200, help="gates of the tensor-core block measurement (0 = skip)")
@@ -76,7 +80,9 @@ def config_of(args, w, plan):
         "workload": f"hea ansatz n={args.n} layers={args.layers} ({w.circuit.n_params} angles), "
                     f"open-chain Ising H ({len(w.terms)} terms), forward + expval + adjoint gradient",
         "n_qubits": args.n, "layers": args.layers, "n_params": w.circuit.n_params,
-        "gates": len(w.circuit.gates), "plan": plan, "amplitudes": "complex64",
+        "gates": len(w.circuit.gates), "plan": plan, "tile_buffers": args.buffers or "default",
+        "pass_kernels": {0: "default", 1: "generic", 2: "specialised"}[args.jit],
+        "amplitudes": "complex64",
         "reductions": "fp64 beyond per-thread partials",
         "l2": "inputs larger than L2 (state 2^n x 8 B; no flush needed)",
         "parallelism": "replicas",
@@ -344,7 +350,7 @@ def main():
     n = w.circuit.n_qubits
     obs = S.Observable(w.terms)
     circ = S.Circuit(w.circuit, mode=args.plan, tile_qubits=args.tile_qubits, low_qubits=args.low_qubits,
-                     device=dev)
+                     device=dev, buffers=args.buffers, jit=args.jit)
     psi = S.State(n, torch.complex64, dev)
     lam = S.State(n, torch.complex64, dev)
     params = torch.tensor(w.params, dtype=torch.float64, device=dev)

@@ -96,7 +96,16 @@ typedef struct {
     uint32_t mode;        /* tqd_plan_mode */
     uint32_t tile_qubits; /* fused tiles hold 2^tile_qubits amplitudes; 0 = default */
     uint32_t low_qubits;  /* contiguous low qubits in every mixed tile; 0 = default */
-    uint32_t reserved[5]; /* must be zero */
+    uint32_t buffers;     /* tile buffers per block in the fused passes: 1 = load, compute and
+                             store one tile at a time; 2 = load the next tile while the current
+                             one is computed (needs twice the shared memory); 0 = default */
+    uint32_t jit;         /* fused passes run 1 = the generic pass kernel, which reads positions,
+                             addresses and matrices from the pass descriptor; 2 = kernels
+                             specialised per pass (straight-line code with those fixed, compiled
+                             at run time with NVRTC on first use; TQD_ERR_UNSUPPORTED when NVRTC
+                             cannot be loaded); 0 = default: specialised from 22 qubits up, when
+                             NVRTC can be loaded */
+    uint32_t reserved[3]; /* must be zero */
 } tqd_plan_opts;
 
 typedef struct tqd_state tqd_state;
@@ -132,6 +141,17 @@ tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gate
                               const tqd_plan_opts *opts, tqd_circuit **out);
 
 tqd_status tqd_circuit_free(tqd_circuit *circuit);
+
+/* Diagnostics that need no GPU: validates the gate list as tqd_circuit_create
+ * does, plans its fused passes on the host (n_qubits >= 12), generates every
+ * pass-specialised kernel (both precisions, both directions; see
+ * tqd_plan_opts.jit) and compiles the distinct ones with NVRTC for compute
+ * capability `arch` (103 for sm_103a).  *n_kernels receives their number.
+ * TQD_ERR_UNSUPPORTED when NVRTC cannot be loaded; TQD_ERR_CUDA when a kernel
+ * fails to compile (tqd_last_error holds the start of the compiler log).  The
+ * paper has no counterpart: this checks code the library writes at run time. */
+tqd_status tqd_jit_check(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
+                         const double *matrices, size_t n_matrix_entries, int arch, int *n_kernels);
 
 /* Number of device launches one tqd_apply_circuit enqueues (for accounting). */
 tqd_status tqd_circuit_info(const tqd_circuit *circuit, int *n_passes, int *n_launches_apply,

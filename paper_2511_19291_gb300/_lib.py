@@ -27,7 +27,8 @@ PLAN_PLAIN, PLAN_FUSED, PLAN_TC = 0, 1, 2
 # Every symbol include/tqd.h declares (checked by the ABI test).
 EXPORTS = (
     "tqd_state_alloc", "tqd_state_reset", "tqd_state_free",
-    "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit",
+    "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_jit_check",
+    "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
     "tqd_backward", "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info", "tqd_batch_free",
     "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
@@ -72,7 +73,7 @@ class BatchOpts(C.Structure):
 
 class PlanOpts(C.Structure):
     _fields_ = [("mode", C.c_uint32), ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32),
-                ("reserved", C.c_uint32 * 5)]
+                ("buffers", C.c_uint32), ("jit", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 _lock = threading.Lock()
@@ -103,6 +104,7 @@ def load(path: str | None = None):
         L.tqd_circuit_free.argtypes = [vp]
         L.tqd_circuit_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.tqd_circuit_check.argtypes = [vp, C.POINTER(i32)]
+        L.tqd_jit_check.argtypes = [i32, vp, sz, i32, vp, sz, i32, C.POINTER(i32)]
         L.tqd_apply_circuit.argtypes = [vp, vp, vp, vp]
         L.tqd_expval.argtypes = [vp, vp, sz, vp, vp]
         L.tqd_expval_terms.argtypes = [vp, vp, sz, vp, vp]

@@ -20,7 +20,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtqd.so")
+GEN = os.path.join(BUILD, "gen")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# device headers handed to the run-time compiler for the pass-specialised kernels
+JIT_HEADERS = ["common.cuh", "tile_desc.h", "tile_dev.cuh"]
 
 
 def nvcc() -> str:
@@ -30,8 +33,29 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def _write_jit_headers() -> None:
+    """Embeds the device headers' text in the library (``tqd_jit_headers.inc``)."""
+    os.makedirs(GEN, exist_ok=True)
+    srcs = []
+    for name in JIT_HEADERS:
+        with open(os.path.join(CSRC, name)) as f:
+            text = f.read()
+        if ")TQDSRC" in text:
+            raise RuntimeError(f"{name} contains the raw-string delimiter")
+        srcs.append(text)
+    out = ["// Generated by build.py from csrc/: header texts for the run-time compiler.",
+           "static const char *const k_jit_header_names[] = {" + ", ".join(f'"{n}"' for n in JIT_HEADERS) + "};",
+           "static const char *const k_jit_header_srcs[] = {"]
+    out += [f'R"TQDSRC({t})TQDSRC",' for t in srcs]
+    out += ["};", f"static const int k_jit_n_headers = {len(JIT_HEADERS)};", ""]
+    path = os.path.join(GEN, "tqd_jit_headers.inc")
+    with open(path + ".tmp", "w") as f:
+        f.write("\n".join(out))
+    os.replace(path + ".tmp", path)
+
+
 def _flags(verbose_ptxas: bool) -> list:
-    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC,
+    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC, "-I", GEN,
                 "--expt-relaxed-constexpr", "-DNDEBUG"]
     if os.environ.get("TQD_CHECKED") == "1":
         # kernels check their shared-memory indices and record failures
@@ -59,6 +83,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
         with open(stamp) as f:
             if f.read().strip() == digest:
                 return LIB
+    _write_jit_headers()
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     cc = nvcc()
     flags = _flags(verbose_ptxas)

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "jit.h"
 #include "launch.h"
 #include "plan.h"
 
@@ -69,7 +70,10 @@ using namespace tqd;
     do {                                                                                  \
         cudaError_t e_ = (expr);                                                          \
         if (e_ != cudaSuccess) {                                                          \
-            tqd::set_error("%s failed: %s", #expr, cudaGetErrorString(e_));               \
+            /* the specialised-kernel errors keep the message they set */                 \
+            if (e_ == cudaErrorNotSupported) return TQD_ERR_UNSUPPORTED;                  \
+            if (e_ != cudaErrorInvalidSource && e_ != cudaErrorInvalidKernelImage)        \
+                tqd::set_error("%s failed: %s", #expr, cudaGetErrorString(e_));           \
             return e_ == cudaErrorMemoryAllocation ? TQD_ERR_OOM : TQD_ERR_CUDA;          \
         }                                                                                 \
     } while (0)
@@ -140,26 +144,28 @@ tqd_status tqd_state_free(tqd_state *state) {
 }
 
 // --------------------------------------------------------------- circuits
-tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
-                              const double *matrices, size_t n_matrix_entries, const tqd_plan_opts *opts,
-                              tqd_circuit **out) {
-    CHECK_ARG(out != nullptr, "tqd_circuit_create: out is NULL");
-    *out = nullptr;
+// Validates a gate list and the plan options; fills *o and *gs.
+static tqd_status validate_circuit(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
+                                   const double *matrices, size_t n_matrix_entries, const tqd_plan_opts *opts,
+                                   tqd_plan_opts *o_out, std::vector<GateH> *gs_out) {
     CHECK_ARG(n_qubits >= 1 && n_qubits <= 34, "tqd_circuit_create: n_qubits %d outside [1, 34]", n_qubits);
     CHECK_ARG(n_gates == 0 || gates != nullptr, "tqd_circuit_create: gates is NULL");
     CHECK_ARG(n_gates <= (1u << 24), "tqd_circuit_create: too many gates");
     CHECK_ARG(n_params >= 0, "tqd_circuit_create: negative n_params");
     CHECK_ARG(n_matrix_entries == 0 || matrices != nullptr, "tqd_circuit_create: matrices is NULL");
-    tqd_plan_opts o;
+    tqd_plan_opts &o = *o_out;
     memset(&o, 0, sizeof(o));
     o.mode = TQD_PLAN_FUSED;
     if (opts) {
         o = *opts;
         CHECK_ARG(o.mode == TQD_PLAN_PLAIN || o.mode == TQD_PLAN_FUSED || o.mode == TQD_PLAN_TC,
                   "tqd_circuit_create: unknown plan mode");
-        for (int i = 0; i < 5; ++i) CHECK_ARG(o.reserved[i] == 0, "tqd_circuit_create: reserved opts not zero");
+        CHECK_ARG(o.buffers <= 2, "tqd_circuit_create: buffers %u not in {0, 1, 2}", o.buffers);
+        CHECK_ARG(o.jit <= 2, "tqd_circuit_create: jit %u not in {0, 1, 2}", o.jit);
+        for (int i = 0; i < 3; ++i) CHECK_ARG(o.reserved[i] == 0, "tqd_circuit_create: reserved opts not zero");
     }
-    std::vector<GateH> gs(n_gates);
+    std::vector<GateH> &gs = *gs_out;
+    gs.assign(n_gates, GateH());
     for (size_t i = 0; i < n_gates; ++i) {
         const tqd_gate &g = gates[i];
         CHECK_ARG(g.kind <= TQD_UNITARY2, "gate %zu: unknown kind %u", i, g.kind);
@@ -199,6 +205,18 @@ tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gate
             return TQD_ERR_NUMERIC;
         }
     }
+    return TQD_OK;
+}
+
+tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
+                              const double *matrices, size_t n_matrix_entries, const tqd_plan_opts *opts,
+                              tqd_circuit **out) {
+    CHECK_ARG(out != nullptr, "tqd_circuit_create: out is NULL");
+    *out = nullptr;
+    tqd_plan_opts o;
+    std::vector<GateH> gs;
+    const tqd_status vs = validate_circuit(n_qubits, gates, n_gates, n_params, matrices, n_matrix_entries, opts, &o, &gs);
+    if (vs != TQD_OK) return vs;
     tqd_circuit *c = new (std::nothrow) tqd_circuit();
     if (!c) {
         set_error("tqd_circuit_create: out of host memory");
@@ -224,6 +242,25 @@ tqd_status tqd_circuit_free(tqd_circuit *c) {
     release_circuit(c);
     delete c;
     return TQD_OK;
+}
+
+tqd_status tqd_jit_check(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params, const double *matrices,
+                         size_t n_matrix_entries, int arch, int *n_kernels) {
+    CHECK_ARG(n_kernels != nullptr, "tqd_jit_check: n_kernels is NULL");
+    *n_kernels = 0;
+    CHECK_ARG(arch >= 100 && arch < 1000, "tqd_jit_check: arch %d is not a compute capability like 103", arch);
+    tqd_plan_opts o;
+    std::vector<GateH> gs;
+    const tqd_status vs = validate_circuit(n_qubits, gates, n_gates, n_params, matrices, n_matrix_entries, nullptr, &o,
+                                           &gs);
+    if (vs != TQD_OK) return vs;
+    CHECK_ARG(n_qubits >= TILE_K && n_gates > 0, "tqd_jit_check: fused passes need >= %d qubits and a gate", TILE_K);
+    tqd_circuit c;
+    c.n = n_qubits;
+    c.n_params = n_params;
+    c.opts = o;
+    c.gates = std::move(gs);
+    return jit_check_host(&c, arch, n_kernels);
 }
 
 tqd_status tqd_circuit_info(const tqd_circuit *c, int *n_passes, int *n_launches_apply, int *n_launches_backward) {

@@ -1,8 +1,10 @@
 // common.cuh -- device helpers shared by the libtqd kernels.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace tqd {
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,9 +35,6 @@ struct GateDev {
     double fixed;
 };
 
-// Generator class of a parametric gate: dG/dt = i * gen_factor * P * G.
-enum Gen { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_P1 = 4, GEN_P11 = 5 };
-
 __host__ __device__ inline int gate_arity(int kind) {
     switch (kind) {
     case TQD_CNOT: case TQD_CZ: case TQD_CPHASE: case TQD_SWAP: case TQD_UNITARY2: return 2;
@@ -60,8 +58,6 @@ __host__ __device__ inline int gate_gen(int kind) {
     default: return GEN_NONE;
     }
 }
-
-constexpr int MAT_STRIDE = 32;  // scalars per gate slot: 4x4 complex, interleaved
 
 // Pauli term grouped for the kernels: a group shares one x mask.
 struct TermDev {
@@ -118,4 +114,9 @@ struct tqd_circuit {
     std::vector<void *> tc_blocks;   // tqd::TcBlock*, forward of passes whose gates all act on qubits 0..5
     tqd::TilePassDev *d_tile_desc;  // [pass][c64, c128] descriptors in device memory
     int *d_err;                  // device error word (bounded waits that gave up, failed checks)
+    // pass-specialised kernels (CUfunction) per [precision][direction][pass],
+    // compiled on first use; nullptr entries run the generic kernel
+    mutable std::mutex jit_mu;
+    mutable std::vector<void *> jit_fn[2][2];
+    mutable bool jit_ready[2][2] = {{false, false}, {false, false}};
 };

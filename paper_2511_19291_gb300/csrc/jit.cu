@@ -1,0 +1,449 @@
+// jit.cu -- generation, run-time compilation (NVRTC) and launch of the
+// pass-specialised tile kernels.
+//
+// NVRTC is loaded with dlopen, so the library also loads where it is absent
+// (the default mode then keeps the generic kernel).  Compiled modules are
+// cached per device by source text: passes of the same shape (an ansatz
+// repeats its layers) share one kernel, whatever their angles, which stay in
+// the matrix buffer.
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <thread>
+#include <unordered_map>
+
+#include "jit.h"
+#include "plan.h"
+#include "prof.h"
+#include "tile.h"
+#include "tile_plan.h"
+
+#include "tqd_jit_headers.inc"  // k_jit_header_names / k_jit_header_srcs / k_jit_n_headers
+
+namespace tqd {
+
+// --------------------------------------------------------------- loading
+namespace {
+
+struct Nvrtc {
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+    bool ok = false;
+};
+
+const Nvrtc &nvrtc() {
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                               "/usr/local/cuda/lib64/libnvrtc.so"};
+        void *h = nullptr;
+        for (const char *nm : names)
+            if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) return;
+        n.create = (decltype(n.create))dlsym(h, "nvrtcCreateProgram");
+        n.compile = (decltype(n.compile))dlsym(h, "nvrtcCompileProgram");
+        n.log_size = (decltype(n.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+        n.log = (decltype(n.log))dlsym(h, "nvrtcGetProgramLog");
+        n.cubin_size = (decltype(n.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+        n.cubin = (decltype(n.cubin))dlsym(h, "nvrtcGetCUBIN");
+        n.destroy = (decltype(n.destroy))dlsym(h, "nvrtcDestroyProgram");
+        n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+    });
+    return n;
+}
+
+typedef CUresult (*FnModuleLoadData)(CUmodule *, const void *);
+typedef CUresult (*FnModuleGetFunction)(CUfunction *, CUmodule, const char *);
+typedef CUresult (*FnFuncSetAttribute)(CUfunction, CUfunction_attribute, int);
+typedef CUresult (*FnFuncGetAttribute)(int *, CUfunction_attribute, CUfunction);
+typedef CUresult (*FnLaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                                   CUstream, void **, void **);
+
+struct Driver {
+    FnModuleLoadData load = nullptr;
+    FnModuleGetFunction get = nullptr;
+    FnFuncSetAttribute attr = nullptr;
+    FnFuncGetAttribute get_attr = nullptr;
+    FnLaunchKernel launch = nullptr;
+    bool ok = false;
+};
+
+void *driver_sym(const char *name, int version) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return p;
+}
+
+const Driver &driver() {
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        d.load = (FnModuleLoadData)driver_sym("cuModuleLoadData", 12000);
+        d.get = (FnModuleGetFunction)driver_sym("cuModuleGetFunction", 12000);
+        d.attr = (FnFuncSetAttribute)driver_sym("cuFuncSetAttribute", 12000);
+        d.get_attr = (FnFuncGetAttribute)driver_sym("cuFuncGetAttribute", 12000);
+        d.launch = (FnLaunchKernel)driver_sym("cuLaunchKernel", 12000);
+        d.ok = d.load && d.get && d.attr && d.get_attr && d.launch;
+    });
+    return d;
+}
+
+// ------------------------------------------------------------ generation
+void put(std::string &o, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    o += buf;
+}
+
+const char *tf(bool b) { return b ? "true" : "false"; }
+
+// One op applied forward (or inverted in the reverse sweep, where it acts on
+// psi and lambda): the generic kernel's apply_op with every field constant.
+void emit_apply(std::string &o, const TilePassDev &D, const TileOp &op, bool adj) {
+    const char *dg = tf(adj), *two = tf(adj);
+    const int ta = op.a & 0x80, tb = op.b & 0x80;
+    switch (op.type) {
+    case TOP_G1R:
+        put(o, "op_g1r<TV, %s, %s, %d>(a, b, c.pool + %d);\n", dg, two, op.a, op.moff);
+        break;
+    case TOP_G1:
+        put(o, "op_g1<TV, %s, %s, %d>(a, b, c.pool + %d);\n", dg, two, op.a, op.moff);
+        break;
+    case TOP_D1:
+        if (ta) put(o, "op_d1t<TV, %s, %s>(a, b, c.pool + %d, tbit(tid, %d));\n", dg, two, op.moff, op.a);
+        else put(o, "op_d1r<TV, %s, %s, %d>(a, b, c.pool + %d);\n", dg, two, op.a, op.moff);
+        break;
+    case TOP_CX:
+        if (ta) put(o, "op_cxt<%s, %d>(a, b, tbit(tid, %d));\n", two, op.b, op.a);
+        else put(o, "op_cxr<%s, %d, %d>(a, b);\n", two, op.a, op.b);
+        break;
+    case TOP_SW:
+        put(o, "op_sw<%s, %d, %d>(a, b);\n", two, op.a, op.b);
+        break;
+    case TOP_G2:
+        put(o, "op_g2<TV, %s, %s, %d, %d>(a, b, c.pool + %d);\n", dg, two, op.a, op.b, op.moff);
+        break;
+    case TOP_D2:
+        if (ta && tb)
+            put(o, "op_d2tt<TV, %s, %s>(a, b, c.pool + %d, tbit(tid, %d) & tbit(tid, %d));\n", dg, two, op.moff, op.a,
+                op.b);
+        else if (ta)
+            put(o, "op_d2tr<TV, %s, %s, %d>(a, b, c.pool + %d, tbit(tid, %d));\n", dg, two, op.b, op.moff, op.a);
+        else if (tb)
+            put(o, "op_d2tr<TV, %s, %s, %d>(a, b, c.pool + %d, tbit(tid, %d));\n", dg, two, op.a, op.moff, op.b);
+        else
+            put(o, "op_d2rr<TV, %s, %s, %d, %d>(a, b, c.pool + %d);\n", dg, two, op.a, op.b, op.moff);
+        break;
+    case TOP_DG: {
+        // thread factor of the run's gates on thread bits, then the table
+        bool any = false;
+        o += "{\nTV f = mkc<TV>(1, 0);\n";
+        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+            const TileSub &sb = D.subs[q];
+            if (!(sb.a & 0x80)) continue;
+            any = true;
+            if (sb.type == TOP_D1)
+                put(o, "f = cmul(f, pool_c<TV>(c.pool, %d + (tbit(tid, %d) ? 6 : 0)));\n", sb.moff, sb.a);
+            else
+                put(o, "if (tbit(tid, %d) & tbit(tid, %d)) f = cmul(f, pool_c<TV>(c.pool, %d));\n", sb.a, sb.b,
+                    sb.moff);
+        }
+        put(o, "op_dg<TV, %s, %s, %s>(a, b, c.dgt + %d * NR, f);\n}\n", dg, two, tf(any), op.moff);
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// Reverse sweep: the op's angle derivatives from (psi, lambda) after it.
+void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
+    if (op.type == TOP_DG) {
+        bool need = false;
+        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) need |= D.subs[q].gslot >= 0;
+        if (!need) return;
+        o += "{\nTT w[NR];\nfor (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);\n";
+        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+            const TileSub &sb = D.subs[q];
+            if (sb.gslot < 0) continue;
+            put(o, "c.gacc[%d * TILE_THREADS + tid] += grad_diag<TV>(%d, %d, %d, %d, w, tid);\n", sb.gslot, sb.type,
+                sb.a, sb.b, sb.gen);
+        }
+        o += "}\n";
+        return;
+    }
+    if (op.gslot < 0) return;
+    if (op.type == TOP_G1 || op.type == TOP_G1R)
+        put(o, "c.gacc[%d * TILE_THREADS + tid] += grad_g1<%d, TV>(%d, a, b);\n", op.gslot, op.a, op.gen);
+    else
+        put(o, "c.gacc[%d * TILE_THREADS + tid] += grad_diag_op<TV>(%d, %d, %d, %d, a, b, tid);\n", op.gslot, op.type,
+            op.a, op.b, op.gen);
+}
+
+std::string generate(const TilePassDev &D, int dt, bool adj) {
+    const TileHead &h = D.h;
+    std::string o;
+    o.reserve(1 << 16);
+    o += "#include \"tile_dev.cuh\"\nnamespace tqd {\n";
+    put(o, "typedef %s TV;\ntypedef %s TT;\nconstexpr bool KADJ = %s;\n", dt == 0 ? "float2" : "double2",
+        dt == 0 ? "float" : "double", tf(adj));
+    o += "struct PassRunner {\nstatic __device__ __forceinline__ void run(const TileCtx<TV> &c) {\n"
+         "int *err = c.err;\n(void)err;\nconst uint32_t tid = c.tid;\nTV a[NR];\nTV b[NR];\n";
+    for (int si = 0; si < h.n_stages; ++si) {
+        const int s = adj ? h.n_stages - 1 - si : si;
+        const TileStage &st = D.stages[s];
+        put(o, "{\nconst uint16_t *tl = c.tbt + %d * TILE_TB;\n", s);
+        o += "const uint32_t bl = stage_base_ld<KADJ>(tl, c.lane, c.warp);\n"
+             "const uint32_t bs = stage_base_st<KADJ>(tl, c.lane, c.warp);\n";
+        const uint16_t *rl = adj ? st.st_roff : st.ld_roff;
+        const uint16_t *rs = adj ? st.ld_roff : st.st_roff;
+        for (int j = 0; j < (1 << TILE_R); ++j) put(o, "tile_ld<TV, KADJ>(c, a, b, %d, bl ^ %uu);\n", j, (unsigned)rl[j]);
+        if (!adj) {
+            for (int k = st.op_begin; k < st.op_end; ++k) emit_apply(o, D, D.ops[k], false);
+        } else {
+            for (int k = (int)st.op_end - 1; k >= (int)st.op_begin; --k) {
+                emit_grad(o, D, D.ops[k]);
+                emit_apply(o, D, D.ops[k], true);
+            }
+        }
+        for (int j = 0; j < (1 << TILE_R); ++j) put(o, "tile_st<TV, KADJ>(c, a, b, %d, bs ^ %uu);\n", j, (unsigned)rs[j]);
+        if (si == h.n_stages - 1) o += "fence_async_smem();\n";
+        o += "__syncthreads();\n}\n";
+    }
+    o += "}\n};\n}  // namespace tqd\n";
+    // the generic kernel's launch bounds (tile_min_blocks<V, ADJ, 1>)
+    const int minb = dt == 0 ? (adj ? 2 : 3) : 1;
+    put(o,
+        "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
+        "tqd_pass(const __grid_constant__ tqd::TmaDesc mp, const __grid_constant__ tqd::TmaDesc ml,\n"
+        "         const tqd::TilePassDev *__restrict__ Pg, const tqd::TT *__restrict__ mats,\n"
+        "         double *__restrict__ partials, int pblk, int *__restrict__ err) {\n"
+        "    tqd::tile_pass_body<tqd::TV, tqd::KADJ, 1, tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n"
+        "}\n",
+        TILE_THREADS, minb);
+    return o;
+}
+
+// ----------------------------------------------------------- compilation
+int device_arch(int dev) {
+    int mj = 0, mn = 0;
+    cudaDeviceGetAttribute(&mj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&mn, cudaDevAttrComputeCapabilityMinor, dev);
+    return mj * 10 + mn;
+}
+
+// Source -> cubin; empty with the log in *log on failure.
+std::string compile_cubin(const std::string &src, int arch, std::string *log) {
+    const Nvrtc &N = nvrtc();
+    nvrtcProgram prog;
+    if (N.create(&prog, src.c_str(), "tqd_pass.cu", k_jit_n_headers, k_jit_header_srcs, k_jit_header_names) !=
+        NVRTC_SUCCESS) {
+        *log = "nvrtcCreateProgram failed";
+        return std::string();
+    }
+    char archopt[64];
+    snprintf(archopt, sizeof(archopt), "--gpu-architecture=sm_%da", arch);
+    const char *opts[] = {archopt, "-std=c++17", "-DNDEBUG",
+#ifdef TQD_CHECKED
+                          "-DTQD_CHECKED",
+#endif
+    };
+    const nvrtcResult r = N.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
+    std::string out;
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        N.log_size(prog, &n);
+        log->assign(n, '\0');
+        if (n) N.log(prog, &(*log)[0]);
+    } else {
+        size_t n = 0;
+        N.cubin_size(prog, &n);
+        out.assign(n, '\0');
+        if (n) N.cubin(prog, &out[0]);
+    }
+    N.destroy(&prog);
+    return out;
+}
+
+std::mutex g_cache_mu;
+std::map<std::pair<int, std::string>, CUfunction> g_cache;  // (device, source) -> kernel
+
+}  // namespace
+
+bool jit_wanted(const tqd_circuit *c) {
+    if (!c->fused || c->opts.jit == 1) return false;
+    if (c->opts.jit == 2) return true;
+    return c->n >= 22 && nvrtc().ok && driver().ok;
+}
+
+std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj) {
+    return generate(c->tile_passes[pass].dev[dt], dt, adj);
+}
+
+static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj) {
+    if (!nvrtc().ok || !driver().ok) {
+        set_error("specialised pass kernels: NVRTC or the CUDA driver entry points are unavailable");
+        return cudaErrorNotSupported;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaFree(nullptr);  // the device's primary context is current from here on
+    const int np = (int)c->tile_passes.size();
+    std::vector<std::string> srcs(np);
+    std::vector<int> need;  // passes whose source is not cached yet (first of each shape)
+    std::unordered_map<std::string, int> first;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        for (int p = 0; p < np; ++p) {
+            if (!adj && dt == 0 && c->tile_passes[p].tc >= 0) continue;  // forward runs on the tensor cores
+            srcs[p] = jit_source(c, p, dt, adj);
+            if (g_cache.count({dev, srcs[p]}) || first.count(srcs[p])) continue;
+            first[srcs[p]] = p;
+            need.push_back(p);
+        }
+    }
+    // compile the new shapes in parallel
+    const int arch = device_arch(dev);
+    std::vector<std::string> cubins(need.size()), logs(need.size());
+    {
+        const int nt = std::max(1, std::min<int>((int)need.size(), (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        std::atomic<int> next(0);
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&] {
+                for (int i; (i = next.fetch_add(1)) < (int)need.size();)
+                    cubins[i] = compile_cubin(srcs[need[i]], arch, &logs[i]);
+            });
+        for (auto &t : th) t.join();
+    }
+    const Driver &D = driver();
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (size_t i = 0; i < need.size(); ++i) {
+        if (cubins[i].empty()) {
+            set_error("specialised pass kernel failed to compile: %.400s", logs[i].c_str());
+            return cudaErrorInvalidSource;
+        }
+        CUmodule mod;
+        CUfunction f;
+        CUresult r = D.load(&mod, cubins[i].data());
+        if (r == CUDA_SUCCESS) r = D.get(&f, mod, "tqd_pass");
+        if (r != CUDA_SUCCESS) {
+            set_error("specialised pass kernel: module load failed (CUresult %d)", (int)r);
+            return cudaErrorInvalidKernelImage;
+        }
+        // dynamic shared memory up to the opt-in limit less the static part
+        int optin = 0, stat = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        r = D.get_attr(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, f);
+        if (r == CUDA_SUCCESS) r = D.attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin - stat);
+        if (r != CUDA_SUCCESS) {
+            set_error("specialised pass kernel: shared-memory attribute rejected (CUresult %d)", (int)r);
+            return cudaErrorInvalidKernelImage;
+        }
+        g_cache[{dev, srcs[need[i]]}] = f;
+    }
+    std::vector<void *> &tab = c->jit_fn[dt][adj ? 1 : 0];
+    tab.assign(np, nullptr);
+    for (int p = 0; p < np; ++p)
+        if (!srcs[p].empty()) tab[p] = (void *)g_cache.at({dev, srcs[p]});
+    c->jit_ready[dt][adj ? 1 : 0] = true;
+    return cudaSuccess;
+}
+
+cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, cudaStream_t s, CUfunction *out) {
+    *out = nullptr;
+    if (!jit_wanted(c)) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(c->jit_mu);
+    const int di = adj ? 1 : 0;
+    if (!c->jit_ready[dt][di]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            return cudaSuccess;  // no module loads inside a capture: generic kernel
+        const cudaError_t e = prepare(c, dt, adj);
+        if (e != cudaSuccess) return e;
+    }
+    const std::vector<void *> &tab = c->jit_fn[dt][di];
+    if (pass < (int)tab.size()) *out = (CUfunction)tab[pass];
+    return cudaSuccess;
+}
+
+cudaError_t jit_launch(CUfunction f, const CUtensorMap &ma, const CUtensorMap &mb, const TilePassDev *desc,
+                       const void *mats, double *partials, int pblk, int *err, int grid, uint32_t smem,
+                       cudaStream_t s) {
+    CUtensorMap a = ma, b = mb;
+    const void *m = mats;
+    void *args[] = {&a, &b, (void *)&desc, (void *)&m, (void *)&partials, (void *)&pblk, (void *)&err};
+    const CUresult r = driver().launch(f, (unsigned)grid, 1, 1, TILE_THREADS, 1, 1, smem, (CUstream)s, args, nullptr);
+    if (r == CUDA_SUCCESS) return cudaSuccess;
+    // a launch the driver refused (nothing ran); the code names the reason
+    set_error("specialised pass kernel launch refused (CUresult %d, grid %d, %u B shared memory)", (int)r, grid, smem);
+    return cudaErrorInvalidKernelImage;
+}
+
+tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
+    *n_kernels = 0;
+    if (!nvrtc().ok) {
+        set_error("tqd_jit_check: NVRTC cannot be loaded");
+        return TQD_ERR_UNSUPPORTED;
+    }
+    c->opts.mode = TQD_PLAN_FUSED;
+    assign_grad_slots(c);
+    std::vector<TilePlanPass> passes = plan_tile_passes(c);
+    for (auto &p : passes)
+        if (!encode_tile_pass(c, p)) {
+            set_error("tqd_jit_check: a pass could not be encoded");
+            return TQD_ERR_INVALID_ARG;
+        }
+    std::vector<std::string> srcs;
+    {
+        std::unordered_map<std::string, int> seen;
+        for (auto &p : passes)
+            for (int dt = 0; dt < 2; ++dt)
+                for (int adj = 0; adj < 2; ++adj) {
+                    std::string src = generate(p.dev[dt], dt, adj != 0);
+                    if (seen.emplace(src, 1).second) srcs.push_back(std::move(src));
+                }
+    }
+    std::vector<std::string> logs(srcs.size());
+    std::vector<char> ok(srcs.size(), 0);
+    const int nt = std::max(1, std::min<int>((int)srcs.size(), (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    std::atomic<int> next(0);
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&] {
+            for (int i; (i = next.fetch_add(1)) < (int)srcs.size();)
+                ok[i] = !compile_cubin(srcs[i], arch, &logs[i]).empty();
+        });
+    for (auto &t : th) t.join();
+    for (size_t i = 0; i < srcs.size(); ++i)
+        if (!ok[i]) {
+            set_error("tqd_jit_check: kernel %zu of %zu failed to compile: %.400s", i, srcs.size(), logs[i].c_str());
+            return TQD_ERR_CUDA;
+        }
+    *n_kernels = (int)srcs.size();
+    return TQD_OK;
+}
+
+void jit_release(tqd_circuit *c) {
+    for (auto &d : c->jit_fn)
+        for (auto &v : d) v.clear();
+}
+
+}  // namespace tqd

@@ -5,6 +5,7 @@
 
 #include <vector>
 
+#include "jit.h"
 #include "launch.h"
 #include "plan.h"
 #include "tc.h"
@@ -27,6 +28,23 @@ static int plain_adjoint_blocks(int n) {
     return stream_grid(((uint64_t)1 << n) / 4, 256);
 }
 
+std::vector<std::vector<int>> assign_grad_slots(tqd_circuit *c) {
+    // gradient slots: one per parametric gate that reads the parameter vector
+    const int ng = (int)c->gates.size();
+    c->grad_slot.assign(ng, -1);
+    c->n_slots = 0;
+    std::vector<std::vector<int>> by_param(c->n_params);
+    for (int g = 0; g < ng; ++g) {
+        const GateH &h = c->gates[g];
+        if (h.param >= 0 && gate_parametric(h.kind)) {
+            c->grad_slot[g] = c->n_slots;
+            by_param[h.param].push_back(c->n_slots);
+            ++c->n_slots;
+        }
+    }
+    return by_param;
+}
+
 tqd_status build_circuit(tqd_circuit *c) {
     const int ng = (int)c->gates.size();
     int dev = 0;
@@ -44,18 +62,7 @@ tqd_status build_circuit(tqd_circuit *c) {
     c->d_tile_desc = nullptr;
     c->fused = false;
 
-    // gradient slots: one per parametric gate that reads the parameter vector
-    c->grad_slot.assign(ng, -1);
-    c->n_slots = 0;
-    std::vector<std::vector<int>> by_param(c->n_params);
-    for (int g = 0; g < ng; ++g) {
-        const GateH &h = c->gates[g];
-        if (h.param >= 0 && gate_parametric(h.kind)) {
-            c->grad_slot[g] = c->n_slots;
-            by_param[h.param].push_back(c->n_slots);
-            ++c->n_slots;
-        }
-    }
+    std::vector<std::vector<int>> by_param = assign_grad_slots(c);
     std::vector<int> ptr(c->n_params + 1, 0), slots;
     for (int p = 0; p < c->n_params; ++p) {
         ptr[p + 1] = ptr[p] + (int)by_param[p].size();
@@ -154,6 +161,7 @@ tqd_status build_circuit(tqd_circuit *c) {
 }
 
 void release_circuit(tqd_circuit *c) {
+    jit_release(c);
     cudaFree(c->d_gates);
     cudaFree(c->d_table);
     cudaFree(c->d_mats64);

@@ -7,6 +7,10 @@
 
 namespace tqd {
 
+// Gradient slot of every parametric gate that reads the parameter vector
+// (c->grad_slot, c->n_slots); returns the slots of each parameter.
+std::vector<std::vector<int>> assign_grad_slots(tqd_circuit *c);
+
 // Validated circuit -> device buffers and launch plan.
 tqd_status build_circuit(tqd_circuit *c);
 void release_circuit(tqd_circuit *c);

@@ -1,0 +1,888 @@
+// tile_dev.cuh -- device code of the fused tile pass (forward and reverse
+// sweep), shared by the generic pass kernel and by the pass-specialised
+// kernels that are compiled at run time (the same text is handed to NVRTC).
+//
+// One persistent block per tile slot: TMA (cp.async.bulk.tensor, 128-byte
+// swizzle) brings the 2^12 amplitudes of a tile into shared memory; every
+// stage then loads each thread's 16 amplitudes into registers in the stage's
+// layout, applies the stage's gates there (Algorithm 1's contraction M x_Q X,
+// with Q mapped onto register bits), and writes them back; a TMA store
+// returns the tile to HBM.  The reverse sweep (Sec. 4.4: recompute the input
+// of every gate as x = U^dagger y instead of storing it) does the same over
+// psi and lambda, walking stages and gates backwards; before un-applying a
+// parametric gate it reduces that gate's angle derivative
+//   dE/dt = 2 Re <lambda| dG/dt |psi_before>
+// (Im<lambda|P|psi> for R_P(t) = exp(-i t P/2), -2 Im<lambda|Pi|psi> for the
+// phase gates) over the tile.
+//
+// Every wait is bounded: a TMA load that does not complete sets the error
+// word and the block returns.
+#pragma once
+
+#include "tile_desc.h"  // first: it supplies the fixed-width integer types under NVRTC
+#include "common.cuh"
+
+namespace tqd {
+
+template <typename V> using RT = typename Real<V>::T;
+constexpr int NR = 1 << TILE_R;
+
+#ifdef __CUDACC_RTC__
+// the tensor map as a kernel parameter (CUtensorMap's size and alignment)
+struct alignas(64) TmaDesc {
+    unsigned long long w[16];
+};
+#endif
+
+template <typename A, typename B> struct same_type { static constexpr bool value = false; };
+template <typename A> struct same_type<A, A> { static constexpr bool value = true; };
+template <int P> struct IC { static constexpr int value = P; };
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sptr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(sptr(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load(int rank, const void *map, uint32_t dst, uint64_t *bar, const int *c) {
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    const uint32_t b = sptr(bar);
+    switch (rank) {
+    case 2:
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                     ::"r"(dst), "l"(m), "r"(c[0]), "r"(c[1]), "r"(b) : "memory");
+        break;
+    case 3:
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(dst), "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(b) : "memory");
+        break;
+    case 4:
+        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                     ::"r"(dst), "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(b) : "memory");
+        break;
+    default:
+        asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                     ::"r"(dst), "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(b) : "memory");
+        break;
+    }
+}
+
+__device__ __forceinline__ void tma_store(int rank, const void *map, uint32_t src, const int *c) {
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    switch (rank) {
+    case 2:
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                     ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(src) : "memory");
+        break;
+    case 3:
+        asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                     ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(src) : "memory");
+        break;
+    case 4:
+        asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+                     ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(src) : "memory");
+        break;
+    default:
+        asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];"
+                     ::"l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(src) : "memory");
+        break;
+    }
+}
+
+// Packed pairs of float (Blackwell's f32x2 pipe): one instruction does the
+// real and imaginary parts of a complex64 amplitude.
+__device__ __forceinline__ uint64_t f2_pack(float2 v) {
+    uint64_t u;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(v.x), "f"(v.y));
+    return u;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t u) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(u));
+    return v;
+}
+// a * b + c, lane by lane
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+    return f2_unpack(d);
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(d);
+}
+
+// 128-byte swizzle of the TMA box, in amplitude units: the 16-byte chunk index
+// inside a 128-byte row is XORed with the row index modulo 8.
+template <typename V> __device__ __forceinline__ uint32_t swz(uint32_t l) {
+    if constexpr (sizeof(V) == 8) return l ^ (((l >> 4) & 7u) << 1);
+    else return l ^ ((l >> 3) & 7u);
+}
+
+// ----------------------------------------------------- register operations
+// Runtime position -> compile-time position (the generic kernel's dispatch).
+template <typename F> __device__ __forceinline__ void with_pos(int p, F &&f) {
+    switch (p) {
+    case 0: f(IC<0>{}); break;
+    case 1: f(IC<1>{}); break;
+    case 2: f(IC<2>{}); break;
+    default: f(IC<3>{}); break;
+    }
+}
+template <typename F> __device__ __forceinline__ void with_pos2(int p, int q, F &&f) {
+    with_pos(p, [&](auto P_) { with_pos(q, [&](auto Q_) { f(P_, Q_); }); });
+}
+
+template <int P, typename V> __device__ __forceinline__ void rg1(V (&a)[NR], const M2<V> &m) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+        if (!(j & (1 << P))) mv2(m, a[j], a[j | (1 << P)]);
+}
+template <int P, typename V> __device__ __forceinline__ void rd1(V (&a)[NR], V d0, V d1) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) a[j] = cmul(a[j], (j & (1 << P)) ? d1 : d0);
+}
+template <int P, typename V> __device__ __forceinline__ void rph(V (&a)[NR], V ph) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+        if (j & (1 << P)) a[j] = cmul(a[j], ph);
+}
+template <int T, typename V> __device__ __forceinline__ void rx(V (&a)[NR]) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+        if (!(j & (1 << T))) {
+            V t = a[j];
+            a[j] = a[j | (1 << T)];
+            a[j | (1 << T)] = t;
+        }
+}
+template <int C, int T, typename V> __device__ __forceinline__ void rcx(V (&a)[NR]) {
+    if constexpr (C != T) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if ((j & (1 << C)) && !(j & (1 << T))) {
+                V t = a[j];
+                a[j] = a[j | (1 << T)];
+                a[j | (1 << T)] = t;
+            }
+    }
+}
+template <int P, int Q, typename V> __device__ __forceinline__ void rsw(V (&a)[NR]) {
+    if constexpr (P != Q) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if ((j & (1 << P)) && !(j & (1 << Q))) {
+                const int k = (j ^ (1 << P)) | (1 << Q);
+                V t = a[j];
+                a[j] = a[k];
+                a[k] = t;
+            }
+    }
+}
+template <int P, int Q, typename V> __device__ __forceinline__ void rd2(V (&a)[NR], V ph) {
+    if constexpr (P != Q) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if ((j & (1 << P)) && (j & (1 << Q))) a[j] = cmul(a[j], ph);
+    }
+}
+// 4x4 with wires[0] on register position P (most significant local index bit).
+template <int P, int Q, typename V> __device__ __forceinline__ void rg2(V (&a)[NR], const V (&m)[16]) {
+    if constexpr (P != Q) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if ((j & (1 << P)) || (j & (1 << Q))) continue;
+            const int i0 = j, i1 = j | (1 << Q), i2 = j | (1 << P), i3 = j | (1 << P) | (1 << Q);
+            const V v0 = a[i0], v1 = a[i1], v2 = a[i2], v3 = a[i3];
+            a[i0] = cfma(m[0], v0, cfma(m[1], v1, cfma(m[2], v2, cmul(m[3], v3))));
+            a[i1] = cfma(m[4], v0, cfma(m[5], v1, cfma(m[6], v2, cmul(m[7], v3))));
+            a[i2] = cfma(m[8], v0, cfma(m[9], v1, cfma(m[10], v2, cmul(m[11], v3))));
+            a[i3] = cfma(m[12], v0, cfma(m[13], v1, cfma(m[14], v2, cmul(m[15], v3))));
+        }
+    }
+}
+
+template <typename V> __device__ __forceinline__ V pool_c(const RT<V> *pool, int off) {
+    return mkc<V>(pool[off], pool[off + 1]);
+}
+
+template <int P, typename V> __device__ __forceinline__ void rg1r(V (&a)[NR], RT<V> m00, RT<V> m01, RT<V> m10,
+                                                                 RT<V> m11) {
+    if constexpr (same_type<V, float2>::value) {
+        // same roundings as the scalar form: m01 * x1 rounded, then fused with m00 * x0
+        const float2 M00 = make_float2(m00, m00), M01 = make_float2(m01, m01);
+        const float2 M10 = make_float2(m10, m10), M11 = make_float2(m11, m11);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j & (1 << P)) continue;
+            const float2 x0 = a[j], x1 = a[j | (1 << P)];
+            a[j] = f2_fma(M00, x0, f2_mul(M01, x1));
+            a[j | (1 << P)] = f2_fma(M10, x0, f2_mul(M11, x1));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j & (1 << P)) continue;
+            const V x0 = a[j], x1 = a[j | (1 << P)];
+            a[j] = mkc<V>(fma(m00, x0.x, m01 * x1.x), fma(m00, x0.y, m01 * x1.y));
+            a[j | (1 << P)] = mkc<V>(fma(m10, x0.x, m11 * x1.x), fma(m10, x0.y, m11 * x1.y));
+        }
+    }
+}
+
+
+// --------------------------------------------------------------- the ops
+// One op with its positions fixed at compile time, applied forward or (DAG)
+// inverted, to a and, when TWO, to b as well (the reverse sweep carries psi
+// and lambda).  m points at the op's scalars in the pool; `bit` is the value
+// of the thread-index bit an op position names.
+template <typename V, bool DAG, bool TWO, int P>
+__device__ __forceinline__ void op_g1(V (&a)[NR], V (&b)[NR], const RT<V> *m) {
+    M2<V> M;
+    M.a = pool_c<V>(m, 0);
+    M.b = pool_c<V>(m, 2);
+    M.c = pool_c<V>(m, 4);
+    M.d = pool_c<V>(m, 6);
+    if (DAG) M = dagger2(M);
+    rg1<P>(a, M);
+    if (TWO) rg1<P>(b, M);
+}
+template <typename V, bool DAG, bool TWO, int P>
+__device__ __forceinline__ void op_g1r(V (&a)[NR], V (&b)[NR], const RT<V> *m) {
+    RT<V> m00 = m[0], m01 = m[2], m10 = m[4], m11 = m[6];
+    if (DAG) {
+        const RT<V> t = m01;
+        m01 = m10;
+        m10 = t;
+    }
+    rg1r<P>(a, m00, m01, m10, m11);
+    if (TWO) rg1r<P>(b, m00, m01, m10, m11);
+}
+template <typename V, bool DAG, bool TWO, int P>
+__device__ __forceinline__ void op_d1r(V (&a)[NR], V (&b)[NR], const RT<V> *m) {
+    V d0 = pool_c<V>(m, 0), d1 = pool_c<V>(m, 6);
+    if (DAG) {
+        d0 = conjv(d0);
+        d1 = conjv(d1);
+    }
+    rd1<P>(a, d0, d1);
+    if (TWO) rd1<P>(b, d0, d1);
+}
+template <typename V, bool DAG, bool TWO>
+__device__ __forceinline__ void op_d1t(V (&a)[NR], V (&b)[NR], const RT<V> *m, uint32_t bit) {
+    V d = pool_c<V>(m, bit ? 6 : 0);
+    if (DAG) d = conjv(d);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        a[j] = cmul(a[j], d);
+        if (TWO) b[j] = cmul(b[j], d);
+    }
+}
+template <bool TWO, int C, int T, typename V> __device__ __forceinline__ void op_cxr(V (&a)[NR], V (&b)[NR]) {
+    rcx<C, T>(a);
+    if (TWO) rcx<C, T>(b);
+}
+template <bool TWO, int T, typename V> __device__ __forceinline__ void op_cxt(V (&a)[NR], V (&b)[NR], uint32_t bit) {
+    if (bit) {
+        rx<T>(a);
+        if (TWO) rx<T>(b);
+    }
+}
+template <bool TWO, int P, int Q, typename V> __device__ __forceinline__ void op_sw(V (&a)[NR], V (&b)[NR]) {
+    rsw<P, Q>(a);
+    if (TWO) rsw<P, Q>(b);
+}
+template <typename V, bool DAG, bool TWO, int P, int Q>
+__device__ __forceinline__ void op_g2(V (&a)[NR], V (&b)[NR], const RT<V> *m) {
+    V M[16];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            M[r * 4 + c] = DAG ? conjv(pool_c<V>(m, 2 * (c * 4 + r))) : pool_c<V>(m, 2 * (r * 4 + c));
+    rg2<P, Q>(a, M);
+    if (TWO) rg2<P, Q>(b, M);
+}
+// phase on |11> of two register positions
+template <typename V, bool DAG, bool TWO, int P, int Q>
+__device__ __forceinline__ void op_d2rr(V (&a)[NR], V (&b)[NR], const RT<V> *m) {
+    V ph = pool_c<V>(m, 0);
+    if (DAG) ph = conjv(ph);
+    rd2<P, Q>(a, ph);
+    if (TWO) rd2<P, Q>(b, ph);
+}
+// one position is a thread bit (value `bit`), the other register position Q
+template <typename V, bool DAG, bool TWO, int Q>
+__device__ __forceinline__ void op_d2tr(V (&a)[NR], V (&b)[NR], const RT<V> *m, uint32_t bit) {
+    if (bit) {
+        V ph = pool_c<V>(m, 0);
+        if (DAG) ph = conjv(ph);
+        rph<Q>(a, ph);
+        if (TWO) rph<Q>(b, ph);
+    }
+}
+// both positions are thread bits; `bit` = both set
+template <typename V, bool DAG, bool TWO>
+__device__ __forceinline__ void op_d2tt(V (&a)[NR], V (&b)[NR], const RT<V> *m, uint32_t bit) {
+    if (bit) {
+        V ph = pool_c<V>(m, 0);
+        if (DAG) ph = conjv(ph);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            a[j] = cmul(a[j], ph);
+            if (TWO) b[j] = cmul(b[j], ph);
+        }
+    }
+}
+// Diagonal run: entry j of the run's phase table t (its gates on register
+// positions), times the thread's factor f (its gates on thread bits) when ANY.
+template <typename V, bool DAG, bool TWO, bool ANY>
+__device__ __forceinline__ void op_dg(V (&a)[NR], V (&b)[NR], const V *t, V f) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        V ph = t[j];
+        if (ANY) ph = cmul(ph, f);
+        if (DAG) ph = conjv(ph);
+        a[j] = cmul(a[j], ph);
+        if (TWO) b[j] = cmul(b[j], ph);
+    }
+}
+
+__device__ __forceinline__ uint32_t tbit(uint32_t tid, uint8_t pos) { return (tid >> (pos & 0x7f)) & 1u; }
+
+// Per-thread factor of a diagonal run: the product of its gates whose
+// positions are all thread bits.  *any tells whether there is one.
+template <typename V>
+__device__ __forceinline__ V dg_thread_factor(const TileOp &op, const TileSub *subs, const RT<V> *pool, uint32_t tid,
+                                              bool &any) {
+    V f = mkc<V>(1, 0);
+    any = false;
+    for (int i = op.sub0; i < op.sub0 + op.nsub; ++i) {
+        const TileSub sb = subs[i];
+        if (!(sb.a & 0x80)) continue;
+        any = true;
+        const uint32_t ba = tbit(tid, sb.a);
+        if (sb.type == TOP_D1) {
+            f = cmul(f, pool_c<V>(pool, sb.moff + (ba ? 6 : 0)));
+        } else if (ba && tbit(tid, sb.b)) {
+            f = cmul(f, pool_c<V>(pool, sb.moff));
+        }
+    }
+    return f;
+}
+
+// The generic kernel's op: positions read from the descriptor.
+template <typename V, bool DAG, bool TWO>
+__device__ __forceinline__ void apply_op(const TileOp &op, V (&a)[NR], V (&b)[NR], const RT<V> *pool, uint32_t tid,
+                                         const TileSub *subs, const V *dgt) {
+    const RT<V> *m = pool + op.moff;
+    switch (op.type) {
+    case TOP_G1R:
+        with_pos(op.a, [&](auto P_) { op_g1r<V, DAG, TWO, decltype(P_)::value>(a, b, m); });
+        break;
+    case TOP_DG: {
+        bool any;
+        const V f = dg_thread_factor<V>(op, subs, pool, tid, any);
+        if (any) op_dg<V, DAG, TWO, true>(a, b, dgt + op.moff * NR, f);
+        else op_dg<V, DAG, TWO, false>(a, b, dgt + op.moff * NR, f);
+        break;
+    }
+    case TOP_G1:
+        with_pos(op.a, [&](auto P_) { op_g1<V, DAG, TWO, decltype(P_)::value>(a, b, m); });
+        break;
+    case TOP_D1:
+        if (op.a & 0x80) op_d1t<V, DAG, TWO>(a, b, m, tbit(tid, op.a));
+        else with_pos(op.a, [&](auto P_) { op_d1r<V, DAG, TWO, decltype(P_)::value>(a, b, m); });
+        break;
+    case TOP_CX:
+        if (op.a & 0x80)
+            with_pos(op.b, [&](auto T_) { op_cxt<TWO, decltype(T_)::value>(a, b, tbit(tid, op.a)); });
+        else
+            with_pos2(op.a, op.b, [&](auto C_, auto T_) {
+                op_cxr<TWO, decltype(C_)::value, decltype(T_)::value>(a, b);
+            });
+        break;
+    case TOP_SW:
+        with_pos2(op.a, op.b, [&](auto P_, auto Q_) { op_sw<TWO, decltype(P_)::value, decltype(Q_)::value>(a, b); });
+        break;
+    case TOP_G2:
+        with_pos2(op.a, op.b, [&](auto P_, auto Q_) {
+            op_g2<V, DAG, TWO, decltype(P_)::value, decltype(Q_)::value>(a, b, m);
+        });
+        break;
+    case TOP_D2: {
+        const bool ta = op.a & 0x80, tb = op.b & 0x80;
+        if (ta && tb) op_d2tt<V, DAG, TWO>(a, b, m, tbit(tid, op.a) & tbit(tid, op.b));
+        else if (ta) with_pos(op.b, [&](auto Q_) { op_d2tr<V, DAG, TWO, decltype(Q_)::value>(a, b, m, tbit(tid, op.a)); });
+        else if (tb) with_pos(op.a, [&](auto Q_) { op_d2tr<V, DAG, TWO, decltype(Q_)::value>(a, b, m, tbit(tid, op.b)); });
+        else with_pos2(op.a, op.b, [&](auto P_, auto Q_) {
+            op_d2rr<V, DAG, TWO, decltype(P_)::value, decltype(Q_)::value>(a, b, m);
+        });
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// Angle derivative of one parametric op from the states after it (a = psi,
+// b = lambda): this thread's share.
+template <int P, typename V>
+__device__ __forceinline__ RT<V> grad_g1(int gen, const V (&a)[NR], const V (&b)[NR]) {
+    if constexpr (same_type<V, float2>::value) {
+        if (gen != GEN_X) {
+            // Re(conj(l1) p0) - Re(conj(l0) p1), both dot products lane by lane
+            float2 sp = make_float2(0.f, 0.f), sm = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                if (j & (1 << P)) continue;
+                sp = f2_fma(b[j | (1 << P)], a[j], sp);
+                sm = f2_fma(b[j], a[j | (1 << P)], sm);
+            }
+            return (sp.x + sp.y) - (sm.x + sm.y);
+        }
+    }
+    RT<V> s = 0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        if (j & (1 << P)) continue;
+        const V p0 = a[j], p1 = a[j | (1 << P)], l0 = b[j], l1 = b[j | (1 << P)];
+        if (gen == GEN_X) s += im_cdot(l0, p1) + im_cdot(l1, p0);
+        else s += re_cdot(l1, p0) - re_cdot(l0, p1);  // GEN_Y
+    }
+    return s;
+}
+
+// Share of one diagonal gate's derivative given w_j = Im(conj(lambda_j) psi_j)
+// (unchanged by diagonal gates, so one w serves a whole run).
+template <typename V>
+__device__ __forceinline__ RT<V> grad_diag(uint8_t type, uint8_t pa, uint8_t pb, uint8_t gen, const RT<V> (&w)[NR],
+                                           uint32_t tid) {
+    using T = RT<V>;
+    T s = 0;
+    auto bit_of = [&](uint8_t pos, int j) -> int {
+        return (pos & 0x80) ? (int)((tid >> (pos & 0x7f)) & 1u) : ((j >> pos) & 1);
+    };
+    if (type == TOP_D1) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const int bit = bit_of(pa, j);
+            if (gen == GEN_Z) s += bit ? -w[j] : w[j];
+            else if (bit) s += w[j];  // GEN_P1
+        }
+        return gen == GEN_P1 ? T(-2) * s : s;
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+        if (bit_of(pa, j) && bit_of(pb, j)) s += w[j];
+    return T(-2) * s;
+}
+
+// Share of a diagonal op's derivative (D1 or D2 outside a run).
+template <typename V>
+__device__ __forceinline__ RT<V> grad_diag_op(uint8_t type, uint8_t pa, uint8_t pb, uint8_t gen, const V (&a)[NR],
+                                              const V (&b)[NR], uint32_t tid) {
+    RT<V> w[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);
+    return grad_diag<V>(type, pa, pb, gen, w, tid);
+}
+
+template <typename V>
+__device__ __forceinline__ RT<V> grad_op(const TileOp &op, const V (&a)[NR], const V (&b)[NR], uint32_t tid) {
+    RT<V> s = 0;
+    if (op.type == TOP_G1 || op.type == TOP_G1R) {
+        with_pos(op.a, [&](auto P_) { s = grad_g1<decltype(P_)::value>(op.gen, a, b); });
+        return s;
+    }
+    return grad_diag_op<V>(op.type, op.a, op.b, op.gen, a, b, tid);
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Matrix scalars copied into the pool for an op: (source offset, length).
+__device__ __forceinline__ void op_pool_span(uint8_t type, int &src, int &len) {
+    switch (type) {
+    case TOP_G1: case TOP_G1R: case TOP_D1: src = 0; len = 8; break;
+    case TOP_G2: src = 0; len = 32; break;
+    case TOP_D2: src = 30; len = 2; break;
+    default: src = 0; len = 0; break;
+    }
+}
+
+struct TileSmem {
+    uint32_t tiles, pool, gacc, dgt, tbt, stages, ops, subs, total;
+};
+
+// Shared-memory layout of a block: NB tile buffers, each holding psi's tile
+// (and lambda's in the reverse sweep), then the pass descriptor's parts.
+template <typename V, bool ADJ, int NB>
+__host__ __device__ inline TileSmem tile_smem(const TileHead &h) {
+    const int pool_len = h.pool_len, n_grad = h.n_grad, n_dg = h.n_dg, n_stages = h.n_stages;
+    TileSmem s;
+    s.tiles = (uint32_t)NB * (ADJ ? 2u : 1u) * (1u << TILE_K) * (uint32_t)sizeof(V);
+    s.pool = (uint32_t)((pool_len * sizeof(RT<V>) + 15) & ~15u);
+    s.gacc = ADJ ? (uint32_t)(n_grad * TILE_THREADS * sizeof(RT<V>)) : 0u;
+    s.gacc = (s.gacc + 15) & ~15u;
+    s.dgt = (uint32_t)(n_dg * NR * sizeof(V));
+    s.tbt = (uint32_t)((n_stages * TILE_TB * sizeof(uint16_t) + 15) & ~15u);
+    s.stages = (uint32_t)(n_stages * sizeof(TileStage));
+    s.ops = (uint32_t)((h.n_ops * sizeof(TileOp) + 15) & ~15u);
+    s.subs = (uint32_t)((h.n_subs * sizeof(TileSub) + 15) & ~15u);
+    s.total = 1024 + s.tiles + s.pool + s.gacc + s.dgt + s.tbt + s.stages + s.ops + s.subs + 16;
+    return s;
+}
+
+// Blocks per SM the register budget is sized for: what the shared memory of
+// the common passes allows.
+template <typename V, bool ADJ, int NB> __host__ __device__ constexpr int tile_min_blocks() {
+    return sizeof(V) == 8 ? (NB == 1 ? (ADJ ? 2 : 3) : (ADJ ? 1 : 2)) : 1;
+}
+
+// Bounds checks of the shared-memory indices, compiled in with TQD_CHECKED:
+// a bad index is recorded in the error word (code 2) and the access skipped.
+#ifdef TQD_CHECKED
+#define TQD_IDX_OK(idx, lim) ((idx) < (lim) ? true : (atomicCAS(err, 0, 2), false))
+#else
+#define TQD_IDX_OK(idx, lim) true
+#endif
+
+// Copy `bytes` (a multiple of 4) from global to shared memory.
+__device__ __forceinline__ void copy_words(void *dst, const void *src, uint32_t bytes) {
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = s[i];
+}
+
+// What a stage runner sees of the current tile and the pass.
+template <typename V> struct TileCtx {
+    V *tile_a;               // psi's tile (2^K amplitudes, swizzled)
+    V *tile_b;               // lambda's tile (reverse sweep)
+    const RT<V> *pool;       // matrix scalars of the pass's ops
+    RT<V> *gacc;             // [gradient op][thread] partial derivatives
+    const V *dgt;            // [diagonal run][16] phase tables
+    const uint16_t *tbt;     // [stage][TILE_TB] lane / warp address tables
+    const TileStage *stages;
+    const TileOp *ops;
+    const TileSub *subs;
+    int n_stages;
+    uint32_t tid;
+    int lane, warp;
+    int *err;
+};
+
+// Register j's tile index in a stage: lane and warp table entries XOR the
+// register offset.  Forward loads through F and stores through G; the
+// reverse sweep the other way.
+template <bool ADJ>
+__device__ __forceinline__ uint32_t stage_base_ld(const uint16_t *tl, int lane, int warp) {
+    constexpr int NW = TILE_THREADS / 32;
+    return ADJ ? (uint32_t)(tl[32 + NW + lane] ^ tl[64 + NW + warp]) : (uint32_t)(tl[lane] ^ tl[32 + warp]);
+}
+template <bool ADJ>
+__device__ __forceinline__ uint32_t stage_base_st(const uint16_t *tl, int lane, int warp) {
+    constexpr int NW = TILE_THREADS / 32;
+    return ADJ ? (uint32_t)(tl[lane] ^ tl[32 + warp]) : (uint32_t)(tl[32 + NW + lane] ^ tl[64 + NW + warp]);
+}
+
+// Register j of a stage from / to the tile at index ad (psi, and lambda in
+// the reverse sweep).
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_ld(const TileCtx<V> &c, V (&a)[NR], V (&b)[NR], int j, uint32_t ad) {
+    int *err = c.err;
+    (void)err;
+    if (TQD_IDX_OK(ad, (uint32_t)(1 << TILE_K))) {
+        a[j] = c.tile_a[ad];
+        if (ADJ) b[j] = c.tile_b[ad];
+    }
+}
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_st(const TileCtx<V> &c, const V (&a)[NR], const V (&b)[NR], int j, uint32_t ad) {
+    int *err = c.err;
+    (void)err;
+    if (TQD_IDX_OK(ad, (uint32_t)(1 << TILE_K))) {
+        c.tile_a[ad] = a[j];
+        if (ADJ) c.tile_b[ad] = b[j];
+    }
+}
+
+// The generic stage runner: interprets the pass's stage and op lists.
+template <typename V, bool ADJ> struct InterpRunner {
+    static __device__ __forceinline__ void run(const TileCtx<V> &c) {
+        using T = RT<V>;
+        int *err = c.err;
+        for (int si = 0; si < c.n_stages; ++si) {
+            const int s = ADJ ? c.n_stages - 1 - si : si;
+            const TileStage &st = c.stages[s];
+            const uint16_t *tl = c.tbt + s * TILE_TB;
+            const uint32_t base_ld = stage_base_ld<ADJ>(tl, c.lane, c.warp);
+            const uint32_t base_st = stage_base_st<ADJ>(tl, c.lane, c.warp);
+            const uint16_t *roff_ld = ADJ ? st.st_roff : st.ld_roff;
+            const uint16_t *roff_st = ADJ ? st.ld_roff : st.st_roff;
+            V a[NR];
+            V b[NR];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const uint32_t ad = base_ld ^ roff_ld[j];
+                if (TQD_IDX_OK(ad, (uint32_t)(1 << TILE_K))) {
+                    a[j] = c.tile_a[ad];
+                    if (ADJ) b[j] = c.tile_b[ad];
+                }
+            }
+            if (!ADJ) {
+                for (int k = st.op_begin; k < st.op_end; ++k)
+                    apply_op<V, false, false>(c.ops[k], a, b, c.pool, c.tid, c.subs, c.dgt);
+            } else {
+                for (int k = (int)st.op_end - 1; k >= (int)st.op_begin; --k) {
+                    const TileOp op = c.ops[k];
+                    if (op.type == TOP_DG) {
+                        T w[NR];
+#pragma unroll
+                        for (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);
+                        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+                            const TileSub sb = c.subs[q];
+                            if (sb.gslot < 0) continue;
+                            c.gacc[sb.gslot * TILE_THREADS + c.tid] += grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, c.tid);
+                        }
+                    } else if (op.gslot >= 0) {
+                        c.gacc[op.gslot * TILE_THREADS + c.tid] += grad_op<V>(op, a, b, c.tid);
+                    }
+                    apply_op<V, true, true>(op, a, b, c.pool, c.tid, c.subs, c.dgt);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const uint32_t ad = base_st ^ roff_st[j];
+                if (TQD_IDX_OK(ad, (uint32_t)(1 << TILE_K))) {
+                    c.tile_a[ad] = a[j];
+                    if (ADJ) c.tile_b[ad] = b[j];
+                }
+            }
+            // the last stage's writes are read next by the TMA store
+            if (si == c.n_stages - 1) fence_async_smem();
+            __syncthreads();
+        }
+    }
+};
+
+// The whole pass for one block: stage the descriptor in shared memory, then
+// load, run and store this block's tiles; in the reverse sweep, write the
+// block's gradient partials.  Runner::run(ctx) applies every stage to the
+// current tile and ends each stage with __syncthreads() (the last one after
+// fence.proxy.async).
+template <typename V, bool ADJ, int NB, typename Runner>
+__device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
+                                               const RT<V> *mats, double *partials, int pblk, int *err) {
+    using T = RT<V>;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ TileHead P;
+    __shared__ int s_timeout;
+    copy_words(&P, &Pg->h, sizeof(TileHead));
+    __syncthreads();
+    const uint32_t pad = (1024u - (sptr(smem_raw) & 1023u)) & 1023u;
+    unsigned char *sm = smem_raw + pad;
+    const TileSmem L = tile_smem<V, ADJ, NB>(P);
+    V *tiles = reinterpret_cast<V *>(sm);  // [buffer][psi, lambda][2^K]
+    T *pool = reinterpret_cast<T *>(sm + L.tiles);
+    T *gacc = reinterpret_cast<T *>(sm + L.tiles + L.pool);  // [grad op][thread]
+    V *dgt = reinterpret_cast<V *>(sm + L.tiles + L.pool + L.gacc);
+    uint16_t *tbt = reinterpret_cast<uint16_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt);
+    TileStage *stages = reinterpret_cast<TileStage *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt);
+    TileOp *ops = reinterpret_cast<TileOp *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages);
+    TileSub *subs = reinterpret_cast<TileSub *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops);
+    uint64_t *bar =
+        reinterpret_cast<uint64_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops + L.subs);
+    const uint32_t tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int TBS = TILE_TB;
+    constexpr int NW = TILE_THREADS / 32;
+
+    copy_words(stages, Pg->stages, P.n_stages * sizeof(TileStage));
+    copy_words(ops, Pg->ops, P.n_ops * sizeof(TileOp));
+    copy_words(subs, Pg->subs, P.n_subs * sizeof(TileSub));
+    __syncthreads();
+
+    // matrices of every op and diagonal sub-op, per-stage lane/warp offsets
+    for (int k = 0; k < P.n_ops; ++k) {
+        const TileOp op = ops[k];
+        if (op.moff < 0 || op.type == TOP_DG) continue;
+        int src, len;
+        op_pool_span(op.type, src, len);
+        for (int i = tid; i < len; i += blockDim.x)
+            if (TQD_IDX_OK((uint32_t)(op.moff + i), (uint32_t)P.pool_len))
+                pool[op.moff + i] = mats[(size_t)Pg->op_gate[k] * MAT_STRIDE + src + i];
+    }
+    for (int k = 0; k < P.n_subs; ++k) {
+        const TileSub sb = subs[k];
+        const int src = sb.type == TOP_D1 ? 0 : 30, len = sb.type == TOP_D1 ? 8 : 2;
+        for (int i = tid; i < len; i += blockDim.x)
+            if (TQD_IDX_OK((uint32_t)(sb.moff + i), (uint32_t)P.pool_len))
+                pool[sb.moff + i] = mats[(size_t)Pg->sub_gate[k] * MAT_STRIDE + src + i];
+    }
+    for (int i = tid; i < P.n_stages * TBS; i += blockDim.x) {
+        const int st = i / TBS, e = i % TBS;
+        const TileStage &S = stages[st];
+        tbt[i] = e < 32 ? S.ld_lo[e] : e < 32 + NW ? S.ld_hi[e - 32] : e < 64 + NW ? S.st_lo[e - 32 - NW] : S.st_hi[e - 64 - NW];
+    }
+    if (ADJ) {
+        for (int i = tid; i < P.n_grad * TILE_THREADS; i += blockDim.x) gacc[i] = T(0);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NB; ++i) mbar_init(bar + i, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // phase tables of the diagonal runs: entry j = product of the run's gates
+    // whose positions are all register bits, evaluated at register index j
+    for (int i = tid; i < P.n_dg * NR; i += blockDim.x) {
+        const int d = i / NR, j = i % NR;
+        const TileOp op = ops[Pg->dg_op[d]];
+        V t = mkc<V>(1, 0);
+        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+            const TileSub sb = subs[q];
+            if (sb.a & 0x80) continue;
+            if (sb.type == TOP_D1) t = cmul(t, pool_c<V>(pool, sb.moff + (((j >> sb.a) & 1) ? 6 : 0)));
+            else if (((j >> sb.a) & 1) && ((j >> sb.b) & 1)) t = cmul(t, pool_c<V>(pool, sb.moff));
+        }
+        dgt[i] = t;
+    }
+    __syncthreads();
+
+    constexpr int TS = 1 << TILE_K;          // amplitudes per tile
+    constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
+    const uint32_t tile_bytes = TS * (uint32_t)sizeof(V);
+    const uint32_t box_bytes = tile_bytes >> P.n_extra;
+    const uint64_t n_tiles = (uint64_t)1 << P.n_tiles_log2;
+
+    // TMA coordinates of copy e of a tile: its global index origin plus the
+    // extra local bits, split into the tensor map's dimensions.
+    auto coords = [&](uint64_t tile, int e, int (&c)[TILE_MAX_DIMS]) {
+        uint64_t g = 0;
+        for (int i = 0; i < P.n_tiles_log2; ++i) g |= ((tile >> i) & 1ull) << P.out_bits[i];
+        for (int i = 0; i < P.n_extra; ++i) g |= (uint64_t)((e >> i) & 1) << P.extra_bits[i];
+#pragma unroll
+        for (int d = 0; d < TILE_MAX_DIMS; ++d)
+            c[d] = d < P.rank ? (int)((g >> P.dim_lo[d]) & ((1ull << P.dim_len[d]) - 1)) : 0;
+    };
+    auto issue_load = [&](uint64_t tile, int buf) {
+        V *dst = tiles + (size_t)buf * NSTATE * TS;
+        mbar_expect_tx(bar + buf, tile_bytes * NSTATE);
+        for (int e = 0; e < (1 << P.n_extra); ++e) {
+            int c[TILE_MAX_DIMS];
+            coords(tile, e, c);
+            tma_load(P.rank, map_psi, sptr(dst) + e * box_bytes, bar + buf, c);
+            if (ADJ) tma_load(P.rank, map_lam, sptr(dst + TS) + e * box_bytes, bar + buf, c);
+        }
+    };
+    auto issue_store = [&](uint64_t tile, int buf) {
+        V *src = tiles + (size_t)buf * NSTATE * TS;
+        for (int e = 0; e < (1 << P.n_extra); ++e) {
+            int c[TILE_MAX_DIMS];
+            coords(tile, e, c);
+            tma_store(P.rank, map_psi, sptr(src) + e * box_bytes, c);
+            if (ADJ) tma_store(P.rank, map_lam, sptr(src + TS) + e * box_bytes, c);
+        }
+        bulk_commit();
+    };
+
+    // Thread 0 waits (bounded) for buffer buf's copy; the block learns the
+    // outcome at the barrier, so every thread takes the same branch.  The
+    // other threads then acquire the completed phase themselves.
+    uint32_t parity = 0;  // bit b: phase parity of buffer b's barrier
+    auto wait_tile = [&](int buf) -> bool {
+        const uint32_t ph = (parity >> buf) & 1u;
+        if (tid == 0) {
+            int to = 0;
+            for (uint32_t it = 0; !mbar_try_wait(bar + buf, ph);)
+                if (++it > (1u << 26)) {
+                    to = 1;
+                    break;
+                }
+            s_timeout = to;
+        }
+        __syncthreads();
+        if (s_timeout) return false;
+        if (tid != 0) mbar_try_wait(bar + buf, ph);
+        parity ^= 1u << buf;
+        return true;
+    };
+
+    TileCtx<V> ctx;
+    ctx.pool = pool;
+    ctx.gacc = gacc;
+    ctx.dgt = dgt;
+    ctx.tbt = tbt;
+    ctx.stages = stages;
+    ctx.ops = ops;
+    ctx.subs = subs;
+    ctx.n_stages = P.n_stages;
+    ctx.tid = tid;
+    ctx.lane = lane;
+    ctx.warp = warp;
+    ctx.err = err;
+
+    // NB = 2: the next tile's copy is in flight while this one is computed;
+    // a buffer is refilled only after its previous store has read it.
+    if (NB == 2 && tid == 0 && blockIdx.x < n_tiles) issue_load(blockIdx.x, 0);
+    int iter = 0;
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
+        const int cur = NB == 2 ? (iter & 1) : 0;
+        if (tid == 0) {
+            const uint64_t next = NB == 2 ? tile + gridDim.x : tile;
+            if (next < n_tiles) {
+                bulk_wait_read0();
+                issue_load(next, NB == 2 ? cur ^ 1 : 0);
+            }
+        }
+        if (!wait_tile(cur)) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                bulk_wait0();
+            }
+            return;
+        }
+        ctx.tile_a = tiles + (size_t)cur * NSTATE * TS;
+        ctx.tile_b = ctx.tile_a + TS;
+        Runner::run(ctx);
+        if (tid == 0) issue_store(tile, cur);
+    }
+    if (tid == 0) bulk_wait0();
+    if (ADJ) {
+        __syncthreads();
+        // per-thread partial sums (state precision, about 16 amplitudes x
+        // the block's tiles each) are added in FP64, one warp per gradient op
+        for (int k = warp; k < P.n_grad; k += NW) {
+            double t = 0;
+            for (int i = lane; i < TILE_THREADS; i += 32) t += (double)gacc[k * TILE_THREADS + i];
+            t = warp_sum(t);
+            if (lane == 0) partials[(size_t)Pg->grad_gate_slot[k] * pblk + blockIdx.x] = t;
+        }
+    }
+}
+
+}  // namespace tqd

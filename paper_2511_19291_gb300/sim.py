@@ -113,41 +113,61 @@ class State:
             self._h = None
 
 
+def _gate_array(circuit: W.Circuit):
+    """The gate list as tqd_gate records, and the matrix table (re, im pairs)."""
+    gates = circuit.gates
+    arr = (_lib.Gate * max(1, len(gates)))()
+    table = []
+    for i, g in enumerate(gates):
+        a = arr[i]
+        a.kind = _lib.KIND_CODES[g.kind]
+        a.nwires = len(g.wires)
+        for j, w in enumerate(g.wires):
+            a.wires[j] = int(w)
+        a.param_idx = int(g.param)
+        a.fixed = float(g.angle)
+        a.mat_idx = -1
+        if g.kind in ("UNITARY1", "UNITARY2"):
+            a.mat_idx = len(table)
+            table.extend(np.asarray(g.matrix, dtype=np.complex128).reshape(-1).tolist())
+    mats = np.array([[v.real, v.imag] for v in table], dtype=np.float64).reshape(-1)
+    return arr, mats, len(table)
+
+
+def jit_check(circuit: W.Circuit, arch: int = 103) -> int:
+    """Compiles the circuit's pass-specialised kernels for compute capability
+    `arch` without a GPU (tqd_jit_check); returns how many distinct kernels."""
+    arr, mats, n_entries = _gate_array(circuit)
+    n = C.c_int32()
+    _lib.check(_L().tqd_jit_check(
+        circuit.n_qubits, C.cast(arr, C.c_void_p), len(circuit.gates), circuit.n_params,
+        mats.ctypes.data_as(C.c_void_p) if n_entries else None, n_entries, arch, C.byref(n)))
+    return n.value
+
+
 class Circuit:
     """A gate list planned by the library (plain gate-by-gate or fused passes)."""
 
     def __init__(self, circuit: W.Circuit, mode: str = "fused", tile_qubits: int = 0, low_qubits: int = 0,
-                 device=None):
+                 device=None, buffers: int = 0, jit: int = 0):
         self.spec = circuit
         self.n = circuit.n_qubits
         self.n_params = circuit.n_params
         self.mode = mode
         gates = circuit.gates
-        arr = (_lib.Gate * max(1, len(gates)))()
-        table = []
-        for i, g in enumerate(gates):
-            a = arr[i]
-            a.kind = _lib.KIND_CODES[g.kind]
-            a.nwires = len(g.wires)
-            for j, w in enumerate(g.wires):
-                a.wires[j] = int(w)
-            a.param_idx = int(g.param)
-            a.fixed = float(g.angle)
-            a.mat_idx = -1
-            if g.kind in ("UNITARY1", "UNITARY2"):
-                a.mat_idx = len(table)
-                table.extend(np.asarray(g.matrix, dtype=np.complex128).reshape(-1).tolist())
-        mats = np.array([[v.real, v.imag] for v in table], dtype=np.float64).reshape(-1)
+        arr, mats, n_entries = _gate_array(circuit)
         opts = _lib.PlanOpts()
         opts.mode = {"plain": _lib.PLAN_PLAIN, "fused": _lib.PLAN_FUSED, "tc": _lib.PLAN_TC}[mode]
         opts.tile_qubits = tile_qubits
         opts.low_qubits = low_qubits
+        opts.buffers = buffers
+        opts.jit = jit
         h = C.c_void_p()
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(dev):
             _lib.check(_L().tqd_circuit_create(
                 self.n, C.cast(arr, C.c_void_p), len(gates), self.n_params,
-                mats.ctypes.data_as(C.c_void_p) if len(table) else None, len(table),
+                mats.ctypes.data_as(C.c_void_p) if n_entries else None, n_entries,
                 C.byref(opts), C.byref(h)))
         self._h = h
         self._mats = mats

@@ -93,3 +93,23 @@ def test_null_handles_rejected(lib):
     assert lib.tqd_backward(None, None, None, None, None, 0, None, 1.0, None, None) == 1
     assert lib.tqd_state_free(None) == 0
     assert lib.tqd_circuit_free(None) == 0
+
+
+def test_specialised_pass_kernels_compile(lib):
+    """The pass-specialised kernels the library generates compile for sm_103a
+    (NVRTC, no GPU): the ansatz form and a random gate list over every kind,
+    both precisions and both directions."""
+    from paper_2511_19291_gb300 import sim as S
+    from paper_2511_19291_gb300 import workloads as W
+    assert S.jit_check(W.hea_ansatz(14, 2)) >= 4
+    circ, _ = W.random_circuit(W.SplitMix64(77), 13, 60, n_params=20)
+    assert S.jit_check(circ) >= 4
+
+
+def test_specialised_check_rejects_small_and_bad_arch(lib):
+    from paper_2511_19291_gb300 import sim as S
+    from paper_2511_19291_gb300 import workloads as W
+    with pytest.raises(_lib.TqdError, match="INVALID_ARG"):
+        S.jit_check(W.hea_ansatz(8, 1))
+    with pytest.raises(_lib.TqdError, match="INVALID_ARG"):
+        S.jit_check(W.hea_ansatz(14, 1), arch=7)

@@ -72,9 +72,9 @@ def test_apply_observable_parity(dtype, n, seed):
     np.testing.assert_allclose(to_numpy(outw), refw, atol=AMP_TOL[dtype] * 60, rtol=0)
 
 
-def gpu_grad(circ, params, terms, mode, dtype, weights=None, scale=1.0):
+def gpu_grad(circ, params, terms, mode, dtype, weights=None, scale=1.0, **kw):
     S = sim()
-    st, c, p = gpu_state(circ, params, mode, dtype)
+    st, c, p = gpu_state(circ, params, mode, dtype, **kw)
     lam = S.State(circ.n_qubits, DTYPES[dtype])
     g = torch.zeros(circ.n_params, dtype=torch.float64, device="cuda")
     S.backward(st, lam, c, p, terms, g, weights=weights, scale=scale)
@@ -98,6 +98,53 @@ def test_gradient_parity_random(mode, dtype, n, ng, seed):
     e0 = np.zeros(1 << n, dtype=complex)
     e0[0] = 1
     np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 10 * math.sqrt(ng), rtol=0)
+
+
+TILE_VARIANTS = {"generic": dict(jit=1), "generic_2buf": dict(jit=1, buffers=2), "specialised": dict(jit=2)}
+
+
+@pytest.mark.parametrize("variant", list(TILE_VARIANTS))
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,ng,seed", [(12, 80, 1), (14, 120, 2), (16, 60, 3)])
+def test_fused_tile_variants_random(variant, dtype, n, ng, seed):
+    """Fused passes through the generic kernel with one and two tile buffers
+    per block, and through the pass-specialised kernels: random gate lists
+    over every kind (several passes, ragged stage schedules), forward state
+    and gradient against the oracle."""
+    kw = TILE_VARIANTS[variant]
+    rng = W.SplitMix64(6000 + seed)
+    circ, params = W.random_circuit(rng, n, ng, n_params=max(2, ng // 3))
+    terms = W.random_pauli_terms(rng, n, 6) + W.sum_z(n)
+    st, _, _ = gpu_state(circ, params, "fused", dtype, **kw)
+    tol = AMP_TOL[dtype] * math.sqrt(ng / 100 + 1)
+    np.testing.assert_allclose(to_numpy(st), oracle.run(circ, params), atol=tol, rtol=0)
+    del st
+    ref = oracle.grad_param_shift(circ, params, terms)
+    g, st = gpu_grad(circ, params, terms, "fused", dtype, **kw)
+    ok, worst = grad_close(g, ref, G_REL[dtype], hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+    assert ok, f"worst relative error {worst}"
+    back = to_numpy(st)
+    e0 = np.zeros(1 << n, dtype=complex)
+    e0[0] = 1
+    np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 10 * math.sqrt(ng), rtol=0)
+
+
+@pytest.mark.parametrize("jit", [1, 2])
+def test_specialised_ansatz_ising_14q(jit):
+    """The ansatz workload's form at 14 qubits through the generic and the
+    pass-specialised kernels: energy and gradient against the oracle."""
+    circ = W.hea_ansatz(14, 3)
+    params = W.config_rng(3).angles(circ.n_params)
+    terms = W.ising(14)
+    ref = oracle.grad_param_shift(circ, params, terms)
+    e_ref = oracle.energy(circ, params, terms)
+    for dtype in ("c64", "c128"):
+        st, _, _ = gpu_state(circ, params, "fused", dtype, jit=jit)
+        assert abs(sim().expval(st, terms).item() - e_ref) < E_TOL[dtype]
+        del st
+        g, _ = gpu_grad(circ, params, terms, "fused", dtype, jit=jit)
+        ok, worst = grad_close(g, ref, G_REL[dtype])
+        assert ok, f"{dtype}: worst relative error {worst}"
 
 
 @pytest.mark.parametrize("mode", MODES)
