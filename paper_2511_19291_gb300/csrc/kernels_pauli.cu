@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "pauli_tile.h"
 #include "prof.h"
 
 namespace tqd {
@@ -259,29 +260,48 @@ static cudaError_t expval_t(tqd_state *st, const std::vector<PauliGroup> &groups
     const int grid = stream_grid(N / 2 > 0 ? N / 2 : 1, PT);
     const int pblk = grid;
     if (mode == 0) {
+        // groups that fit a 12-qubit tile share passes; the rest one pass per group
+        std::vector<int> left;
+        const std::vector<PauliTileDesc> tiles = plan_pauli_tiles(groups, n, &left);
+        const int tgrid = tiles.empty() ? 0 : pauli_tile_grid(n);
         size_t launches = 0;
-        for (const auto &g : groups) launches += (g.terms.size() + MAXT - 1) / MAXT;
-        if (launches == 0) {
+        for (int gi : left) launches += (groups[gi].terms.size() + MAXT - 1) / MAXT;
+        const size_t rows = tiles.size() + launches;
+        if (rows == 0) {
             k_fill<<<1, 32, 0, s>>>(dev_out, 1, 0.0);
             return cudaGetLastError();
         }
-        cudaError_t e = ensure_work(st, launches * (size_t)pblk + launches, s);
+        const int w = std::max(pblk, tgrid);
+        cudaError_t e = ensure_work(st, rows * (size_t)w + rows, s);
         if (e != cudaSuccess) return e;
-        double *parts = st->work, *sums = st->work + launches * (size_t)pblk;
+        double *parts = st->work, *sums = st->work + rows * (size_t)w;
+        if (!tiles.empty()) {
+            e = launch_pauli_tile_expval(st, tiles, parts, w, s);
+            if (e != cudaSuccess) return e;
+            ProfScope ps(PK_REDUCE, 0.0, s);
+            k_sum_rows<<<(int)tiles.size(), PT, 0, s>>>(parts, w, tgrid, sums);
+        }
+        if (launches == 0) {
+            ProfScope ps(PK_REDUCE, 0.0, s);
+            k_sum_all<<<1, 32, 0, s>>>(sums, (int)rows, dev_out);
+            return cudaGetLastError();
+        }
+        parts += tiles.size() * (size_t)w;
         size_t slot = 0;
-        for (const auto &g : groups) {
+        for (int gi : left) {
+            const PauliGroup &g = groups[gi];
             for (size_t from = 0; from < g.terms.size(); from += MAXT) {
                 TermPack tp;
                 const size_t cnt = std::min((size_t)MAXT, g.terms.size() - from);
                 fill_pack(tp, g.xmask, g.terms, from, cnt, true);
                 ProfScope ps(PK_EXPVAL, (double)N * sizeof(V), s);
-                k_expval_total<V><<<grid, PT, 0, s>>>((const V *)st->amps, n, tp, parts + slot * pblk);
+                k_expval_total<V><<<grid, PT, 0, s>>>((const V *)st->amps, n, tp, parts + slot * w);
                 ++slot;
             }
         }
         ProfScope ps(PK_REDUCE, 0.0, s);
-        k_sum_rows<<<(int)launches, PT, 0, s>>>(parts, pblk, grid, sums);
-        k_sum_all<<<1, 32, 0, s>>>(sums, (int)launches, dev_out);
+        k_sum_rows<<<(int)launches, PT, 0, s>>>(parts, w, grid, sums + tiles.size());
+        k_sum_all<<<1, 32, 0, s>>>(sums, (int)rows, dev_out);
         return cudaGetLastError();
     }
     if (n_terms == 0) return cudaSuccess;
@@ -315,7 +335,15 @@ static cudaError_t apply_obs_t(const tqd_state *psi, const std::vector<PauliGrou
     const uint64_t N = (uint64_t)1 << n;
     const int grid = stream_grid(N / 2 > 0 ? N / 2 : 1, PT);
     int accumulate = 0;
-    for (const auto &g : groups) {
+    std::vector<int> left;
+    const std::vector<PauliTileDesc> tiles = plan_pauli_tiles(groups, n, &left);
+    if (!tiles.empty()) {
+        cudaError_t e = launch_pauli_tile_apply(psi, tiles, weights, scale, out, false, s);
+        if (e != cudaSuccess) return e;
+        accumulate = 1;
+    }
+    for (int gi : left) {
+        const PauliGroup &g = groups[gi];
         for (size_t from = 0; from < g.terms.size(); from += MAXT) {
             TermPack tp;
             fill_pack(tp, g.xmask, g.terms, from, std::min((size_t)MAXT, g.terms.size() - from), true);
