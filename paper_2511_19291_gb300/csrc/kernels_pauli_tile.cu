@@ -147,9 +147,6 @@ __global__ void __launch_bounds__(PTHR) k_pauli_tile_expval(const V *__restrict_
             tile[l] = psi[global_of(S.hoff, origin, l)];
         }
         __syncthreads();
-        V a[PPER];  // this thread's amplitudes, reused by every group
-#pragma unroll
-        for (int r = 0; r < PPER; ++r) a[r] = tile[r * PTHR + tid];
         for (int g = 0; g < S.P.n_groups; ++g) {
             const uint32_t xl = S.P.gx[g];
             V D[PPER];
@@ -157,12 +154,13 @@ __global__ void __launch_bounds__(PTHR) k_pauli_tile_expval(const V *__restrict_
             RT<V> part = 0;
             if (xl == 0) {
 #pragma unroll
-                for (int r = 0; r < PPER; ++r) part = fma(norm2(a[r]), D[r].x, part);
+                for (int r = 0; r < PPER; ++r) part = fma(norm2(tile[r * PTHR + tid]), D[r].x, part);
             } else {
 #pragma unroll
                 for (int r = 0; r < PPER; ++r) {
-                    const V ap = tile[(r * PTHR + tid) ^ xl];
-                    const RT<V> ur = re_cdot(ap, a[r]), ui = im_cdot(ap, a[r]);  // conj(psi_{b^x}) psi_b
+                    const uint32_t l = r * PTHR + tid;
+                    const V a = tile[l], ap = tile[l ^ xl];
+                    const RT<V> ur = re_cdot(ap, a), ui = im_cdot(ap, a);  // conj(psi_{b^x}) psi_b
                     part = fma(ur, D[r].x, fma(-ui, D[r].y, part));
                 }
             }
