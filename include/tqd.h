@@ -96,16 +96,23 @@ typedef struct {
     uint32_t mode;        /* tqd_plan_mode */
     uint32_t tile_qubits; /* fused tiles hold 2^tile_qubits amplitudes; 0 = default */
     uint32_t low_qubits;  /* contiguous low qubits in every mixed tile; 0 = default */
-    uint32_t buffers;     /* tile buffers per block in the fused passes: 1 = load, compute and
-                             store one tile at a time; 2 = load the next tile while the current
-                             one is computed (needs twice the shared memory); 0 = default */
+    uint32_t buffers;     /* tile buffers in the fused passes: 1 = each block loads, computes and
+                             stores one tile at a time; 2 = each block loads its next tile while
+                             the current one is computed (twice the shared memory); 3 = ring:
+                             one block per SM whose groups of 256 threads share a ring of tile
+                             buffers, each refilled by TMA as soon as its tile is stored
+                             (complex64 only; complex128 uses 1); 0 = default: the ring for
+                             complex64 states of 21 qubits and more, else 1 */
     uint32_t jit;         /* fused passes run 1 = the generic pass kernel, which reads positions,
                              addresses and matrices from the pass descriptor; 2 = kernels
                              specialised per pass (straight-line code with those fixed, compiled
                              at run time with NVRTC on first use; TQD_ERR_UNSUPPORTED when NVRTC
                              cannot be loaded); 0 = default: specialised from 22 qubits up, when
                              NVRTC can be loaded */
-    uint32_t reserved[3]; /* must be zero */
+    uint32_t max_blocks;  /* cap on the blocks of a fused pass launch (0 = no cap: one per SM for
+                             the ring, the occupancy limit otherwise); a smaller grid gives each
+                             block more tiles */
+    uint32_t reserved[2]; /* must be zero */
 } tqd_plan_opts;
 
 typedef struct tqd_state tqd_state;

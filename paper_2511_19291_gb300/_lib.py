@@ -73,7 +73,8 @@ class BatchOpts(C.Structure):
 
 class PlanOpts(C.Structure):
     _fields_ = [("mode", C.c_uint32), ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32),
-                ("buffers", C.c_uint32), ("jit", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("buffers", C.c_uint32), ("jit", C.c_uint32), ("max_blocks", C.c_uint32),
+                ("reserved", C.c_uint32 * 2)]
 
 
 _lock = threading.Lock()

@@ -13,6 +13,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <thread>
 #include <unordered_map>
@@ -183,7 +184,7 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
             const TileSub &sb = D.subs[q];
             if (sb.gslot < 0) continue;
-            put(o, "c.gacc[%d * TILE_THREADS + tid] += grad_diag<TV>(%d, %d, %d, %d, w, tid);\n", sb.gslot, sb.type,
+            put(o, "gacc_add<KRING>(c.gacc, %d, tid, grad_diag<TV>(%d, %d, %d, %d, w, tid));\n", sb.gslot, sb.type,
                 sb.a, sb.b, sb.gen);
         }
         o += "}\n";
@@ -191,19 +192,19 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
     }
     if (op.gslot < 0) return;
     if (op.type == TOP_G1 || op.type == TOP_G1R)
-        put(o, "c.gacc[%d * TILE_THREADS + tid] += grad_g1<%d, TV>(%d, a, b);\n", op.gslot, op.a, op.gen);
+        put(o, "gacc_add<KRING>(c.gacc, %d, tid, grad_g1<%d, TV>(%d, a, b));\n", op.gslot, op.a, op.gen);
     else
-        put(o, "c.gacc[%d * TILE_THREADS + tid] += grad_diag_op<TV>(%d, %d, %d, %d, a, b, tid);\n", op.gslot, op.type,
-            op.a, op.b, op.gen);
+        put(o, "gacc_add<KRING>(c.gacc, %d, tid, grad_diag_op<TV>(%d, %d, %d, %d, a, b, tid));\n", op.gslot,
+            op.type, op.a, op.b, op.gen);
 }
 
-std::string generate(const TilePassDev &D, int dt, bool adj) {
+std::string generate(const TilePassDev &D, int dt, bool adj, bool ring) {
     const TileHead &h = D.h;
     std::string o;
     o.reserve(1 << 16);
     o += "#include \"tile_dev.cuh\"\nnamespace tqd {\n";
-    put(o, "typedef %s TV;\ntypedef %s TT;\nconstexpr bool KADJ = %s;\n", dt == 0 ? "float2" : "double2",
-        dt == 0 ? "float" : "double", tf(adj));
+    put(o, "typedef %s TV;\ntypedef %s TT;\nconstexpr bool KADJ = %s;\nconstexpr bool KRING = %s;\n",
+        dt == 0 ? "float2" : "double2", dt == 0 ? "float" : "double", tf(adj), tf(ring));
     o += "struct PassRunner {\nstatic __device__ __forceinline__ void run(const TileCtx<TV> &c) {\n"
          "int *err = c.err;\n(void)err;\nconst uint32_t tid = c.tid;\nTV a[NR];\nTV b[NR];\n";
     for (int si = 0; si < h.n_stages; ++si) {
@@ -225,19 +226,22 @@ std::string generate(const TilePassDev &D, int dt, bool adj) {
         }
         for (int j = 0; j < (1 << TILE_R); ++j) put(o, "tile_st<TV, KADJ>(c, a, b, %d, bs ^ %uu);\n", j, (unsigned)rs[j]);
         if (si == h.n_stages - 1) o += "fence_async_smem();\n";
-        o += "__syncthreads();\n}\n";
+        o += "tile_sync(c);\n}\n";
     }
     o += "}\n};\n}  // namespace tqd\n";
-    // the generic kernel's launch bounds (tile_min_blocks<V, ADJ, 1>)
+    // the generic kernels' launch bounds (tile_min_blocks<V, ADJ, 1>; ring: one block of G groups)
     const int minb = dt == 0 ? (adj ? 2 : 3) : 1;
     put(o,
         "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
         "tqd_pass(const __grid_constant__ tqd::TmaDesc mp, const __grid_constant__ tqd::TmaDesc ml,\n"
         "         const tqd::TilePassDev *__restrict__ Pg, const tqd::TT *__restrict__ mats,\n"
-        "         double *__restrict__ partials, int pblk, int *__restrict__ err) {\n"
-        "    tqd::tile_pass_body<tqd::TV, tqd::KADJ, 1, tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n"
-        "}\n",
-        TILE_THREADS, minb);
+        "         double *__restrict__ partials, int pblk, int *__restrict__ err) {\n",
+        ring ? (adj ? RingCfg<true>::G : RingCfg<false>::G) * TILE_THREADS : TILE_THREADS, ring ? 1 : minb);
+    if (ring)
+        o += "    tqd::tile_pass_ring<tqd::TV, tqd::KADJ, tqd::RingCfg<tqd::KADJ>::G, tqd::RingCfg<tqd::KADJ>::B,\n"
+             "                        tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n}\n";
+    else
+        o += "    tqd::tile_pass_body<tqd::TV, tqd::KADJ, 1, tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n}\n";
     return o;
 }
 
@@ -260,13 +264,22 @@ std::string compile_cubin(const std::string &src, int arch, std::string *log) {
     }
     char archopt[64];
     snprintf(archopt, sizeof(archopt), "--gpu-architecture=sm_%da", arch);
-    const char *opts[] = {archopt, "-std=c++17", "-DNDEBUG",
+    // TQD_JIT_VERBOSE=1: ptxas reports registers and spills into the log
+    const bool verbose = getenv("TQD_JIT_VERBOSE") && getenv("TQD_JIT_VERBOSE")[0] == '1';
+    const char *opts[] = {archopt, "-std=c++17", "-DNDEBUG", verbose ? "--ptxas-options=-v" : "-DTQD_QUIET",
 #ifdef TQD_CHECKED
                           "-DTQD_CHECKED",
 #endif
     };
     const nvrtcResult r = N.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
     std::string out;
+    if (verbose) {
+        size_t n = 0;
+        N.log_size(prog, &n);
+        std::string lg(n, '\0');
+        if (n) N.log(prog, &lg[0]);
+        fprintf(stderr, "[tqd jit] %s\n", lg.c_str());
+    }
     if (r != NVRTC_SUCCESS) {
         size_t n = 0;
         N.log_size(prog, &n);
@@ -293,11 +306,11 @@ bool jit_wanted(const tqd_circuit *c) {
     return c->n >= 22 && nvrtc().ok && driver().ok;
 }
 
-std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj) {
-    return generate(c->tile_passes[pass].dev[dt], dt, adj);
+std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring) {
+    return generate(c->tile_passes[pass].dev[dt], dt, adj, ring);
 }
 
-static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj) {
+static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring) {
     if (!nvrtc().ok || !driver().ok) {
         set_error("specialised pass kernels: NVRTC or the CUDA driver entry points are unavailable");
         return cudaErrorNotSupported;
@@ -313,7 +326,7 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj) {
         std::lock_guard<std::mutex> lk(g_cache_mu);
         for (int p = 0; p < np; ++p) {
             if (!adj && dt == 0 && c->tile_passes[p].tc >= 0) continue;  // forward runs on the tensor cores
-            srcs[p] = jit_source(c, p, dt, adj);
+            srcs[p] = jit_source(c, p, dt, adj, ring);
             if (g_cache.count({dev, srcs[p]}) || first.count(srcs[p])) continue;
             first[srcs[p]] = p;
             need.push_back(p);
@@ -367,7 +380,8 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj) {
     return cudaSuccess;
 }
 
-cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, cudaStream_t s, CUfunction *out) {
+cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, cudaStream_t s,
+                         CUfunction *out) {
     *out = nullptr;
     if (!jit_wanted(c)) return cudaSuccess;
     std::lock_guard<std::mutex> lk(c->jit_mu);
@@ -376,7 +390,7 @@ cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, cudaS
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
             return cudaSuccess;  // no module loads inside a capture: generic kernel
-        const cudaError_t e = prepare(c, dt, adj);
+        const cudaError_t e = prepare(c, dt, adj, ring);
         if (e != cudaSuccess) return e;
     }
     const std::vector<void *> &tab = c->jit_fn[dt][di];
@@ -385,12 +399,12 @@ cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, cudaS
 }
 
 cudaError_t jit_launch(CUfunction f, const CUtensorMap &ma, const CUtensorMap &mb, const TilePassDev *desc,
-                       const void *mats, double *partials, int pblk, int *err, int grid, uint32_t smem,
-                       cudaStream_t s) {
+                       const void *mats, double *partials, int pblk, int *err, int grid, int threads,
+                       uint32_t smem, cudaStream_t s) {
     CUtensorMap a = ma, b = mb;
     const void *m = mats;
     void *args[] = {&a, &b, (void *)&desc, (void *)&m, (void *)&partials, (void *)&pblk, (void *)&err};
-    const CUresult r = driver().launch(f, (unsigned)grid, 1, 1, TILE_THREADS, 1, 1, smem, (CUstream)s, args, nullptr);
+    const CUresult r = driver().launch(f, (unsigned)grid, 1, 1, (unsigned)threads, 1, 1, smem, (CUstream)s, args, nullptr);
     if (r == CUDA_SUCCESS) return cudaSuccess;
     // a launch the driver refused (nothing ran); the code names the reason
     set_error("specialised pass kernel launch refused (CUresult %d, grid %d, %u B shared memory)", (int)r, grid, smem);
@@ -416,10 +430,11 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
         std::unordered_map<std::string, int> seen;
         for (auto &p : passes)
             for (int dt = 0; dt < 2; ++dt)
-                for (int adj = 0; adj < 2; ++adj) {
-                    std::string src = generate(p.dev[dt], dt, adj != 0);
-                    if (seen.emplace(src, 1).second) srcs.push_back(std::move(src));
-                }
+                for (int adj = 0; adj < 2; ++adj)
+                    for (int ring = 0; ring < (dt == 0 ? 2 : 1); ++ring) {
+                        std::string src = generate(p.dev[dt], dt, adj != 0, ring != 0);
+                        if (seen.emplace(src, 1).second) srcs.push_back(std::move(src));
+                    }
     }
     std::vector<std::string> logs(srcs.size());
     std::vector<char> ok(srcs.size(), 0);

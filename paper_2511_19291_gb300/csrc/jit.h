@@ -23,7 +23,9 @@ namespace tqd {
 bool jit_wanted(const tqd_circuit *c);
 
 // Source text of pass `pass`'s specialised kernel (dt: 0 complex64, 1 complex128).
-std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj);
+// `ring`: the kernel runs on a ring of tile buffers (tile_pass_ring) instead of
+// one buffer per block (tile_pass_body).
+std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring);
 
 // The specialised kernel of pass `pass`, compiling every pass of (dt, adj)
 // on first use.  *out = nullptr means "run the generic kernel": the circuit
@@ -31,12 +33,13 @@ std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj);
 // mode, the pass is replaced by a tensor-core block, or s is capturing a
 // graph before the kernels exist.  Errors: NVRTC missing when the circuit
 // requires it (cudaErrorNotSupported) or a failed compile / module load.
-cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, cudaStream_t s, CUfunction *out);
+cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, cudaStream_t s,
+                         CUfunction *out);
 
 // Launches a specialised kernel with the generic kernel's arguments.
 cudaError_t jit_launch(CUfunction f, const CUtensorMap &ma, const CUtensorMap &mb, const TilePassDev *desc,
-                       const void *mats, double *partials, int pblk, int *err, int grid, uint32_t smem,
-                       cudaStream_t s);
+                       const void *mats, double *partials, int pblk, int *err, int grid, int threads,
+                       uint32_t smem, cudaStream_t s);
 
 // Host only (no GPU): plans circuit c's fused passes, generates every
 // specialised kernel (both precisions, both directions) and compiles the

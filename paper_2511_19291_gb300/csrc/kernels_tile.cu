@@ -26,6 +26,16 @@ __global__ void __launch_bounds__(TILE_THREADS, tile_min_blocks<V, ADJ, NB>())
     tile_pass_body<V, ADJ, NB, InterpRunner<V, ADJ>>(&map_psi, &map_lam, Pg, mats, partials, pblk, err);
 }
 
+// The generic pass on a ring of tile buffers (one block per SM, G groups).
+template <typename V, bool ADJ>
+__global__ void __launch_bounds__(RingCfg<ADJ>::G * TILE_THREADS, 1)
+    k_tile_ring(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam,
+                const TilePassDev *__restrict__ Pg, const RT<V> *__restrict__ mats, double *__restrict__ partials,
+                int pblk, int *__restrict__ err) {
+    tile_pass_ring<V, ADJ, RingCfg<ADJ>::G, RingCfg<ADJ>::B, InterpRunner<V, ADJ, true>>(&map_psi, &map_lam, Pg, mats,
+                                                                                          partials, pblk, err);
+}
+
 // ------------------------------------------------------------------- host
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static std::once_flag once;
@@ -97,15 +107,37 @@ static int smem_optin_limit() {
     return v;
 }
 
-// Tile buffers per block: two only when the caller asks for them and one
-// block's shared memory holds them.  One is the default: the passes are
-// bound by instruction issue, and on a GB300 the second buffer's shared
-// memory costs more resident blocks than the overlapped copy gains (26-qubit
-// ansatz: forward 2151 vs 2000 GB/s, reverse 1779 vs 1331 GB/s).
+// Tile buffers per block.  complex64 defaults to the ring (one block per SM
+// whose groups share a ring of buffers refilled as soon as a tile is stored:
+// the load latency hides behind other tiles' stages).  Otherwise one buffer:
+// load, compute and store a tile, with several blocks per SM; two only when
+// the caller asks for them and one block's shared memory holds them.
+enum { TB_ONE = 1, TB_TWO = 2, TB_RING = 3 };
+
+template <typename V, bool ADJ>
+static uint32_t max_smem_ring(const tqd_circuit *c, int dt) {
+    uint32_t m = 0;
+    for (const auto &p : c->tile_passes) {
+        const TileSmem s = tile_smem_ring<V, ADJ, RingCfg<ADJ>::B>(p.dev[dt].h);
+        if (s.total > m) m = s.total;
+    }
+    return m;
+}
+
+// Static shared memory of the ring body (descriptor head, barriers, counters).
+template <bool ADJ> static constexpr uint32_t ring_static_smem() {
+    return (uint32_t)(sizeof(TileHead) + RingCfg<ADJ>::B * (8 + 4) + RingCfg<ADJ>::G * 4 + 256);
+}
+
 template <typename V, bool ADJ>
 static int buffers_for(const tqd_circuit *c, int dt) {
-    if (c->opts.buffers != 2) return 1;
-    return (int)max_smem<V, ADJ, 2>(c, dt) <= smem_optin_limit() ? 2 : 1;
+    const uint32_t want = c->opts.buffers;
+    // the ring pays off once every block has several tiles (n >= 21: >= 1.7 per group)
+    if (sizeof(V) == 8 && (want == TB_RING || (want == 0 && c->n >= 21)) &&
+        max_smem_ring<V, ADJ>(c, dt) + ring_static_smem<ADJ>() <= (uint32_t)smem_optin_limit())
+        return TB_RING;
+    if (want != TB_TWO) return TB_ONE;
+    return (int)max_smem<V, ADJ, 2>(c, dt) <= smem_optin_limit() ? TB_TWO : TB_ONE;
 }
 
 template <typename V, bool ADJ, int NB>
@@ -115,12 +147,27 @@ static int grid_nb(const tqd_circuit *c, int dt) {
     uint64_t g = (uint64_t)device_sm_count() * nb;
     if (g > tiles) g = tiles;
     if (g > (uint64_t)c->pblk) g = c->pblk;
+    if (c->opts.max_blocks && g > c->opts.max_blocks) g = c->opts.max_blocks;
+    return (int)g;
+}
+
+// Ring: one block per SM.
+static int grid_ring(const tqd_circuit *c) {
+    const uint64_t tiles = (uint64_t)1 << (c->n - TILE_K);
+    uint64_t g = (uint64_t)device_sm_count();
+    if (g > tiles) g = tiles;
+    if (g > (uint64_t)c->pblk) g = c->pblk;
+    if (c->opts.max_blocks && g > c->opts.max_blocks) g = c->opts.max_blocks;
     return (int)g;
 }
 
 template <typename V, bool ADJ>
 static int grid_for(const tqd_circuit *c, int dt) {
-    return buffers_for<V, ADJ>(c, dt) == 2 ? grid_nb<V, ADJ, 2>(c, dt) : grid_nb<V, ADJ, 1>(c, dt);
+    switch (buffers_for<V, ADJ>(c, dt)) {
+    case TB_RING: return grid_ring(c);
+    case TB_TWO: return grid_nb<V, ADJ, 2>(c, dt);
+    default: return grid_nb<V, ADJ, 1>(c, dt);
+    }
 }
 
 int tile_grid(const tqd_circuit *c, int dt, bool adj) {
@@ -144,6 +191,30 @@ static cudaError_t launch_nb(const CUtensorMap &ma, const CUtensorMap &mb, const
 }
 
 template <typename V, bool ADJ>
+static cudaError_t launch_ring_generic(const CUtensorMap &ma, const CUtensorMap &mb, const tqd_circuit *c, int pass,
+                                       cudaStream_t s) {
+    const int dt = sizeof(V) == 8 ? 0 : 1;
+    static std::mutex mu;
+    static uint32_t set_to = 0;
+    const uint32_t need = max_smem_ring<V, ADJ>(c, dt);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (need > set_to) {
+            cudaFuncSetAttribute(k_tile_ring<V, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            set_to = need;
+        }
+    }
+    const TilePlanPass &pp = c->tile_passes[pass];
+    const TileSmem sm = tile_smem_ring<V, ADJ, RingCfg<ADJ>::B>(pp.dev[dt].h);
+    const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
+    ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
+    const RT<V> *mats = dt == 0 ? (const RT<V> *)c->d_mats32 : (const RT<V> *)c->d_mats64;
+    k_tile_ring<V, ADJ><<<grid_ring(c), RingCfg<ADJ>::G * TILE_THREADS, sm.total, s>>>(
+        ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials, c->pblk, c->d_err);
+    return cudaGetLastError();
+}
+
+template <typename V, bool ADJ>
 static cudaError_t launch_t(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s) {
     const int dt = sizeof(V) == 8 ? 0 : 1;
     const TilePlanPass &pp = c->tile_passes[pass];
@@ -156,20 +227,28 @@ static cudaError_t launch_t(tqd_state *psi, tqd_state *lam, const tqd_circuit *c
     } else {
         mb = ma;
     }
-    if (buffers_for<V, ADJ>(c, dt) == 2) return launch_nb<V, ADJ, 2>(ma, mb, c, pass, s);
+    const int tb = buffers_for<V, ADJ>(c, dt);
+    if (tb == TB_TWO) return launch_nb<V, ADJ, 2>(ma, mb, c, pass, s);
     // the pass-specialised kernel when the circuit has one: same descriptor,
-    // shared memory and grid as the generic kernel
+    // shared memory and grid as the generic kernel of the same kind
+    const bool ring = tb == TB_RING;
     CUfunction f = nullptr;
-    e = jit_function(c, pass, dt, ADJ, s, &f);
+    e = jit_function(c, pass, dt, ADJ, ring, s, &f);
     if (e != cudaSuccess) return e;
-    if (!f) return launch_nb<V, ADJ, 1>(ma, mb, c, pass, s);
-    const TileSmem sm = tile_smem<V, ADJ, 1>(pp.dev[dt].h);
-    const int grid = grid_nb<V, ADJ, 1>(c, dt);
+    if (!f) {
+        if constexpr (sizeof(V) == 8) {
+            if (ring) return launch_ring_generic<V, ADJ>(ma, mb, c, pass, s);
+        }
+        return launch_nb<V, ADJ, 1>(ma, mb, c, pass, s);
+    }
+    const TileSmem sm = ring ? tile_smem_ring<V, ADJ, RingCfg<ADJ>::B>(pp.dev[dt].h) : tile_smem<V, ADJ, 1>(pp.dev[dt].h);
+    const int grid = ring ? grid_ring(c) : grid_nb<V, ADJ, 1>(c, dt);
+    const int threads = ring ? RingCfg<ADJ>::G * TILE_THREADS : TILE_THREADS;
     const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
     ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
     const void *mats = dt == 0 ? (const void *)c->d_mats32 : (const void *)c->d_mats64;
     return jit_launch(f, ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials, c->pblk, c->d_err, grid,
-                      sm.total, s);
+                      threads, sm.total, s);
 }
 
 cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s) {

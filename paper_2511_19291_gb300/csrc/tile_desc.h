@@ -97,6 +97,18 @@ struct TileStage {
 constexpr int TILE_TB = 2 * (32 + TILE_THREADS / 32);  // per-stage lane/warp table entries
 constexpr int TILE_MAX_GRAD = 32;                        // gradient ops per pass
 
+// Ring kernels (complex64): groups of 256 threads per block and tile buffers
+// in the ring.  Forward: 3 groups, 6 buffers of 32 KiB (three tiles being
+// computed, three loading).  Reverse sweep: 2 groups, 3 buffers of 64 KiB
+// (psi and lambda).
+template <bool ADJ> struct RingCfg {
+    static constexpr int G = ADJ ? 2 : 3;
+    static constexpr int B = ADJ ? 3 : 6;
+};
+// Gradient-partial columns of a ring kernel (threads t and t + 128 of every
+// group share one).
+constexpr int GACC_RING_COLS = TILE_THREADS / 2;
+
 // Scalar part of a pass descriptor.
 struct TileHead {
     int n;                 // qubits of the state

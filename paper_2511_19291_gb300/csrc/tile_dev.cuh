@@ -539,15 +539,16 @@ struct TileSmem {
     uint32_t tiles, pool, gacc, dgt, tbt, stages, ops, subs, total;
 };
 
-// Shared-memory layout of a block: NB tile buffers, each holding psi's tile
-// (and lambda's in the reverse sweep), then the pass descriptor's parts.
-template <typename V, bool ADJ, int NB>
-__host__ __device__ inline TileSmem tile_smem(const TileHead &h) {
+// Shared-memory layout of a block: `nbuf` tile buffers, each holding psi's
+// tile (and lambda's in the reverse sweep), then the pass descriptor's parts;
+// `gcols` gradient-partial columns per gradient op.
+template <typename V, bool ADJ>
+__host__ __device__ inline TileSmem tile_smem_n(const TileHead &h, int nbuf, int gcols) {
     const int pool_len = h.pool_len, n_grad = h.n_grad, n_dg = h.n_dg, n_stages = h.n_stages;
     TileSmem s;
-    s.tiles = (uint32_t)NB * (ADJ ? 2u : 1u) * (1u << TILE_K) * (uint32_t)sizeof(V);
+    s.tiles = (uint32_t)nbuf * (ADJ ? 2u : 1u) * (1u << TILE_K) * (uint32_t)sizeof(V);
     s.pool = (uint32_t)((pool_len * sizeof(RT<V>) + 15) & ~15u);
-    s.gacc = ADJ ? (uint32_t)(n_grad * TILE_THREADS * sizeof(RT<V>)) : 0u;
+    s.gacc = ADJ ? (uint32_t)(n_grad * gcols * sizeof(RT<V>)) : 0u;
     s.gacc = (s.gacc + 15) & ~15u;
     s.dgt = (uint32_t)(n_dg * NR * sizeof(V));
     s.tbt = (uint32_t)((n_stages * TILE_TB * sizeof(uint16_t) + 15) & ~15u);
@@ -556,6 +557,15 @@ __host__ __device__ inline TileSmem tile_smem(const TileHead &h) {
     s.subs = (uint32_t)((h.n_subs * sizeof(TileSub) + 15) & ~15u);
     s.total = 1024 + s.tiles + s.pool + s.gacc + s.dgt + s.tbt + s.stages + s.ops + s.subs + 16;
     return s;
+}
+template <typename V, bool ADJ, int NB>
+__host__ __device__ inline TileSmem tile_smem(const TileHead &h) {
+    return tile_smem_n<V, ADJ>(h, NB, TILE_THREADS);
+}
+// Ring kernels: B buffers shared by the block's groups; 128 gradient columns.
+template <typename V, bool ADJ, int B>
+__host__ __device__ inline TileSmem tile_smem_ring(const TileHead &h) {
+    return tile_smem_n<V, ADJ>(h, B, GACC_RING_COLS);
 }
 
 // Blocks per SM the register budget is sized for: what the shared memory of
@@ -591,10 +601,26 @@ template <typename V> struct TileCtx {
     const TileOp *ops;
     const TileSub *subs;
     int n_stages;
-    uint32_t tid;
+    uint32_t tid;            // thread index within the group of 256 that works on the tile
     int lane, warp;
+    uint32_t bar_id;         // named barrier of that group (0 = the whole block of 256)
     int *err;
 };
+
+// End of a stage: the group's threads meet (bar.sync on the group's barrier).
+template <typename V> __device__ __forceinline__ void tile_sync(const TileCtx<V> &c) {
+    asm volatile("bar.sync %0, %1;" ::"r"(c.bar_id), "n"(TILE_THREADS) : "memory");
+}
+
+// Gradient partials: [gradient op][column].  One block per tile (ATOM false):
+// a column per thread, plain read-modify-write.  Ring kernels (ATOM true):
+// the groups share 128 columns (threads t and t + 128 of every group), added
+// with shared-memory atomics (GACC_RING_COLS columns).
+template <bool ATOM, typename T>
+__device__ __forceinline__ void gacc_add(T *gacc, int slot, uint32_t tid, T v) {
+    if constexpr (ATOM) atomicAdd(gacc + slot * GACC_RING_COLS + (tid & (GACC_RING_COLS - 1)), v);
+    else gacc[slot * TILE_THREADS + tid] += v;
+}
 
 // Register j's tile index in a stage: lane and warp table entries XOR the
 // register offset.  Forward loads through F and stores through G; the
@@ -632,7 +658,7 @@ __device__ __forceinline__ void tile_st(const TileCtx<V> &c, const V (&a)[NR], c
 }
 
 // The generic stage runner: interprets the pass's stage and op lists.
-template <typename V, bool ADJ> struct InterpRunner {
+template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
     static __device__ __forceinline__ void run(const TileCtx<V> &c) {
         using T = RT<V>;
         int *err = c.err;
@@ -667,10 +693,10 @@ template <typename V, bool ADJ> struct InterpRunner {
                         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
                             const TileSub sb = c.subs[q];
                             if (sb.gslot < 0) continue;
-                            c.gacc[sb.gslot * TILE_THREADS + c.tid] += grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, c.tid);
+                            gacc_add<ATOM>(c.gacc, sb.gslot, c.tid, grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, c.tid));
                         }
                     } else if (op.gslot >= 0) {
-                        c.gacc[op.gslot * TILE_THREADS + c.tid] += grad_op<V>(op, a, b, c.tid);
+                        gacc_add<ATOM>(c.gacc, op.gslot, c.tid, grad_op<V>(op, a, b, c.tid));
                     }
                     apply_op<V, true, true>(op, a, b, c.pool, c.tid, c.subs, c.dgt);
                 }
@@ -685,130 +711,196 @@ template <typename V, bool ADJ> struct InterpRunner {
             }
             // the last stage's writes are read next by the TMA store
             if (si == c.n_stages - 1) fence_async_smem();
-            __syncthreads();
+            tile_sync(c);
         }
     }
 };
 
-// The whole pass for one block: stage the descriptor in shared memory, then
-// load, run and store this block's tiles; in the reverse sweep, write the
-// block's gradient partials.  Runner::run(ctx) applies every stage to the
-// current tile and ends each stage with __syncthreads() (the last one after
-// fence.proxy.async).
-template <typename V, bool ADJ, int NB, typename Runner>
-__device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
-                                               const RT<V> *mats, double *partials, int pblk, int *err) {
+// Shared-memory pointers of a block, and the descriptor staged there.
+template <typename V> struct TileShared {
+    V *tiles;
+    RT<V> *pool;
+    RT<V> *gacc;
+    V *dgt;
+    uint16_t *tbt;
+    TileStage *stages;
+    TileOp *ops;
+    TileSub *subs;
+    uint64_t *bar;  // NB body: its tile barriers (dynamic part); unused by the ring
+};
+
+// Carves the dynamic shared memory by layout L, copies the pass descriptor
+// into it, gathers the ops' matrices into the pool, builds the per-stage
+// address tables and the diagonal runs' phase tables, and zeroes the
+// gradient partials (gcols columns).  All threads of the block take part;
+// ends with __syncthreads().
+template <typename V, bool ADJ>
+__device__ __forceinline__ TileShared<V> tile_setup(const TileHead &P, const TilePassDev *Pg, const RT<V> *mats,
+                                                    const TileSmem &L, int gcols, int *err) {
     using T = RT<V>;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ TileHead P;
-    __shared__ int s_timeout;
-    copy_words(&P, &Pg->h, sizeof(TileHead));
-    __syncthreads();
+    (void)err;
     const uint32_t pad = (1024u - (sptr(smem_raw) & 1023u)) & 1023u;
     unsigned char *sm = smem_raw + pad;
-    const TileSmem L = tile_smem<V, ADJ, NB>(P);
-    V *tiles = reinterpret_cast<V *>(sm);  // [buffer][psi, lambda][2^K]
-    T *pool = reinterpret_cast<T *>(sm + L.tiles);
-    T *gacc = reinterpret_cast<T *>(sm + L.tiles + L.pool);  // [grad op][thread]
-    V *dgt = reinterpret_cast<V *>(sm + L.tiles + L.pool + L.gacc);
-    uint16_t *tbt = reinterpret_cast<uint16_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt);
-    TileStage *stages = reinterpret_cast<TileStage *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt);
-    TileOp *ops = reinterpret_cast<TileOp *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages);
-    TileSub *subs = reinterpret_cast<TileSub *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops);
-    uint64_t *bar =
-        reinterpret_cast<uint64_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops + L.subs);
+    TileShared<V> S;
+    S.tiles = reinterpret_cast<V *>(sm);
+    S.pool = reinterpret_cast<T *>(sm + L.tiles);
+    S.gacc = reinterpret_cast<T *>(sm + L.tiles + L.pool);
+    S.dgt = reinterpret_cast<V *>(sm + L.tiles + L.pool + L.gacc);
+    S.tbt = reinterpret_cast<uint16_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt);
+    S.stages = reinterpret_cast<TileStage *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt);
+    S.ops = reinterpret_cast<TileOp *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages);
+    S.subs = reinterpret_cast<TileSub *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops);
+    S.bar = reinterpret_cast<uint64_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt + L.stages + L.ops + L.subs);
     const uint32_t tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
     constexpr int TBS = TILE_TB;
     constexpr int NW = TILE_THREADS / 32;
 
-    copy_words(stages, Pg->stages, P.n_stages * sizeof(TileStage));
-    copy_words(ops, Pg->ops, P.n_ops * sizeof(TileOp));
-    copy_words(subs, Pg->subs, P.n_subs * sizeof(TileSub));
+    copy_words(S.stages, Pg->stages, P.n_stages * sizeof(TileStage));
+    copy_words(S.ops, Pg->ops, P.n_ops * sizeof(TileOp));
+    copy_words(S.subs, Pg->subs, P.n_subs * sizeof(TileSub));
     __syncthreads();
 
     // matrices of every op and diagonal sub-op, per-stage lane/warp offsets
     for (int k = 0; k < P.n_ops; ++k) {
-        const TileOp op = ops[k];
+        const TileOp op = S.ops[k];
         if (op.moff < 0 || op.type == TOP_DG) continue;
         int src, len;
         op_pool_span(op.type, src, len);
         for (int i = tid; i < len; i += blockDim.x)
             if (TQD_IDX_OK((uint32_t)(op.moff + i), (uint32_t)P.pool_len))
-                pool[op.moff + i] = mats[(size_t)Pg->op_gate[k] * MAT_STRIDE + src + i];
+                S.pool[op.moff + i] = mats[(size_t)Pg->op_gate[k] * MAT_STRIDE + src + i];
     }
     for (int k = 0; k < P.n_subs; ++k) {
-        const TileSub sb = subs[k];
+        const TileSub sb = S.subs[k];
         const int src = sb.type == TOP_D1 ? 0 : 30, len = sb.type == TOP_D1 ? 8 : 2;
         for (int i = tid; i < len; i += blockDim.x)
             if (TQD_IDX_OK((uint32_t)(sb.moff + i), (uint32_t)P.pool_len))
-                pool[sb.moff + i] = mats[(size_t)Pg->sub_gate[k] * MAT_STRIDE + src + i];
+                S.pool[sb.moff + i] = mats[(size_t)Pg->sub_gate[k] * MAT_STRIDE + src + i];
     }
     for (int i = tid; i < P.n_stages * TBS; i += blockDim.x) {
         const int st = i / TBS, e = i % TBS;
-        const TileStage &S = stages[st];
-        tbt[i] = e < 32 ? S.ld_lo[e] : e < 32 + NW ? S.ld_hi[e - 32] : e < 64 + NW ? S.st_lo[e - 32 - NW] : S.st_hi[e - 64 - NW];
+        const TileStage &St = S.stages[st];
+        S.tbt[i] = e < 32 ? St.ld_lo[e] : e < 32 + NW ? St.ld_hi[e - 32] : e < 64 + NW ? St.st_lo[e - 32 - NW]
+                                                                                     : St.st_hi[e - 64 - NW];
     }
     if (ADJ) {
-        for (int i = tid; i < P.n_grad * TILE_THREADS; i += blockDim.x) gacc[i] = T(0);
-    }
-    if (tid == 0) {
-        for (int i = 0; i < NB; ++i) mbar_init(bar + i, 1);
-        mbar_fence_init();
+        for (int i = tid; i < P.n_grad * gcols; i += blockDim.x) S.gacc[i] = T(0);
     }
     __syncthreads();
     // phase tables of the diagonal runs: entry j = product of the run's gates
     // whose positions are all register bits, evaluated at register index j
     for (int i = tid; i < P.n_dg * NR; i += blockDim.x) {
         const int d = i / NR, j = i % NR;
-        const TileOp op = ops[Pg->dg_op[d]];
+        const TileOp op = S.ops[Pg->dg_op[d]];
         V t = mkc<V>(1, 0);
         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
-            const TileSub sb = subs[q];
+            const TileSub sb = S.subs[q];
             if (sb.a & 0x80) continue;
-            if (sb.type == TOP_D1) t = cmul(t, pool_c<V>(pool, sb.moff + (((j >> sb.a) & 1) ? 6 : 0)));
-            else if (((j >> sb.a) & 1) && ((j >> sb.b) & 1)) t = cmul(t, pool_c<V>(pool, sb.moff));
+            if (sb.type == TOP_D1) t = cmul(t, pool_c<V>(S.pool, sb.moff + (((j >> sb.a) & 1) ? 6 : 0)));
+            else if (((j >> sb.a) & 1) && ((j >> sb.b) & 1)) t = cmul(t, pool_c<V>(S.pool, sb.moff));
         }
-        dgt[i] = t;
+        S.dgt[i] = t;
     }
     __syncthreads();
+    return S;
+}
 
-    constexpr int TS = 1 << TILE_K;          // amplitudes per tile
+// TMA coordinates of copy e of a tile: its global index origin plus the
+// extra local bits, split into the tensor map's dimensions.
+__device__ __forceinline__ void tile_coords(const TileHead &P, uint64_t tile, int e, int (&c)[TILE_MAX_DIMS]) {
+    uint64_t g = 0;
+    for (int i = 0; i < P.n_tiles_log2; ++i) g |= ((tile >> i) & 1ull) << P.out_bits[i];
+    for (int i = 0; i < P.n_extra; ++i) g |= (uint64_t)((e >> i) & 1) << P.extra_bits[i];
+#pragma unroll
+    for (int d = 0; d < TILE_MAX_DIMS; ++d)
+        c[d] = d < P.rank ? (int)((g >> P.dim_lo[d]) & ((1ull << P.dim_len[d]) - 1)) : 0;
+}
+
+// One thread: TMA loads of a tile (psi, and lambda when ADJ) into `dst`,
+// completing on barrier `bar`.
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_issue_load(const TileHead &P, const void *map_psi, const void *map_lam, V *dst,
+                                                uint64_t *bar, uint64_t tile) {
+    constexpr int TS = 1 << TILE_K;
     constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
     const uint32_t tile_bytes = TS * (uint32_t)sizeof(V);
     const uint32_t box_bytes = tile_bytes >> P.n_extra;
-    const uint64_t n_tiles = (uint64_t)1 << P.n_tiles_log2;
+    mbar_expect_tx(bar, tile_bytes * NSTATE);
+    for (int e = 0; e < (1 << P.n_extra); ++e) {
+        int c[TILE_MAX_DIMS];
+        tile_coords(P, tile, e, c);
+        tma_load(P.rank, map_psi, sptr(dst) + e * box_bytes, bar, c);
+        if (ADJ) tma_load(P.rank, map_lam, sptr(dst + TS) + e * box_bytes, bar, c);
+    }
+}
 
-    // TMA coordinates of copy e of a tile: its global index origin plus the
-    // extra local bits, split into the tensor map's dimensions.
-    auto coords = [&](uint64_t tile, int e, int (&c)[TILE_MAX_DIMS]) {
-        uint64_t g = 0;
-        for (int i = 0; i < P.n_tiles_log2; ++i) g |= ((tile >> i) & 1ull) << P.out_bits[i];
-        for (int i = 0; i < P.n_extra; ++i) g |= (uint64_t)((e >> i) & 1) << P.extra_bits[i];
-#pragma unroll
-        for (int d = 0; d < TILE_MAX_DIMS; ++d)
-            c[d] = d < P.rank ? (int)((g >> P.dim_lo[d]) & ((1ull << P.dim_len[d]) - 1)) : 0;
-    };
-    auto issue_load = [&](uint64_t tile, int buf) {
-        V *dst = tiles + (size_t)buf * NSTATE * TS;
-        mbar_expect_tx(bar + buf, tile_bytes * NSTATE);
-        for (int e = 0; e < (1 << P.n_extra); ++e) {
-            int c[TILE_MAX_DIMS];
-            coords(tile, e, c);
-            tma_load(P.rank, map_psi, sptr(dst) + e * box_bytes, bar + buf, c);
-            if (ADJ) tma_load(P.rank, map_lam, sptr(dst + TS) + e * box_bytes, bar + buf, c);
-        }
-    };
-    auto issue_store = [&](uint64_t tile, int buf) {
-        V *src = tiles + (size_t)buf * NSTATE * TS;
-        for (int e = 0; e < (1 << P.n_extra); ++e) {
-            int c[TILE_MAX_DIMS];
-            coords(tile, e, c);
-            tma_store(P.rank, map_psi, sptr(src) + e * box_bytes, c);
-            if (ADJ) tma_store(P.rank, map_lam, sptr(src + TS) + e * box_bytes, c);
-        }
-        bulk_commit();
-    };
+// One thread: TMA stores of the tile in `src`, as one bulk group.
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_issue_store(const TileHead &P, const void *map_psi, const void *map_lam,
+                                                 V *src, uint64_t tile) {
+    constexpr int TS = 1 << TILE_K;
+    const uint32_t box_bytes = (TS * (uint32_t)sizeof(V)) >> P.n_extra;
+    for (int e = 0; e < (1 << P.n_extra); ++e) {
+        int c[TILE_MAX_DIMS];
+        tile_coords(P, tile, e, c);
+        tma_store(P.rank, map_psi, sptr(src) + e * box_bytes, c);
+        if (ADJ) tma_store(P.rank, map_lam, sptr(src + TS) + e * box_bytes, c);
+    }
+    bulk_commit();
+}
+
+// Bounded wait of one thread for phase `parity` of barrier `bar`: 1 when the
+// phase completed, 0 when the wait gave up.
+__device__ __forceinline__ int mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; !mbar_try_wait(bar, parity);)
+        if (++it > (1u << 26)) return 0;
+    return 1;
+}
+
+// Gradient partials of the block (gcols columns per gradient op, state
+// precision) added in FP64, one warp per gradient op.  Ends the pass.
+template <typename T>
+__device__ __forceinline__ void tile_write_partials(const TileHead &P, const TilePassDev *Pg, const T *gacc, int gcols,
+                                                    double *partials, int pblk) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < P.n_grad; k += nw) {
+        double t = 0;
+        for (int i = lane; i < gcols; i += 32) t += (double)gacc[k * gcols + i];
+        t = warp_sum(t);
+        if (lane == 0) partials[(size_t)Pg->grad_gate_slot[k] * pblk + blockIdx.x] = t;
+    }
+}
+
+// The whole pass for one block of 256 threads with NB tile buffers: stage the
+// descriptor in shared memory, then load, run and store this block's tiles;
+// in the reverse sweep, write the block's gradient partials.
+// Runner::run(ctx) applies every stage to the current tile and ends each
+// stage with tile_sync(ctx) (the last one after fence.proxy.async).
+template <typename V, bool ADJ, int NB, typename Runner>
+__device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
+                                               const RT<V> *mats, double *partials, int pblk, int *err) {
+    __shared__ TileHead P;
+    __shared__ int s_timeout;
+    copy_words(&P, &Pg->h, sizeof(TileHead));
+    __syncthreads();
+    const TileSmem L = tile_smem<V, ADJ, NB>(P);
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) {
+        // the barriers sit after the descriptor parts; initialised before the
+        // setup's first __syncthreads
+        extern __shared__ unsigned char smem_raw[];
+        const uint32_t pad = (1024u - (sptr(smem_raw) & 1023u)) & 1023u;
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + pad + L.total - 1024 - 16);
+        for (int i = 0; i < NB; ++i) mbar_init(bar + i, 1);
+        mbar_fence_init();
+    }
+    const TileShared<V> S = tile_setup<V, ADJ>(P, Pg, mats, L, TILE_THREADS, err);
+    uint64_t *bar = S.bar;
+
+    constexpr int TS = 1 << TILE_K;          // amplitudes per tile
+    constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
+    const uint64_t n_tiles = (uint64_t)1 << P.n_tiles_log2;
 
     // Thread 0 waits (bounded) for buffer buf's copy; the block learns the
     // outcome at the barrier, so every thread takes the same branch.  The
@@ -816,15 +908,7 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     uint32_t parity = 0;  // bit b: phase parity of buffer b's barrier
     auto wait_tile = [&](int buf) -> bool {
         const uint32_t ph = (parity >> buf) & 1u;
-        if (tid == 0) {
-            int to = 0;
-            for (uint32_t it = 0; !mbar_try_wait(bar + buf, ph);)
-                if (++it > (1u << 26)) {
-                    to = 1;
-                    break;
-                }
-            s_timeout = to;
-        }
+        if (tid == 0) s_timeout = !mbar_wait_bounded(bar + buf, ph);
         __syncthreads();
         if (s_timeout) return false;
         if (tid != 0) mbar_try_wait(bar + buf, ph);
@@ -833,22 +917,24 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     };
 
     TileCtx<V> ctx;
-    ctx.pool = pool;
-    ctx.gacc = gacc;
-    ctx.dgt = dgt;
-    ctx.tbt = tbt;
-    ctx.stages = stages;
-    ctx.ops = ops;
-    ctx.subs = subs;
+    ctx.pool = S.pool;
+    ctx.gacc = S.gacc;
+    ctx.dgt = S.dgt;
+    ctx.tbt = S.tbt;
+    ctx.stages = S.stages;
+    ctx.ops = S.ops;
+    ctx.subs = S.subs;
     ctx.n_stages = P.n_stages;
     ctx.tid = tid;
-    ctx.lane = lane;
-    ctx.warp = warp;
+    ctx.lane = tid & 31;
+    ctx.warp = tid >> 5;
+    ctx.bar_id = 0;
     ctx.err = err;
 
     // NB = 2: the next tile's copy is in flight while this one is computed;
     // a buffer is refilled only after its previous store has read it.
-    if (NB == 2 && tid == 0 && blockIdx.x < n_tiles) issue_load(blockIdx.x, 0);
+    if (NB == 2 && tid == 0 && blockIdx.x < n_tiles)
+        tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles, bar, blockIdx.x);
     int iter = 0;
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
         const int cur = NB == 2 ? (iter & 1) : 0;
@@ -856,7 +942,8 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
             const uint64_t next = NB == 2 ? tile + gridDim.x : tile;
             if (next < n_tiles) {
                 bulk_wait_read0();
-                issue_load(next, NB == 2 ? cur ^ 1 : 0);
+                const int nb = NB == 2 ? cur ^ 1 : 0;
+                tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)nb * NSTATE * TS, bar + nb, next);
             }
         }
         if (!wait_tile(cur)) {
@@ -866,22 +953,122 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
             }
             return;
         }
-        ctx.tile_a = tiles + (size_t)cur * NSTATE * TS;
+        ctx.tile_a = S.tiles + (size_t)cur * NSTATE * TS;
         ctx.tile_b = ctx.tile_a + TS;
         Runner::run(ctx);
-        if (tid == 0) issue_store(tile, cur);
+        if (tid == 0) tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile);
     }
     if (tid == 0) bulk_wait0();
     if (ADJ) {
         __syncthreads();
         // per-thread partial sums (state precision, about 16 amplitudes x
         // the block's tiles each) are added in FP64, one warp per gradient op
-        for (int k = warp; k < P.n_grad; k += NW) {
-            double t = 0;
-            for (int i = lane; i < TILE_THREADS; i += 32) t += (double)gacc[k * TILE_THREADS + i];
-            t = warp_sum(t);
-            if (lane == 0) partials[(size_t)Pg->grad_gate_slot[k] * pblk + blockIdx.x] = t;
+        tile_write_partials(P, Pg, S.gacc, TILE_THREADS, partials, pblk);
+    }
+}
+
+// The whole pass for one block of G groups of 256 threads sharing a ring of
+// B tile buffers (one block per SM).  Tile k of the block's sequence
+// (global tile blockIdx.x + k * gridDim.x) goes through buffer k mod B and
+// is computed by group k mod G.  The group's first thread waits (bounded) for
+// the buffer's copy, the group runs every stage (meeting on its own named
+// barrier), and the same thread stores the tile by TMA, waits until the store
+// has read the buffer and loads tile k + B into it at once -- so up to B - G
+// tiles are on their way in while G are computed.  A buffer passes between
+// groups when B is not a multiple of G: the waiter for tile k + B first waits
+// until tile k has been taken (gen[buffer] counts the tiles taken from each
+// buffer), so the barrier parity it waits on is never one phase stale.
+template <typename V, bool ADJ, int G, int B, typename Runner>
+__device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
+                                               const RT<V> *mats, double *partials, int pblk, int *err) {
+    static_assert(B >= G, "a ring needs a buffer per group");
+    __shared__ TileHead P;
+    __shared__ uint64_t fullb[B];
+    __shared__ int gen[B];
+    __shared__ int s_timeout[G];
+    copy_words(&P, &Pg->h, sizeof(TileHead));
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < B; ++i) {
+            mbar_init(fullb + i, 1);
+            gen[i] = 0;
         }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const TileSmem L = tile_smem_ring<V, ADJ, B>(P);
+    const TileShared<V> S = tile_setup<V, ADJ>(P, Pg, mats, L, GACC_RING_COLS, err);
+
+    constexpr int TS = 1 << TILE_K;
+    constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
+    const uint64_t n_tiles = (uint64_t)1 << P.n_tiles_log2;
+    const uint64_t n_local = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int grp = (int)(tid >> 8);
+    const uint32_t gtid = tid & (TILE_THREADS - 1);
+
+    if (tid == 0)
+        for (int k = 0; k < B && (uint64_t)k < n_local; ++k)
+            tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
+                                    blockIdx.x + (uint64_t)k * gridDim.x);
+
+    TileCtx<V> ctx;
+    ctx.pool = S.pool;
+    ctx.gacc = S.gacc;
+    ctx.dgt = S.dgt;
+    ctx.tbt = S.tbt;
+    ctx.stages = S.stages;
+    ctx.ops = S.ops;
+    ctx.subs = S.subs;
+    ctx.n_stages = P.n_stages;
+    ctx.tid = gtid;
+    ctx.lane = gtid & 31;
+    ctx.warp = gtid >> 5;
+    ctx.bar_id = 1 + grp;
+    ctx.err = err;
+
+    for (uint64_t k = grp; k < n_local; k += G) {
+        const int slot = (int)(k % B);
+        const uint32_t round = (uint32_t)(k / B);
+        if (gtid == 0) {
+            int ok = 1;
+            // tile k - B taken (only needed when buffers pass between groups)
+            if (B % G != 0) {
+                volatile int *gv = gen;
+                for (uint32_t it = 0; gv[slot] < (int)round;)
+                    if (++it > (1u << 26)) {
+                        ok = 0;
+                        break;
+                    }
+            }
+            if (ok) ok = mbar_wait_bounded(fullb + slot, round & 1u);
+            if (ok && B % G != 0) {
+                volatile int *gv = gen;
+                gv[slot] = (int)round + 1;
+            }
+            s_timeout[grp] = !ok;
+        }
+        asm volatile("bar.sync %0, %1;" ::"r"(ctx.bar_id), "n"(TILE_THREADS) : "memory");
+        if (s_timeout[grp]) {
+            if (gtid == 0) atomicExch(err, 1);
+            break;
+        }
+        if (gtid != 0) mbar_try_wait(fullb + slot, round & 1u);
+        ctx.tile_a = S.tiles + (size_t)slot * NSTATE * TS;
+        ctx.tile_b = ctx.tile_a + TS;
+        Runner::run(ctx);
+        if (gtid == 0) {
+            const uint64_t tile = blockIdx.x + k * gridDim.x;
+            tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile);
+            if (k + B < n_local) {
+                bulk_wait_read0();
+                tile_issue_load<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, fullb + slot, tile + (uint64_t)B * gridDim.x);
+            }
+        }
+    }
+    if (gtid == 0) bulk_wait0();
+    if (ADJ) {
+        __syncthreads();
+        tile_write_partials(P, Pg, S.gacc, GACC_RING_COLS, partials, pblk);
     }
 }
 

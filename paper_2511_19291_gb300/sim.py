@@ -149,7 +149,7 @@ class Circuit:
     """A gate list planned by the library (plain gate-by-gate or fused passes)."""
 
     def __init__(self, circuit: W.Circuit, mode: str = "fused", tile_qubits: int = 0, low_qubits: int = 0,
-                 device=None, buffers: int = 0, jit: int = 0):
+                 device=None, buffers: int = 0, jit: int = 0, max_blocks: int = 0):
         self.spec = circuit
         self.n = circuit.n_qubits
         self.n_params = circuit.n_params
@@ -162,6 +162,7 @@ class Circuit:
         opts.low_qubits = low_qubits
         opts.buffers = buffers
         opts.jit = jit
+        opts.max_blocks = max_blocks
         h = C.c_void_p()
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(dev):

@@ -100,7 +100,9 @@ def test_gradient_parity_random(mode, dtype, n, ng, seed):
     np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 10 * math.sqrt(ng), rtol=0)
 
 
-TILE_VARIANTS = {"generic": dict(jit=1), "generic_2buf": dict(jit=1, buffers=2), "specialised": dict(jit=2)}
+TILE_VARIANTS = {"generic": dict(jit=1), "generic_2buf": dict(jit=1, buffers=2), "specialised": dict(jit=2),
+                 "generic_ring": dict(jit=1, buffers=3, max_blocks=2),
+                 "specialised_ring": dict(jit=2, buffers=3, max_blocks=2)}
 
 
 @pytest.mark.parametrize("variant", list(TILE_VARIANTS))
@@ -127,6 +129,32 @@ def test_fused_tile_variants_random(variant, dtype, n, ng, seed):
     e0 = np.zeros(1 << n, dtype=complex)
     e0[0] = 1
     np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 10 * math.sqrt(ng), rtol=0)
+
+
+@pytest.mark.parametrize("jit", [1, 2])
+@pytest.mark.parametrize("n,layers,max_blocks", [(15, 2, 1), (17, 2, 3)])
+def test_ring_many_tiles_per_block(jit, n, layers, max_blocks):
+    """Ring kernels with few blocks, so that each block cycles through many
+    tiles: buffers are refilled after their stores and (reverse sweep: 3
+    buffers, 2 groups) handed from one group to the other.  The ansatz with
+    the Ising observable, energy and gradient against the oracle."""
+    circ = W.hea_ansatz(n, layers)
+    params = W.config_rng(3).angles(circ.n_params)
+    terms = W.ising(n)
+    ref = oracle.grad_param_shift(circ, params, terms)
+    e_ref = oracle.energy(circ, params, terms)
+    kw = dict(jit=jit, buffers=3, max_blocks=max_blocks)
+    st, _, _ = gpu_state(circ, params, "fused", "c64", **kw)
+    assert abs(sim().expval(st, terms).item() - e_ref) < E_TOL["c64"]
+    np.testing.assert_allclose(to_numpy(st), oracle.run(circ, params), atol=AMP_TOL["c64"] * 4, rtol=0)
+    del st
+    g, st = gpu_grad(circ, params, terms, "fused", "c64", **kw)
+    ok, worst = grad_close(g, ref, G_REL["c64"], hnorm=W.observable_l1(terms))
+    assert ok, f"worst relative error {worst}"
+    back = to_numpy(st)
+    e0 = np.zeros(1 << n, dtype=complex)
+    e0[0] = 1
+    np.testing.assert_allclose(back, e0, atol=AMP_TOL["c64"] * 40, rtol=0)
 
 
 @pytest.mark.parametrize("jit", [1, 2])
