@@ -160,7 +160,7 @@ static tqd_status validate_circuit(int n_qubits, const tqd_gate *gates, size_t n
         o = *opts;
         CHECK_ARG(o.mode == TQD_PLAN_PLAIN || o.mode == TQD_PLAN_FUSED || o.mode == TQD_PLAN_TC,
                   "tqd_circuit_create: unknown plan mode");
-        CHECK_ARG(o.buffers <= 3, "tqd_circuit_create: buffers %u not in {0, 1, 2, 3}", o.buffers);
+        CHECK_ARG(o.buffers <= 4, "tqd_circuit_create: buffers %u not in {0, ..., 4}", o.buffers);
         CHECK_ARG(o.jit <= 2, "tqd_circuit_create: jit %u not in {0, 1, 2}", o.jit);
         for (int i = 0; i < 2; ++i) CHECK_ARG(o.reserved[i] == 0, "tqd_circuit_create: reserved opts not zero");
     }

@@ -17,6 +17,7 @@
 #include <map>
 #include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "jit.h"
 #include "plan.h"
@@ -115,6 +116,40 @@ void put(std::string &o, const char *fmt, ...) {
 
 const char *tf(bool b) { return b ? "true" : "false"; }
 
+// Whether a diagonal run has gates on thread bits (a per-thread factor).
+bool dg_has_thread_subs(const TilePassDev &D, const TileOp &op) {
+    for (int q = op.sub0; q < op.sub0 + op.nsub; ++q)
+        if (D.subs[q].a & 0x80) return true;
+    return false;
+}
+
+// The runner's init: every diagonal run's thread factor (the product of its
+// gates on thread bits at this thread's bit values) into member f<run>.  It
+// depends only on the thread and the pass, not on the tile.
+void emit_init(std::string &o, const TilePassDev &D) {
+    for (int k = 0; k < D.h.n_ops; ++k) {
+        const TileOp &op = D.ops[k];
+        if (op.type == TOP_DG && dg_has_thread_subs(D, op)) put(o, "TV f%d;\n", op.moff);
+    }
+    o += "__device__ __forceinline__ void init(const TileCtx<TV> &c) {\nconst uint32_t tid = c.tid;\n(void)tid;\n";
+    for (int k = 0; k < D.h.n_ops; ++k) {
+        const TileOp &op = D.ops[k];
+        if (op.type != TOP_DG || !dg_has_thread_subs(D, op)) continue;
+        put(o, "{\nTV f = mkc<TV>(1, 0);\n");
+        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+            const TileSub &sb = D.subs[q];
+            if (!(sb.a & 0x80)) continue;
+            if (sb.type == TOP_D1)
+                put(o, "f = cmul(f, pool_c<TV>(c.pool, %d + (tbit(tid, %d) ? 6 : 0)));\n", sb.moff, sb.a);
+            else
+                put(o, "if (tbit(tid, %d) & tbit(tid, %d)) f = cmul(f, pool_c<TV>(c.pool, %d));\n", sb.a, sb.b,
+                    sb.moff);
+        }
+        put(o, "f%d = f;\n}\n", op.moff);
+    }
+    o += "}\n";
+}
+
 // One op applied forward (or inverted in the reverse sweep, where it acts on
 // psi and lambda): the generic kernel's apply_op with every field constant.
 void emit_apply(std::string &o, const TilePassDev &D, const TileOp &op, bool adj) {
@@ -152,23 +187,11 @@ void emit_apply(std::string &o, const TilePassDev &D, const TileOp &op, bool adj
         else
             put(o, "op_d2rr<TV, %s, %s, %d, %d>(a, b, c.pool + %d);\n", dg, two, op.a, op.b, op.moff);
         break;
-    case TOP_DG: {
-        // thread factor of the run's gates on thread bits, then the table
-        bool any = false;
-        o += "{\nTV f = mkc<TV>(1, 0);\n";
-        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
-            const TileSub &sb = D.subs[q];
-            if (!(sb.a & 0x80)) continue;
-            any = true;
-            if (sb.type == TOP_D1)
-                put(o, "f = cmul(f, pool_c<TV>(c.pool, %d + (tbit(tid, %d) ? 6 : 0)));\n", sb.moff, sb.a);
-            else
-                put(o, "if (tbit(tid, %d) & tbit(tid, %d)) f = cmul(f, pool_c<TV>(c.pool, %d));\n", sb.a, sb.b,
-                    sb.moff);
-        }
-        put(o, "op_dg<TV, %s, %s, %s>(a, b, c.dgt + %d * NR, f);\n}\n", dg, two, tf(any), op.moff);
+    case TOP_DG:
+        // the table, times the run's thread factor (computed once per block by init)
+        if (dg_has_thread_subs(D, op)) put(o, "op_dg<TV, %s, %s, true>(a, b, c.dgt + %d * NR, f%d);\n", dg, two, op.moff, op.moff);
+        else put(o, "op_dg<TV, %s, %s, false>(a, b, c.dgt + %d * NR, mkc<TV>(1, 0));\n", dg, two, op.moff);
         break;
-    }
     default:
         break;
     }
@@ -198,24 +221,53 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
             op.type, op.a, op.b, op.gen);
 }
 
-std::string generate(const TilePassDev &D, int dt, bool adj, bool ring) {
+// The 16 shared-memory accesses of a stage: register j of the thread sits at
+// tile index base ^ roff[j], base = lo[lane] ^ hi[warp].  Every bit base can
+// have lies in TB (the union of the lo and hi entries), so with u = roff[j] & TB
+// the index is (base ^ u) + (roff[j] & ~TB): the sum of a per-thread value and
+// a constant with disjoint bits.  Each distinct u gets one XOR; the constant
+// becomes the access's immediate offset.
+void emit_access(std::string &o, const char *fn, const char *base, const uint16_t *lo, const uint16_t *hi,
+                 const uint16_t *roff) {
+    uint32_t tb = 0;
+    for (int l = 0; l < 32; ++l) tb |= lo[l];
+    for (int w = 0; w < TILE_THREADS / 32; ++w) tb |= hi[w];
+    std::vector<uint32_t> us;
+    int idx[1 << TILE_R];
+    for (int j = 0; j < (1 << TILE_R); ++j) {
+        const uint32_t u = roff[j] & tb;
+        int k = 0;
+        while (k < (int)us.size() && us[k] != u) ++k;
+        if (k == (int)us.size()) {
+            us.push_back(u);
+            put(o, "const uint32_t %s%d = %s ^ %uu;\n", base, k, base, u);
+        }
+        idx[j] = k;
+    }
+    for (int j = 0; j < (1 << TILE_R); ++j)
+        put(o, "%s<TV, KADJ>(c, a, b, %d, %s%d + %uu);\n", fn, j, base, idx[j], (unsigned)(roff[j] & ~tb));
+}
+
+std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tmaw) {
     const TileHead &h = D.h;
     std::string o;
     o.reserve(1 << 16);
     o += "#include \"tile_dev.cuh\"\nnamespace tqd {\n";
     put(o, "typedef %s TV;\ntypedef %s TT;\nconstexpr bool KADJ = %s;\nconstexpr bool KRING = %s;\n",
         dt == 0 ? "float2" : "double2", dt == 0 ? "float" : "double", tf(adj), tf(ring));
-    o += "struct PassRunner {\nstatic __device__ __forceinline__ void run(const TileCtx<TV> &c) {\n"
-         "int *err = c.err;\n(void)err;\nconst uint32_t tid = c.tid;\nTV a[NR];\nTV b[NR];\n";
+    o += "struct PassRunner {\n";
+    emit_init(o, D);
+    o += "__device__ __forceinline__ void run(const TileCtx<TV> &c) const {\n"
+         "int *err = c.err;\n(void)err;\nconst uint32_t tid = c.tid;\n(void)tid;\nTV a[NR];\nTV b[NR];\n";
     for (int si = 0; si < h.n_stages; ++si) {
         const int s = adj ? h.n_stages - 1 - si : si;
         const TileStage &st = D.stages[s];
         put(o, "{\nconst uint16_t *tl = c.tbt + %d * TILE_TB;\n", s);
-        o += "const uint32_t bl = stage_base_ld<KADJ>(tl, c.lane, c.warp);\n"
-             "const uint32_t bs = stage_base_st<KADJ>(tl, c.lane, c.warp);\n";
+        o += "const uint32_t bl = stage_base_ld<KADJ>(tl, c.lane, c.warp);\n";
+        // the reverse sweep loads through the store map and stores through the load map
         const uint16_t *rl = adj ? st.st_roff : st.ld_roff;
         const uint16_t *rs = adj ? st.ld_roff : st.st_roff;
-        for (int j = 0; j < (1 << TILE_R); ++j) put(o, "tile_ld<TV, KADJ>(c, a, b, %d, bl ^ %uu);\n", j, (unsigned)rl[j]);
+        emit_access(o, "tile_ld", "bl", adj ? st.st_lo : st.ld_lo, adj ? st.st_hi : st.ld_hi, rl);
         if (!adj) {
             for (int k = st.op_begin; k < st.op_end; ++k) emit_apply(o, D, D.ops[k], false);
         } else {
@@ -224,7 +276,8 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring) {
                 emit_apply(o, D, D.ops[k], true);
             }
         }
-        for (int j = 0; j < (1 << TILE_R); ++j) put(o, "tile_st<TV, KADJ>(c, a, b, %d, bs ^ %uu);\n", j, (unsigned)rs[j]);
+        o += "const uint32_t bs = stage_base_st<KADJ>(tl, c.lane, c.warp);\n";
+        emit_access(o, "tile_st", "bs", adj ? st.ld_lo : st.st_lo, adj ? st.ld_hi : st.st_hi, rs);
         if (si == h.n_stages - 1) o += "fence_async_smem();\n";
         o += "tile_sync(c);\n}\n";
     }
@@ -236,10 +289,10 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring) {
         "tqd_pass(const __grid_constant__ tqd::TmaDesc mp, const __grid_constant__ tqd::TmaDesc ml,\n"
         "         const tqd::TilePassDev *__restrict__ Pg, const tqd::TT *__restrict__ mats,\n"
         "         double *__restrict__ partials, int pblk, int *__restrict__ err) {\n",
-        ring ? (adj ? RingCfg<true>::G : RingCfg<false>::G) * TILE_THREADS : TILE_THREADS, ring ? 1 : minb);
+        ring ? (adj ? (tmaw ? RingCfg<true>::THREADS_TMAW : RingCfg<true>::THREADS) : (tmaw ? RingCfg<false>::THREADS_TMAW : RingCfg<false>::THREADS)) : TILE_THREADS, ring ? 1 : minb);
     if (ring)
-        o += "    tqd::tile_pass_ring<tqd::TV, tqd::KADJ, tqd::RingCfg<tqd::KADJ>::G, tqd::RingCfg<tqd::KADJ>::B,\n"
-             "                        tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n}\n";
+        put(o, "    tqd::tile_pass_ring<tqd::TV, tqd::KADJ, tqd::RingCfg<tqd::KADJ>::G, tqd::RingCfg<tqd::KADJ>::B, %s,\n"
+               "                        tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n}\n", tf(tmaw));
     else
         o += "    tqd::tile_pass_body<tqd::TV, tqd::KADJ, 1, tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n}\n";
     return o;
@@ -306,11 +359,11 @@ bool jit_wanted(const tqd_circuit *c) {
     return c->n >= 22 && nvrtc().ok && driver().ok;
 }
 
-std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring) {
-    return generate(c->tile_passes[pass].dev[dt], dt, adj, ring);
+std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw) {
+    return generate(c->tile_passes[pass].dev[dt], dt, adj, ring, tmaw);
 }
 
-static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring) {
+static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bool tmaw) {
     if (!nvrtc().ok || !driver().ok) {
         set_error("specialised pass kernels: NVRTC or the CUDA driver entry points are unavailable");
         return cudaErrorNotSupported;
@@ -326,7 +379,7 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring) {
         std::lock_guard<std::mutex> lk(g_cache_mu);
         for (int p = 0; p < np; ++p) {
             if (!adj && dt == 0 && c->tile_passes[p].tc >= 0) continue;  // forward runs on the tensor cores
-            srcs[p] = jit_source(c, p, dt, adj, ring);
+            srcs[p] = jit_source(c, p, dt, adj, ring, tmaw);
             if (g_cache.count({dev, srcs[p]}) || first.count(srcs[p])) continue;
             first[srcs[p]] = p;
             need.push_back(p);
@@ -380,7 +433,7 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring) {
     return cudaSuccess;
 }
 
-cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, cudaStream_t s,
+cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, cudaStream_t s,
                          CUfunction *out) {
     *out = nullptr;
     if (!jit_wanted(c)) return cudaSuccess;
@@ -390,7 +443,7 @@ cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool 
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
             return cudaSuccess;  // no module loads inside a capture: generic kernel
-        const cudaError_t e = prepare(c, dt, adj, ring);
+        const cudaError_t e = prepare(c, dt, adj, ring, tmaw);
         if (e != cudaSuccess) return e;
     }
     const std::vector<void *> &tab = c->jit_fn[dt][di];
@@ -431,8 +484,8 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
         for (auto &p : passes)
             for (int dt = 0; dt < 2; ++dt)
                 for (int adj = 0; adj < 2; ++adj)
-                    for (int ring = 0; ring < (dt == 0 ? 2 : 1); ++ring) {
-                        std::string src = generate(p.dev[dt], dt, adj != 0, ring != 0);
+                    for (int ring = 0; ring < (dt == 0 ? 3 : 1); ++ring) {
+                        std::string src = generate(p.dev[dt], dt, adj != 0, ring != 0, ring == 2);
                         if (seen.emplace(src, 1).second) srcs.push_back(std::move(src));
                     }
     }

@@ -24,8 +24,8 @@ bool jit_wanted(const tqd_circuit *c);
 
 // Source text of pass `pass`'s specialised kernel (dt: 0 complex64, 1 complex128).
 // `ring`: the kernel runs on a ring of tile buffers (tile_pass_ring) instead of
-// one buffer per block (tile_pass_body).
-std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring);
+// one buffer per block (tile_pass_body); `tmaw`: the ring has a TMA warp.
+std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw);
 
 // The specialised kernel of pass `pass`, compiling every pass of (dt, adj)
 // on first use.  *out = nullptr means "run the generic kernel": the circuit
@@ -33,7 +33,7 @@ std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ri
 // mode, the pass is replaced by a tensor-core block, or s is capturing a
 // graph before the kernels exist.  Errors: NVRTC missing when the circuit
 // requires it (cudaErrorNotSupported) or a failed compile / module load.
-cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, cudaStream_t s,
+cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, cudaStream_t s,
                          CUfunction *out);
 
 // Launches a specialised kernel with the generic kernel's arguments.

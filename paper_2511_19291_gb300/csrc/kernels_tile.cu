@@ -26,14 +26,15 @@ __global__ void __launch_bounds__(TILE_THREADS, tile_min_blocks<V, ADJ, NB>())
     tile_pass_body<V, ADJ, NB, InterpRunner<V, ADJ>>(&map_psi, &map_lam, Pg, mats, partials, pblk, err);
 }
 
-// The generic pass on a ring of tile buffers (one block per SM, G groups).
-template <typename V, bool ADJ>
-__global__ void __launch_bounds__(RingCfg<ADJ>::G * TILE_THREADS, 1)
+// The generic pass on a ring of tile buffers (one block per SM, G groups,
+// TMAW: plus a TMA warp).
+template <typename V, bool ADJ, bool TMAW>
+__global__ void __launch_bounds__((TMAW ? RingCfg<ADJ>::THREADS_TMAW : RingCfg<ADJ>::THREADS), 1)
     k_tile_ring(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam,
                 const TilePassDev *__restrict__ Pg, const RT<V> *__restrict__ mats, double *__restrict__ partials,
                 int pblk, int *__restrict__ err) {
-    tile_pass_ring<V, ADJ, RingCfg<ADJ>::G, RingCfg<ADJ>::B, InterpRunner<V, ADJ, true>>(&map_psi, &map_lam, Pg, mats,
-                                                                                          partials, pblk, err);
+    tile_pass_ring<V, ADJ, RingCfg<ADJ>::G, RingCfg<ADJ>::B, TMAW, InterpRunner<V, ADJ, true>>(
+        &map_psi, &map_lam, Pg, mats, partials, pblk, err);
 }
 
 // ------------------------------------------------------------------- host
@@ -112,7 +113,10 @@ static int smem_optin_limit() {
 // the load latency hides behind other tiles' stages).  Otherwise one buffer:
 // load, compute and store a tile, with several blocks per SM; two only when
 // the caller asks for them and one block's shared memory holds them.
-enum { TB_ONE = 1, TB_TWO = 2, TB_RING = 3 };
+enum { TB_ONE = 1, TB_TWO = 2, TB_RING = 3, TB_RING_TMAW = 4 };
+
+// Default ring flavour per direction (set by measurement on the 26-qubit ansatz).
+static int ring_default(bool adj) { return adj ? TB_RING_TMAW : TB_RING; }
 
 template <typename V, bool ADJ>
 static uint32_t max_smem_ring(const tqd_circuit *c, int dt) {
@@ -126,16 +130,16 @@ static uint32_t max_smem_ring(const tqd_circuit *c, int dt) {
 
 // Static shared memory of the ring body (descriptor head, barriers, counters).
 template <bool ADJ> static constexpr uint32_t ring_static_smem() {
-    return (uint32_t)(sizeof(TileHead) + RingCfg<ADJ>::B * (8 + 4) + RingCfg<ADJ>::G * 4 + 256);
+    return (uint32_t)(sizeof(TileHead) + RingCfg<ADJ>::B * (8 + 8 + 4) + RingCfg<ADJ>::G * 4 + 256);
 }
 
 template <typename V, bool ADJ>
 static int buffers_for(const tqd_circuit *c, int dt) {
     const uint32_t want = c->opts.buffers;
     // the ring pays off once every block has several tiles (n >= 21: >= 1.7 per group)
-    if (sizeof(V) == 8 && (want == TB_RING || (want == 0 && c->n >= 21)) &&
+    if (sizeof(V) == 8 && (want >= TB_RING || (want == 0 && c->n >= 21)) &&
         max_smem_ring<V, ADJ>(c, dt) + ring_static_smem<ADJ>() <= (uint32_t)smem_optin_limit())
-        return TB_RING;
+        return want >= TB_RING ? (int)want : ring_default(ADJ);
     if (want != TB_TWO) return TB_ONE;
     return (int)max_smem<V, ADJ, 2>(c, dt) <= smem_optin_limit() ? TB_TWO : TB_ONE;
 }
@@ -164,7 +168,7 @@ static int grid_ring(const tqd_circuit *c) {
 template <typename V, bool ADJ>
 static int grid_for(const tqd_circuit *c, int dt) {
     switch (buffers_for<V, ADJ>(c, dt)) {
-    case TB_RING: return grid_ring(c);
+    case TB_RING: case TB_RING_TMAW: return grid_ring(c);
     case TB_TWO: return grid_nb<V, ADJ, 2>(c, dt);
     default: return grid_nb<V, ADJ, 1>(c, dt);
     }
@@ -190,7 +194,7 @@ static cudaError_t launch_nb(const CUtensorMap &ma, const CUtensorMap &mb, const
     return cudaGetLastError();
 }
 
-template <typename V, bool ADJ>
+template <typename V, bool ADJ, bool TMAW>
 static cudaError_t launch_ring_generic(const CUtensorMap &ma, const CUtensorMap &mb, const tqd_circuit *c, int pass,
                                        cudaStream_t s) {
     const int dt = sizeof(V) == 8 ? 0 : 1;
@@ -200,7 +204,7 @@ static cudaError_t launch_ring_generic(const CUtensorMap &ma, const CUtensorMap 
     {
         std::lock_guard<std::mutex> lk(mu);
         if (need > set_to) {
-            cudaFuncSetAttribute(k_tile_ring<V, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            cudaFuncSetAttribute(k_tile_ring<V, ADJ, TMAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
             set_to = need;
         }
     }
@@ -209,7 +213,7 @@ static cudaError_t launch_ring_generic(const CUtensorMap &ma, const CUtensorMap 
     const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
     ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
     const RT<V> *mats = dt == 0 ? (const RT<V> *)c->d_mats32 : (const RT<V> *)c->d_mats64;
-    k_tile_ring<V, ADJ><<<grid_ring(c), RingCfg<ADJ>::G * TILE_THREADS, sm.total, s>>>(
+    k_tile_ring<V, ADJ, TMAW><<<grid_ring(c), (TMAW ? RingCfg<ADJ>::THREADS_TMAW : RingCfg<ADJ>::THREADS), sm.total, s>>>(
         ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials, c->pblk, c->d_err);
     return cudaGetLastError();
 }
@@ -231,19 +235,20 @@ static cudaError_t launch_t(tqd_state *psi, tqd_state *lam, const tqd_circuit *c
     if (tb == TB_TWO) return launch_nb<V, ADJ, 2>(ma, mb, c, pass, s);
     // the pass-specialised kernel when the circuit has one: same descriptor,
     // shared memory and grid as the generic kernel of the same kind
-    const bool ring = tb == TB_RING;
+    const bool ring = tb == TB_RING || tb == TB_RING_TMAW, tmaw = tb == TB_RING_TMAW;
     CUfunction f = nullptr;
-    e = jit_function(c, pass, dt, ADJ, ring, s, &f);
+    e = jit_function(c, pass, dt, ADJ, ring, tmaw, s, &f);
     if (e != cudaSuccess) return e;
     if (!f) {
         if constexpr (sizeof(V) == 8) {
-            if (ring) return launch_ring_generic<V, ADJ>(ma, mb, c, pass, s);
+            if (tmaw) return launch_ring_generic<V, ADJ, true>(ma, mb, c, pass, s);
+            if (ring) return launch_ring_generic<V, ADJ, false>(ma, mb, c, pass, s);
         }
         return launch_nb<V, ADJ, 1>(ma, mb, c, pass, s);
     }
     const TileSmem sm = ring ? tile_smem_ring<V, ADJ, RingCfg<ADJ>::B>(pp.dev[dt].h) : tile_smem<V, ADJ, 1>(pp.dev[dt].h);
     const int grid = ring ? grid_ring(c) : grid_nb<V, ADJ, 1>(c, dt);
-    const int threads = ring ? RingCfg<ADJ>::G * TILE_THREADS : TILE_THREADS;
+    const int threads = ring ? (tmaw ? RingCfg<ADJ>::THREADS_TMAW : RingCfg<ADJ>::THREADS) : TILE_THREADS;
     const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
     ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
     const void *mats = dt == 0 ? (const void *)c->d_mats32 : (const void *)c->d_mats64;

@@ -97,13 +97,16 @@ struct TileStage {
 constexpr int TILE_TB = 2 * (32 + TILE_THREADS / 32);  // per-stage lane/warp table entries
 constexpr int TILE_MAX_GRAD = 32;                        // gradient ops per pass
 
-// Ring kernels (complex64): groups of 256 threads per block and tile buffers
-// in the ring.  Forward: 3 groups, 6 buffers of 32 KiB (three tiles being
+// Ring kernels (complex64): groups of 256 threads per block, plus one warp
+// that issues the TMA copies, and tile buffers in the ring.  Forward: 3 groups, 6 buffers of 32 KiB (three tiles being
 // computed, three loading).  Reverse sweep: 2 groups, 3 buffers of 64 KiB
 // (psi and lambda).
 template <bool ADJ> struct RingCfg {
     static constexpr int G = ADJ ? 2 : 3;
     static constexpr int B = ADJ ? 3 : 6;
+    // threads of a block: the groups, and the TMA warp when there is one
+    static constexpr int THREADS = G * TILE_THREADS;
+    static constexpr int THREADS_TMAW = G * TILE_THREADS + 32;
 };
 // Gradient-partial columns of a ring kernel (threads t and t + 128 of every
 // group share one).

@@ -59,6 +59,9 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity
         : "memory");
     return ok;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
@@ -659,7 +662,8 @@ __device__ __forceinline__ void tile_st(const TileCtx<V> &c, const V (&a)[NR], c
 
 // The generic stage runner: interprets the pass's stage and op lists.
 template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
-    static __device__ __forceinline__ void run(const TileCtx<V> &c) {
+    __device__ __forceinline__ void init(const TileCtx<V> &) {}
+    __device__ __forceinline__ void run(const TileCtx<V> &c) const {
         using T = RT<V>;
         int *err = c.err;
         for (int si = 0; si < c.n_stages; ++si) {
@@ -875,8 +879,9 @@ __device__ __forceinline__ void tile_write_partials(const TileHead &P, const Til
 // The whole pass for one block of 256 threads with NB tile buffers: stage the
 // descriptor in shared memory, then load, run and store this block's tiles;
 // in the reverse sweep, write the block's gradient partials.
-// Runner::run(ctx) applies every stage to the current tile and ends each
-// stage with tile_sync(ctx) (the last one after fence.proxy.async).
+// Runner::init(ctx) computes once per block what does not depend on the
+// tile; run(ctx) applies every stage to the current tile and ends each stage
+// with tile_sync(ctx) (the last one after fence.proxy.async).
 template <typename V, bool ADJ, int NB, typename Runner>
 __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
                                                const RT<V> *mats, double *partials, int pblk, int *err) {
@@ -930,6 +935,8 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     ctx.warp = tid >> 5;
     ctx.bar_id = 0;
     ctx.err = err;
+    Runner runner;  // per-thread values of the pass that do not depend on the tile
+    runner.init(ctx);
 
     // NB = 2: the next tile's copy is in flight while this one is computed;
     // a buffer is refilled only after its previous store has read it.
@@ -955,7 +962,7 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
         }
         ctx.tile_a = S.tiles + (size_t)cur * NSTATE * TS;
         ctx.tile_b = ctx.tile_a + TS;
-        Runner::run(ctx);
+        runner.run(ctx);
         if (tid == 0) tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile);
     }
     if (tid == 0) bulk_wait0();
@@ -968,22 +975,28 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
 }
 
 // The whole pass for one block of G groups of 256 threads sharing a ring of
-// B tile buffers (one block per SM).  Tile k of the block's sequence
-// (global tile blockIdx.x + k * gridDim.x) goes through buffer k mod B and
-// is computed by group k mod G.  The group's first thread waits (bounded) for
-// the buffer's copy, the group runs every stage (meeting on its own named
-// barrier), and the same thread stores the tile by TMA, waits until the store
-// has read the buffer and loads tile k + B into it at once -- so up to B - G
-// tiles are on their way in while G are computed.  A buffer passes between
-// groups when B is not a multiple of G: the waiter for tile k + B first waits
-// until tile k has been taken (gen[buffer] counts the tiles taken from each
-// buffer), so the barrier parity it waits on is never one phase stale.
-template <typename V, bool ADJ, int G, int B, typename Runner>
+// B tile buffers, plus (TMAW) one TMA warp (one block per SM).  Tile k of the
+// block's sequence (global tile blockIdx.x + k * gridDim.x) goes through
+// buffer k mod B and is computed by group k mod G.
+//  - TMAW: the TMA warp's first thread issues every copy: it loads the first B
+//    tiles, then for k = 0, 1, ...: waits until tile k is computed
+//    (done[buffer]), stores it, waits until the store has read the buffer and
+//    loads tile k + B into it.  The compute groups never wait for a store.
+//  - A group's first thread waits (bounded) for its tile's load (full[buffer]);
+//    the group runs every stage, meeting on its own named barrier, and the
+//    first thread marks the buffer done (TMAW), or else stores the tile itself,
+//    waits until the store has read the buffer and loads tile k + B into it.
+// Up to B - G tiles are on their way in while G are computed.  A buffer passes
+// between groups when B is not a multiple of G: the waiter for tile k + B
+// first waits until tile k has been taken (gen[buffer] counts the tiles taken
+// from each buffer), so the barrier parity it waits on is never a phase stale.
+template <typename V, bool ADJ, int G, int B, bool TMAW, typename Runner>
 __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
                                                const RT<V> *mats, double *partials, int pblk, int *err) {
     static_assert(B >= G, "a ring needs a buffer per group");
     __shared__ TileHead P;
     __shared__ uint64_t fullb[B];
+    __shared__ uint64_t doneb[B];
     __shared__ int gen[B];
     __shared__ int s_timeout[G];
     copy_words(&P, &Pg->h, sizeof(TileHead));
@@ -991,6 +1004,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     if (tid == 0) {
         for (int i = 0; i < B; ++i) {
             mbar_init(fullb + i, 1);
+            mbar_init(doneb + i, 1);
             gen[i] = 0;
         }
         mbar_fence_init();
@@ -1003,69 +1017,100 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
     const uint64_t n_tiles = (uint64_t)1 << P.n_tiles_log2;
     const uint64_t n_local = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int grp = (int)(tid >> 8);
-    const uint32_t gtid = tid & (TILE_THREADS - 1);
+    const int grp = (int)(tid >> 8);  // G: the TMA warp
 
-    if (tid == 0)
+    if (!TMAW && tid == 0)
         for (int k = 0; k < B && (uint64_t)k < n_local; ++k)
             tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
                                     blockIdx.x + (uint64_t)k * gridDim.x);
-
-    TileCtx<V> ctx;
-    ctx.pool = S.pool;
-    ctx.gacc = S.gacc;
-    ctx.dgt = S.dgt;
-    ctx.tbt = S.tbt;
-    ctx.stages = S.stages;
-    ctx.ops = S.ops;
-    ctx.subs = S.subs;
-    ctx.n_stages = P.n_stages;
-    ctx.tid = gtid;
-    ctx.lane = gtid & 31;
-    ctx.warp = gtid >> 5;
-    ctx.bar_id = 1 + grp;
-    ctx.err = err;
-
-    for (uint64_t k = grp; k < n_local; k += G) {
-        const int slot = (int)(k % B);
-        const uint32_t round = (uint32_t)(k / B);
-        if (gtid == 0) {
-            int ok = 1;
-            // tile k - B taken (only needed when buffers pass between groups)
-            if (B % G != 0) {
-                volatile int *gv = gen;
-                for (uint32_t it = 0; gv[slot] < (int)round;)
-                    if (++it > (1u << 26)) {
-                        ok = 0;
-                        break;
-                    }
+    if (TMAW && grp == G) {
+        if (tid == (uint32_t)G * TILE_THREADS) {
+            for (int k = 0; k < B && (uint64_t)k < n_local; ++k)
+                tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
+                                        blockIdx.x + (uint64_t)k * gridDim.x);
+            for (uint64_t k = 0; k < n_local; ++k) {
+                const int slot = (int)(k % B);
+                V *buf = S.tiles + (size_t)slot * NSTATE * TS;
+                if (!mbar_wait_bounded(doneb + slot, (uint32_t)(k / B) & 1u)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                const uint64_t tile = blockIdx.x + k * gridDim.x;
+                tile_issue_store<V, ADJ>(P, map_psi, map_lam, buf, tile);
+                if (k + B < n_local) {
+                    bulk_wait_read0();
+                    tile_issue_load<V, ADJ>(P, map_psi, map_lam, buf, fullb + slot, tile + (uint64_t)B * gridDim.x);
+                }
             }
-            if (ok) ok = mbar_wait_bounded(fullb + slot, round & 1u);
-            if (ok && B % G != 0) {
-                volatile int *gv = gen;
-                gv[slot] = (int)round + 1;
+            bulk_wait0();
+        }
+    } else {
+        const uint32_t gtid = tid & (TILE_THREADS - 1);
+        TileCtx<V> ctx;
+        ctx.pool = S.pool;
+        ctx.gacc = S.gacc;
+        ctx.dgt = S.dgt;
+        ctx.tbt = S.tbt;
+        ctx.stages = S.stages;
+        ctx.ops = S.ops;
+        ctx.subs = S.subs;
+        ctx.n_stages = P.n_stages;
+        ctx.tid = gtid;
+        ctx.lane = gtid & 31;
+        ctx.warp = gtid >> 5;
+        ctx.bar_id = 1 + grp;
+        ctx.err = err;
+        Runner runner;
+        runner.init(ctx);
+        for (uint64_t k = grp; k < n_local; k += G) {
+            const int slot = (int)(k % B);
+            const uint32_t round = (uint32_t)(k / B);
+            if (gtid == 0) {
+                int ok = 1;
+                // tile k - B taken (only needed when buffers pass between groups)
+                if (B % G != 0) {
+                    volatile int *gv = gen;
+                    for (uint32_t it = 0; gv[slot] < (int)round;)
+                        if (++it > (1u << 26)) {
+                            ok = 0;
+                            break;
+                        }
+                }
+                if (ok) ok = mbar_wait_bounded(fullb + slot, round & 1u);
+                if (ok && B % G != 0) {
+                    volatile int *gv = gen;
+                    gv[slot] = (int)round + 1;
+                }
+                s_timeout[grp] = !ok;
             }
-            s_timeout[grp] = !ok;
-        }
-        asm volatile("bar.sync %0, %1;" ::"r"(ctx.bar_id), "n"(TILE_THREADS) : "memory");
-        if (s_timeout[grp]) {
-            if (gtid == 0) atomicExch(err, 1);
-            break;
-        }
-        if (gtid != 0) mbar_try_wait(fullb + slot, round & 1u);
-        ctx.tile_a = S.tiles + (size_t)slot * NSTATE * TS;
-        ctx.tile_b = ctx.tile_a + TS;
-        Runner::run(ctx);
-        if (gtid == 0) {
-            const uint64_t tile = blockIdx.x + k * gridDim.x;
-            tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile);
-            if (k + B < n_local) {
-                bulk_wait_read0();
-                tile_issue_load<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, fullb + slot, tile + (uint64_t)B * gridDim.x);
+            asm volatile("bar.sync %0, %1;" ::"r"(ctx.bar_id), "n"(TILE_THREADS) : "memory");
+            if (s_timeout[grp]) {
+                if (gtid == 0) atomicExch(err, 1);
+                break;
+            }
+            if (gtid != 0) mbar_try_wait(fullb + slot, round & 1u);
+            ctx.tile_a = S.tiles + (size_t)slot * NSTATE * TS;
+            ctx.tile_b = ctx.tile_a + TS;
+            runner.run(ctx);
+            if (TMAW) {
+                // every thread of the group has written the tile and fenced it
+                // for the async proxy (the last stage's barrier): hand it to
+                // the TMA warp
+                if (gtid == 0) mbar_arrive(doneb + slot);
+            } else if (gtid == 0) {
+                // without a TMA warp the group's first thread stores the tile,
+                // waits until the store has read the buffer and refills it
+                const uint64_t tile = blockIdx.x + k * gridDim.x;
+                tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile);
+                if (k + B < n_local) {
+                    bulk_wait_read0();
+                    tile_issue_load<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, fullb + slot,
+                                            tile + (uint64_t)B * gridDim.x);
+                }
             }
         }
+        if (!TMAW && gtid == 0) bulk_wait0();
     }
-    if (gtid == 0) bulk_wait0();
     if (ADJ) {
         __syncthreads();
         tile_write_partials(P, Pg, S.gacc, GACC_RING_COLS, partials, pblk);
