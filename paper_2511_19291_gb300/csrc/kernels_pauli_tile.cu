@@ -211,13 +211,304 @@ __global__ void __launch_bounds__(PTHR) k_pauli_tile_apply(const V *__restrict__
     }
 }
 
+// ---------------------------------------- complex64: streamed, double-buffered
+// The same sums for complex64 states, built for bandwidth.  Each block keeps
+// two tile buffers: while one tile is evaluated, the next one arrives by
+// cp.async (16-byte copies, 8 per thread).  In a tile a thread owns local
+// indices l = r * 256 + tid (r = 0..15: local bits 8..11).  A term's sign
+// (-1)^{|b & z|} splits into the tile origin's parity (per tile and term,
+// from the term's z bits outside Q written as tile-index bits), the thread's
+// (local bits 0..7) and the register index's, (-1)^{|r & zr|} with zr the
+// term's local bits 8..11.  The host sorts every group's terms by zr, so a
+// group's per-r factor D(r) = sum_j C_j (-1)^{|r & zr_j|} is a 16-point
+// Walsh-Hadamard transform of the coefficients gathered by zr (and, the
+// other way round, E needs the transform of the per-r products at the
+// terms' zr), with every array index fixed at compile time.
+struct Pauli2Desc {
+    PauliTileDesc P;                       // terms of each group sorted by zr
+    uint16_t zfirst[PT_MAXG][17];          // terms of group g with zr == m: [zfirst[g][m], zfirst[g][m + 1])
+};
+
+struct Pauli2Smem {
+    Pauli2Desc D;
+    uint64_t hoff[256];
+    uint64_t tz[PT_MAXT];                  // z bits outside Q as tile-index bits
+    float2 ce[PT_MAXT];                    // this tile's coefficients (weights, scale, origin sign)
+    float2 cw[PT_MAXT];                    // coefficients with weights and scale
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Unnormalised 16-point Walsh-Hadamard transform in place:
+// v[m] <- sum_r v[r] (-1)^{|m & r|}.
+template <typename T> __device__ __forceinline__ void wht16(T (&v)[16]) {
+#pragma unroll
+    for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (!(i & h)) {
+                const T a = v[i], b = v[i | h];
+                v[i] = a + b;
+                v[i | h] = a - b;
+            }
+}
+
+__device__ __forceinline__ void p2_setup(Pauli2Smem &S, const Pauli2Desc &Dg, const double *weights, double scale) {
+    copy_in(&S.D, &Dg, sizeof(Pauli2Desc));
+    __syncthreads();
+    const PauliTileDesc &P = S.D.P;
+    for (int h = threadIdx.x; h < 256; h += blockDim.x) {
+        uint64_t o = 0;
+        for (int i = 0; i < 8; ++i) o |= (uint64_t)((h >> i) & 1) << P.hi[i];
+        S.hoff[h] = o;
+    }
+    for (int j = threadIdx.x; j < P.n_terms; j += blockDim.x) {
+        uint64_t t = 0;
+        for (int i = 0; i < P.n - PK; ++i) t |= ((P.zo[j] >> P.out_q[i]) & 1ull) << i;
+        S.tz[j] = t;
+        double w = scale;
+        if (weights) w *= weights[P.idx[j]];
+        S.cw[j] = make_float2((float)(P.cre[j] * w), (float)(P.cim[j] * w));
+    }
+    __syncthreads();
+}
+
+// Tile t's global origin and cp.async copies into buf (this thread's 8 chunks
+// of 2 amplitudes: local indices k * 512 + 2 * tid, k = 0..7).
+__device__ __forceinline__ void p2_load(const Pauli2Smem &S, const float2 *__restrict__ psi, float2 *buf,
+                                        uint64_t origin, uint32_t tid) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t l = (uint32_t)k * 512u + 2u * tid;
+        cp_async16(smem_u32(buf + l), psi + (origin | S.hoff[l >> 4] | (l & 15u)));
+    }
+}
+
+__device__ __forceinline__ uint64_t p2_origin(const PauliTileDesc &P, uint64_t t) {
+    uint64_t g = 0;
+    for (int i = 0; i < P.n - PK; ++i) g |= ((t >> i) & 1ull) << P.out_q[i];
+    return g;
+}
+
+// Tile t's coefficients: weights, scale and the origin's sign.
+__device__ __forceinline__ void p2_coeffs(Pauli2Smem &S, uint64_t t) {
+    for (int j = threadIdx.x; j < S.D.P.n_terms; j += blockDim.x) {
+        const float2 c = S.cw[j];
+        S.ce[j] = (__popcll(t & S.tz[j]) & 1) ? make_float2(-c.x, -c.y) : c;
+    }
+}
+
+// E over the tiles of one launch (complex64).
+__global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restrict__ psi, const Pauli2Desc Dg,
+                                                        double *__restrict__ partials) {
+    __shared__ Pauli2Smem S;
+    __shared__ double sh[PTHR / 32];
+    extern __shared__ __align__(16) unsigned char pt_dyn[];
+    float2 *bufs = reinterpret_cast<float2 *>(pt_dyn);  // 2 x PTS amplitudes
+    p2_setup(S, Dg, nullptr, 1.0);
+    const PauliTileDesc &P = S.D.P;
+    const uint32_t tid = threadIdx.x;
+    const uint64_t n_tiles = (uint64_t)1 << (P.n - PK);
+    // this thread's sign of every term (local bits 0..7 = thread bits)
+    uint64_t tpar = 0;
+    for (int j = 0; j < P.n_terms; ++j) tpar |= (uint64_t)(__popc(tid & P.zl[j] & 0xFFu) & 1) << j;
+    uint64_t t = blockIdx.x;
+    if (t < n_tiles) p2_load(S, psi, bufs, p2_origin(P, t), tid);
+    cp_async_commit();
+    double acc = 0;
+    for (int cur = 0; t < n_tiles; t += gridDim.x, cur ^= 1) {
+        const uint64_t tn = t + gridDim.x;
+        if (tn < n_tiles) p2_load(S, psi, bufs + (cur ^ 1) * PTS, p2_origin(P, tn), tid);
+        cp_async_commit();
+        p2_coeffs(S, t);
+        cp_async_wait1();
+        __syncthreads();
+        const float2 *tile = bufs + cur * PTS;
+        float2 a[PPER];
+#pragma unroll
+        for (int r = 0; r < PPER; ++r) a[r] = tile[r * PTHR + tid];
+        float part = 0.f;
+        for (int g = 0; g < P.n_groups; ++g) {
+            const uint32_t xl = P.gx[g];
+            const uint16_t *zf = S.D.zfirst[g];
+            // u_r = conj(psi_{l ^ x}) psi_l
+            float ur[PPER], ui[PPER];
+            if (xl == 0) {
+#pragma unroll
+                for (int r = 0; r < PPER; ++r) {
+                    ur[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
+                    ui[r] = 0.f;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < PPER; ++r) {
+                    const float2 b = tile[(r * PTHR + tid) ^ xl];
+                    ur[r] = fmaf(b.x, a[r].x, b.y * a[r].y);
+                    ui[r] = fmaf(b.x, a[r].y, -b.y * a[r].x);
+                }
+            }
+            // the transform only when some term has register bits in z
+            const bool any_zr = zf[16] > zf[1];
+            if (any_zr) {
+                wht16(ur);
+                if (xl != 0) wht16(ui);
+            } else {
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int r = 0; r < PPER; ++r) {
+                    sr += ur[r];
+                    si += ui[r];
+                }
+                ur[0] = sr;
+                ui[0] = si;
+            }
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                if (m > 0 && !any_zr) break;
+                for (int j = zf[m]; j < zf[m + 1]; ++j) {
+                    float2 c = S.ce[j];
+                    if ((tpar >> j) & 1) c = make_float2(-c.x, -c.y);
+                    part = fmaf(c.x, ur[m], fmaf(-c.y, ui[m], part));
+                }
+            }
+        }
+        acc += (double)part;
+        __syncthreads();
+    }
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// out (+)= scale * sum_j w_j c_j P_j psi over the launch's groups (complex64):
+// out_b += D_x(b ^ x) psi_{b ^ x} per group.
+__global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restrict__ psi, float2 *__restrict__ out,
+                                                       const Pauli2Desc Dg, const double *__restrict__ weights,
+                                                       double scale, int accumulate) {
+    __shared__ Pauli2Smem S;
+    extern __shared__ __align__(16) unsigned char pt_dyn[];
+    float2 *bufs = reinterpret_cast<float2 *>(pt_dyn);
+    p2_setup(S, Dg, weights, scale);
+    const PauliTileDesc &P = S.D.P;
+    const uint32_t tid = threadIdx.x;
+    const uint64_t n_tiles = (uint64_t)1 << (P.n - PK);
+    // sign of every term at the partner's local index l ^ x: thread bits of
+    // (tid ^ x) and the register part x's own parity (group's x)
+    uint64_t tpar = 0;
+    for (int g = 0; g < P.n_groups; ++g)
+        for (int j = P.gfirst[g]; j < P.gfirst[g + 1]; ++j) {
+            const uint32_t z = P.zl[j];
+            const int par = (__popc((tid ^ P.gx[g]) & z & 0xFFu) + __popc((P.gx[g] >> 8) & (z >> 8))) & 1;
+            tpar |= (uint64_t)par << j;
+        }
+    uint64_t t = blockIdx.x;
+    if (t < n_tiles) p2_load(S, psi, bufs, p2_origin(P, t), tid);
+    cp_async_commit();
+    for (int cur = 0; t < n_tiles; t += gridDim.x, cur ^= 1) {
+        const uint64_t tn = t + gridDim.x;
+        if (tn < n_tiles) p2_load(S, psi, bufs + (cur ^ 1) * PTS, p2_origin(P, tn), tid);
+        cp_async_commit();
+        const uint64_t origin = p2_origin(P, t);
+        float2 o[PPER];
+        if (accumulate) {
+#pragma unroll
+            for (int r = 0; r < PPER; ++r) {
+                const uint32_t l = r * PTHR + tid;
+                o[r] = out[origin | S.hoff[l >> 4] | (l & 15u)];
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < PPER; ++r) o[r] = make_float2(0.f, 0.f);
+        }
+        p2_coeffs(S, t);
+        cp_async_wait1();
+        __syncthreads();
+        const float2 *tile = bufs + cur * PTS;
+        for (int g = 0; g < P.n_groups; ++g) {
+            const uint32_t xl = P.gx[g];
+            const uint16_t *zf = S.D.zfirst[g];
+            // A_m = sum of the group's coefficients with zr == m (signed for
+            // this thread and tile), D(r) = its transform
+            float dr[PPER], di[PPER];
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                float sr = 0.f, si = 0.f;
+                for (int j = zf[m]; j < zf[m + 1]; ++j) {
+                    float2 c = S.ce[j];
+                    if ((tpar >> j) & 1) c = make_float2(-c.x, -c.y);
+                    sr += c.x;
+                    si += c.y;
+                }
+                dr[m] = sr;
+                di[m] = si;
+            }
+            if (zf[16] > zf[1]) {
+                wht16(dr);
+                wht16(di);
+            } else {
+#pragma unroll
+                for (int r = 1; r < PPER; ++r) {
+                    dr[r] = dr[0];
+                    di[r] = di[0];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < PPER; ++r) {
+                const float2 b = tile[(r * PTHR + tid) ^ xl];
+                o[r].x = fmaf(dr[r], b.x, fmaf(-di[r], b.y, o[r].x));
+                o[r].y = fmaf(dr[r], b.y, fmaf(di[r], b.x, o[r].y));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PPER; ++r) {
+            const uint32_t l = r * PTHR + tid;
+            out[origin | S.hoff[l >> 4] | (l & 15u)] = o[r];
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ host
 int high_count(uint64_t x) { return __builtin_popcountll(x >> 4); }
 
-int tile_grid_pauli(int n) {
+// complex64: 2 blocks per SM (two 32 KiB tile buffers and 128 registers a
+// thread each); complex128: 4.
+int tile_grid_pauli(int n, int dtype) {
     const uint64_t tiles = (uint64_t)1 << (n - PK);
-    uint64_t g = (uint64_t)device_sm_count() * 4;
+    uint64_t g = (uint64_t)device_sm_count() * (dtype == TQD_C64 ? 2 : 4);
     return (int)std::min<uint64_t>(g, tiles);
+}
+
+// The complex64 kernels' descriptor: each group's terms sorted by their z
+// bits on the register index (local bits 8..11), with the range of each value.
+Pauli2Desc make_pauli2(const PauliTileDesc &src) {
+    Pauli2Desc d;
+    memset(&d, 0, sizeof(d));
+    d.P = src;
+    for (int g = 0; g < src.n_groups; ++g) {
+        const int a = src.gfirst[g], b = src.gfirst[g + 1];
+        std::vector<int> ord;
+        for (int j = a; j < b; ++j) ord.push_back(j);
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return (src.zl[x] >> 8) < (src.zl[y] >> 8); });
+        for (int k = 0; k < b - a; ++k) {
+            const int j = ord[k], t = a + k;
+            d.P.zl[t] = src.zl[j];
+            d.P.zo[t] = src.zo[j];
+            d.P.cre[t] = src.cre[j];
+            d.P.cim[t] = src.cim[j];
+            d.P.idx[t] = src.idx[j];
+        }
+        int k = a;
+        for (int m = 0; m <= 16; ++m) {
+            while (m < 16 && k < b && (d.P.zl[k] >> 8) < m) ++k;
+            d.zfirst[g][m] = (uint16_t)(m == 16 ? b : k);
+        }
+    }
+    return d;
 }
 
 // The staged tile is dynamic shared memory (64 KiB for complex128).
@@ -322,10 +613,22 @@ std::vector<PauliTileDesc> plan_pauli_tiles(const std::vector<PauliGroup> &group
     return out;
 }
 
+static cudaError_t tile_expval_c64(const tqd_state *st, const std::vector<PauliTileDesc> &launches,
+                                   double *partials, int pblk, cudaStream_t s) {
+    const int grid = tile_grid_pauli(st->n, TQD_C64);
+    allow_tile_smem(k_pauli2_expval, 2 * PTS * sizeof(float2));
+    for (size_t i = 0; i < launches.size(); ++i) {
+        const Pauli2Desc d = make_pauli2(launches[i]);
+        ProfScope ps(PK_EXPVAL, (double)((uint64_t)1 << st->n) * sizeof(float2), s);
+        k_pauli2_expval<<<grid, PTHR, 2 * PTS * sizeof(float2), s>>>((const float2 *)st->amps, d, partials + i * pblk);
+    }
+    return cudaGetLastError();
+}
+
 template <typename V>
 static cudaError_t tile_expval_t(const tqd_state *st, const std::vector<PauliTileDesc> &launches,
                                  double *partials, int pblk, cudaStream_t s) {
-    const int grid = tile_grid_pauli(st->n);
+    const int grid = tile_grid_pauli(st->n, st->dtype);
     allow_tile_smem(k_pauli_tile_expval<V>, PTS * sizeof(V));
     for (size_t i = 0; i < launches.size(); ++i) {
         ProfScope ps(PK_EXPVAL, (double)((uint64_t)1 << st->n) * sizeof(V), s);
@@ -337,17 +640,33 @@ static cudaError_t tile_expval_t(const tqd_state *st, const std::vector<PauliTil
 
 cudaError_t launch_pauli_tile_expval(const tqd_state *st, const std::vector<PauliTileDesc> &launches,
                                      double *partials, int pblk, cudaStream_t s) {
-    if (st->dtype == TQD_C64) return tile_expval_t<float2>(st, launches, partials, pblk, s);
+    if (st->dtype == TQD_C64) return tile_expval_c64(st, launches, partials, pblk, s);
     return tile_expval_t<double2>(st, launches, partials, pblk, s);
 }
 
-int pauli_tile_grid(int n) { return tile_grid_pauli(n); }
+int pauli_tile_grid(int n, int dtype) { return tile_grid_pauli(n, dtype); }
+
+static cudaError_t tile_apply_c64(const tqd_state *psi, const std::vector<PauliTileDesc> &launches,
+                                  const double *weights, double scale, tqd_state *out, bool accumulate,
+                                  cudaStream_t s) {
+    const int grid = tile_grid_pauli(psi->n, TQD_C64);
+    allow_tile_smem(k_pauli2_apply, 2 * PTS * sizeof(float2));
+    const double N = (double)((uint64_t)1 << psi->n) * sizeof(float2);
+    for (size_t i = 0; i < launches.size(); ++i) {
+        const Pauli2Desc d = make_pauli2(launches[i]);
+        const int acc = (accumulate || i > 0) ? 1 : 0;
+        ProfScope ps(PK_APPLY_OBS, N * (acc ? 3 : 2), s);
+        k_pauli2_apply<<<grid, PTHR, 2 * PTS * sizeof(float2), s>>>((const float2 *)psi->amps, (float2 *)out->amps, d,
+                                                                    weights, scale, acc);
+    }
+    return cudaGetLastError();
+}
 
 template <typename V>
 static cudaError_t tile_apply_t(const tqd_state *psi, const std::vector<PauliTileDesc> &launches,
                                 const double *weights, double scale, tqd_state *out, bool accumulate,
                                 cudaStream_t s) {
-    const int grid = tile_grid_pauli(psi->n);
+    const int grid = tile_grid_pauli(psi->n, psi->dtype);
     allow_tile_smem(k_pauli_tile_apply<V>, PTS * sizeof(V));
     const double N = (double)((uint64_t)1 << psi->n) * sizeof(V);
     for (size_t i = 0; i < launches.size(); ++i) {
@@ -363,7 +682,7 @@ static cudaError_t tile_apply_t(const tqd_state *psi, const std::vector<PauliTil
 cudaError_t launch_pauli_tile_apply(const tqd_state *psi, const std::vector<PauliTileDesc> &launches,
                                     const double *weights, double scale, tqd_state *out, bool accumulate,
                                     cudaStream_t s) {
-    if (psi->dtype == TQD_C64) return tile_apply_t<float2>(psi, launches, weights, scale, out, accumulate, s);
+    if (psi->dtype == TQD_C64) return tile_apply_c64(psi, launches, weights, scale, out, accumulate, s);
     return tile_apply_t<double2>(psi, launches, weights, scale, out, accumulate, s);
 }
 
