@@ -65,6 +65,30 @@ __device__ __forceinline__ uint64_t insert00(uint64_t x, int p0, int p1) {
 
 __device__ __forceinline__ int parity64(uint64_t x) { return __popcll(x) & 1; }
 
+// Packed pairs of float (Blackwell's f32x2 pipe): one instruction does the
+// real and imaginary parts of a complex64 amplitude.
+__device__ __forceinline__ uint64_t f2_pack(float2 v) {
+    uint64_t u;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(v.x), "f"(v.y));
+    return u;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t u) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(u));
+    return v;
+}
+// a * b + c, lane by lane
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+    return f2_unpack(d);
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+    return f2_unpack(d);
+}
+
 // ------------------------------------------------------------- reductions
 // Kahan-compensated FP32 (or plain FP64) running sum.
 template <typename T> struct KSum {

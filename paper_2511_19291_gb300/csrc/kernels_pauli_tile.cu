@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(PTHR) k_pauli_tile_apply(const V *__restrict__
 struct Pauli2Desc {
     PauliTileDesc P;                       // terms of each group sorted by zr
     uint16_t zfirst[PT_MAXG][17];          // terms of group g with zr == m: [zfirst[g][m], zfirst[g][m + 1])
+    uint32_t real_groups;                  // bit g: every coefficient of group g is real
 };
 
 struct Pauli2Smem {
@@ -303,13 +304,54 @@ __device__ __forceinline__ void p2_coeffs(Pauli2Smem &S, uint64_t t) {
     }
 }
 
+template <int P> struct XI { static constexpr int value = P; };
+// The partner of register r in a group with x bits xr on the register index
+// is row r ^ xr.  Masks of at most one bit (all that single-qubit x strings
+// give) become compile-time constants, so each partner load has a constant
+// offset; other masks take the row index at run time (XI<-1>).
+template <typename F> __device__ __forceinline__ void with_xr(uint32_t x, F &&f) {
+    switch (x) {
+    case 0: f(XI<0>{}); break;
+    case 1: f(XI<1>{}); break;
+    case 2: f(XI<2>{}); break;
+    case 4: f(XI<4>{}); break;
+    case 8: f(XI<8>{}); break;
+    default: f(XI<-1>{}); break;
+    }
+}
+template <int XR> __device__ __forceinline__ uint32_t prow(int r, uint32_t xr) {
+    return XR >= 0 ? (uint32_t)(r ^ XR) : ((uint32_t)r ^ xr);
+}
+
+// Tile origins from three tables of 256 entries (tile-index bits 0..7,
+// 8..15, 16..23 scattered onto the qubits outside Q).
+struct P2Origin {
+    uint64_t t[3][256];
+};
+__device__ __forceinline__ void p2_origin_tables(P2Origin &O, const PauliTileDesc &P) {
+    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) {
+        const int k = i >> 8, v = i & 255;
+        uint64_t g = 0;
+        for (int b = 0; b < 8; ++b) {
+            const int bit = 8 * k + b;
+            if (bit < P.n - PK && ((v >> b) & 1)) g |= 1ull << P.out_q[bit];
+        }
+        O.t[k][v] = g;
+    }
+}
+__device__ __forceinline__ uint64_t p2_origin_t(const P2Origin &O, uint64_t t) {
+    return O.t[0][t & 255] | O.t[1][(t >> 8) & 255] | O.t[2][(t >> 16) & 255];
+}
+
 // E over the tiles of one launch (complex64).
 __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restrict__ psi, const Pauli2Desc Dg,
-                                                        double *__restrict__ partials) {
+                                                           double *__restrict__ partials) {
     __shared__ Pauli2Smem S;
+    __shared__ P2Origin O;
     __shared__ double sh[PTHR / 32];
     extern __shared__ __align__(16) unsigned char pt_dyn[];
     float2 *bufs = reinterpret_cast<float2 *>(pt_dyn);  // 2 x PTS amplitudes
+    p2_origin_tables(O, Dg.P);
     p2_setup(S, Dg, nullptr, 1.0);
     const PauliTileDesc &P = S.D.P;
     const uint32_t tid = threadIdx.x;
@@ -318,12 +360,12 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
     uint64_t tpar = 0;
     for (int j = 0; j < P.n_terms; ++j) tpar |= (uint64_t)(__popc(tid & P.zl[j] & 0xFFu) & 1) << j;
     uint64_t t = blockIdx.x;
-    if (t < n_tiles) p2_load(S, psi, bufs, p2_origin(P, t), tid);
+    if (t < n_tiles) p2_load(S, psi, bufs, p2_origin_t(O, t), tid);
     cp_async_commit();
     double acc = 0;
     for (int cur = 0; t < n_tiles; t += gridDim.x, cur ^= 1) {
         const uint64_t tn = t + gridDim.x;
-        if (tn < n_tiles) p2_load(S, psi, bufs + (cur ^ 1) * PTS, p2_origin(P, tn), tid);
+        if (tn < n_tiles) p2_load(S, psi, bufs + (cur ^ 1) * PTS, p2_origin_t(O, tn), tid);
         cp_async_commit();
         p2_coeffs(S, t);
         cp_async_wait1();
@@ -336,44 +378,76 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
         for (int g = 0; g < P.n_groups; ++g) {
             const uint32_t xl = P.gx[g];
             const uint16_t *zf = S.D.zfirst[g];
-            // u_r = conj(psi_{l ^ x}) psi_l
-            float ur[PPER], ui[PPER];
-            if (xl == 0) {
-#pragma unroll
-                for (int r = 0; r < PPER; ++r) {
-                    ur[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
-                    ui[r] = 0.f;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < PPER; ++r) {
-                    const float2 b = tile[(r * PTHR + tid) ^ xl];
-                    ur[r] = fmaf(b.x, a[r].x, b.y * a[r].y);
-                    ui[r] = fmaf(b.x, a[r].y, -b.y * a[r].x);
-                }
-            }
-            // the transform only when some term has register bits in z
+            const int j0 = P.gfirst[g], j1 = P.gfirst[g + 1];
+            const bool real = (S.D.real_groups >> g) & 1u;
             const bool any_zr = zf[16] > zf[1];
-            if (any_zr) {
-                wht16(ur);
-                if (xl != 0) wht16(ui);
-            } else {
-                float sr = 0.f, si = 0.f;
+            // u_r = conj(psi_{l ^ x}) psi_l, l = r * 256 + tid; the partner
+            // sits at register index r ^ xr of thread tid ^ xt
+            const float2 *pt = tile + (tid ^ (xl & 0xFFu));
+            const uint32_t xr = xl >> 8;
+            if (!any_zr) {
+                // every term's factor is constant over r: one sum of u
+                float sr, si = 0.f;
+                // four independent accumulators (r mod 4) keep the FMA chains short
+                float2 s2[4], t2[4];
 #pragma unroll
-                for (int r = 0; r < PPER; ++r) {
-                    sr += ur[r];
-                    si += ui[r];
+                for (int q = 0; q < 4; ++q) s2[q] = t2[q] = make_float2(0.f, 0.f);
+                if (xl == 0) {
+#pragma unroll
+                    for (int r = 0; r < PPER; ++r) s2[r & 3] = f2_fma(a[r], a[r], s2[r & 3]);
+                } else if (real) {
+                    with_xr(xr, [&](auto XR_) {
+                        constexpr int XR = decltype(XR_)::value;
+#pragma unroll
+                        for (int r = 0; r < PPER; ++r) s2[r & 3] = f2_fma(pt[prow<XR>(r, xr) * PTHR], a[r], s2[r & 3]);
+                    });
+                } else {
+                    with_xr(xr, [&](auto XR_) {
+                        constexpr int XR = decltype(XR_)::value;
+#pragma unroll
+                        for (int r = 0; r < PPER; ++r) {
+                            const float2 b = pt[prow<XR>(r, xr) * PTHR];
+                            s2[r & 3] = f2_fma(b, a[r], s2[r & 3]);                          // b.x a.x, b.y a.y
+                            t2[r & 3] = f2_fma(b, make_float2(a[r].y, -a[r].x), t2[r & 3]);  // b.x a.y, -b.y a.x
+                        }
+                    });
                 }
-                ur[0] = sr;
-                ui[0] = si;
-            }
-#pragma unroll
-            for (int m = 0; m < 16; ++m) {
-                if (m > 0 && !any_zr) break;
-                for (int j = zf[m]; j < zf[m + 1]; ++j) {
+                sr = ((s2[0].x + s2[1].x) + (s2[2].x + s2[3].x)) + ((s2[0].y + s2[1].y) + (s2[2].y + s2[3].y));
+                if (xl != 0 && !real)
+                    si = ((t2[0].x + t2[1].x) + (t2[2].x + t2[3].x)) + ((t2[0].y + t2[1].y) + (t2[2].y + t2[3].y));
+                for (int j = j0; j < j1; ++j) {
                     float2 c = S.ce[j];
                     if ((tpar >> j) & 1) c = make_float2(-c.x, -c.y);
-                    part = fmaf(c.x, ur[m], fmaf(-c.y, ui[m], part));
+                    part = fmaf(c.x, sr, fmaf(-c.y, si, part));
+                }
+            } else {
+                float ur[PPER], ui[PPER];
+                if (xl == 0) {
+#pragma unroll
+                    for (int r = 0; r < PPER; ++r) {
+                        ur[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
+                        ui[r] = 0.f;
+                    }
+                } else {
+                    with_xr(xr, [&](auto XR_) {
+                        constexpr int XR = decltype(XR_)::value;
+#pragma unroll
+                        for (int r = 0; r < PPER; ++r) {
+                            const float2 b = pt[prow<XR>(r, xr) * PTHR];
+                            ur[r] = fmaf(b.x, a[r].x, b.y * a[r].y);
+                            ui[r] = fmaf(b.x, a[r].y, -b.y * a[r].x);
+                        }
+                    });
+                }
+                wht16(ur);
+                if (xl != 0 && !real) wht16(ui);
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    for (int j = zf[m]; j < zf[m + 1]; ++j) {
+                        float2 c = S.ce[j];
+                        if ((tpar >> j) & 1) c = make_float2(-c.x, -c.y);
+                        part = fmaf(c.x, ur[m], fmaf(-c.y, ui[m], part));
+                    }
                 }
             }
         }
@@ -387,11 +461,13 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
 // out (+)= scale * sum_j w_j c_j P_j psi over the launch's groups (complex64):
 // out_b += D_x(b ^ x) psi_{b ^ x} per group.
 __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restrict__ psi, float2 *__restrict__ out,
-                                                       const Pauli2Desc Dg, const double *__restrict__ weights,
-                                                       double scale, int accumulate) {
+                                                          const Pauli2Desc Dg, const double *__restrict__ weights,
+                                                          double scale, int accumulate) {
     __shared__ Pauli2Smem S;
+    __shared__ P2Origin O;
     extern __shared__ __align__(16) unsigned char pt_dyn[];
     float2 *bufs = reinterpret_cast<float2 *>(pt_dyn);
+    p2_origin_tables(O, Dg.P);
     p2_setup(S, Dg, weights, scale);
     const PauliTileDesc &P = S.D.P;
     const uint32_t tid = threadIdx.x;
@@ -406,20 +482,19 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
             tpar |= (uint64_t)par << j;
         }
     uint64_t t = blockIdx.x;
-    if (t < n_tiles) p2_load(S, psi, bufs, p2_origin(P, t), tid);
+    if (t < n_tiles) p2_load(S, psi, bufs, p2_origin_t(O, t), tid);
     cp_async_commit();
     for (int cur = 0; t < n_tiles; t += gridDim.x, cur ^= 1) {
         const uint64_t tn = t + gridDim.x;
-        if (tn < n_tiles) p2_load(S, psi, bufs + (cur ^ 1) * PTS, p2_origin(P, tn), tid);
+        if (tn < n_tiles) p2_load(S, psi, bufs + (cur ^ 1) * PTS, p2_origin_t(O, tn), tid);
         cp_async_commit();
-        const uint64_t origin = p2_origin(P, t);
+        const uint64_t origin = p2_origin_t(O, t);
+        // this thread's outputs: 16 runs of 16 amplitudes, one per r
+        const float2 *orow = out + (origin | (tid & 15u));
         float2 o[PPER];
         if (accumulate) {
 #pragma unroll
-            for (int r = 0; r < PPER; ++r) {
-                const uint32_t l = r * PTHR + tid;
-                o[r] = out[origin | S.hoff[l >> 4] | (l & 15u)];
-            }
+            for (int r = 0; r < PPER; ++r) o[r] = orow[S.hoff[(r * PTHR + tid) >> 4]];
         } else {
 #pragma unroll
             for (int r = 0; r < PPER; ++r) o[r] = make_float2(0.f, 0.f);
@@ -431,8 +506,41 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
         for (int g = 0; g < P.n_groups; ++g) {
             const uint32_t xl = P.gx[g];
             const uint16_t *zf = S.D.zfirst[g];
+            const int j0 = P.gfirst[g], j1 = P.gfirst[g + 1];
+            const bool real = (S.D.real_groups >> g) & 1u;
+            const float2 *pt = tile + (tid ^ (xl & 0xFFu));
+            const uint32_t xr = xl >> 8;
+            if (zf[16] <= zf[1]) {
+                // D constant over r: the sum of the group's signed coefficients
+                float dr = 0.f, di = 0.f;
+                for (int j = j0; j < j1; ++j) {
+                    float2 c = S.ce[j];
+                    if ((tpar >> j) & 1) c = make_float2(-c.x, -c.y);
+                    dr += c.x;
+                    di += c.y;
+                }
+                const float2 d2 = make_float2(dr, dr);
+                if (real) {
+                    with_xr(xr, [&](auto XR_) {
+                        constexpr int XR = decltype(XR_)::value;
+#pragma unroll
+                        for (int r = 0; r < PPER; ++r) o[r] = f2_fma(d2, pt[prow<XR>(r, xr) * PTHR], o[r]);
+                    });
+                } else {
+                    const float2 e2 = make_float2(-di, di);
+                    with_xr(xr, [&](auto XR_) {
+                        constexpr int XR = decltype(XR_)::value;
+#pragma unroll
+                        for (int r = 0; r < PPER; ++r) {
+                            const float2 b = pt[prow<XR>(r, xr) * PTHR];
+                            o[r] = f2_fma(d2, b, f2_fma(e2, make_float2(b.y, b.x), o[r]));
+                        }
+                    });
+                }
+                continue;
+            }
             // A_m = sum of the group's coefficients with zr == m (signed for
-            // this thread and tile), D(r) = its transform
+            // this thread and tile), D(r ^ xr) = its transform at r
             float dr[PPER], di[PPER];
 #pragma unroll
             for (int m = 0; m < 16; ++m) {
@@ -446,28 +554,30 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
                 dr[m] = sr;
                 di[m] = si;
             }
-            if (zf[16] > zf[1]) {
-                wht16(dr);
-                wht16(di);
+            wht16(dr);
+            if (real) {
+                with_xr(xr, [&](auto XR_) {
+                    constexpr int XR = decltype(XR_)::value;
+#pragma unroll
+                    for (int r = 0; r < PPER; ++r)
+                        o[r] = f2_fma(make_float2(dr[r], dr[r]), pt[prow<XR>(r, xr) * PTHR], o[r]);
+                });
             } else {
+                wht16(di);
+                with_xr(xr, [&](auto XR_) {
+                    constexpr int XR = decltype(XR_)::value;
 #pragma unroll
-                for (int r = 1; r < PPER; ++r) {
-                    dr[r] = dr[0];
-                    di[r] = di[0];
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < PPER; ++r) {
-                const float2 b = tile[(r * PTHR + tid) ^ xl];
-                o[r].x = fmaf(dr[r], b.x, fmaf(-di[r], b.y, o[r].x));
-                o[r].y = fmaf(dr[r], b.y, fmaf(di[r], b.x, o[r].y));
+                    for (int r = 0; r < PPER; ++r) {
+                        const float2 b = pt[prow<XR>(r, xr) * PTHR];
+                        o[r] = f2_fma(make_float2(dr[r], dr[r]), b,
+                                      f2_fma(make_float2(-di[r], di[r]), make_float2(b.y, b.x), o[r]));
+                    }
+                });
             }
         }
+        float2 *wrow = out + (origin | (tid & 15u));
 #pragma unroll
-        for (int r = 0; r < PPER; ++r) {
-            const uint32_t l = r * PTHR + tid;
-            out[origin | S.hoff[l >> 4] | (l & 15u)] = o[r];
-        }
+        for (int r = 0; r < PPER; ++r) wrow[S.hoff[(r * PTHR + tid) >> 4]] = o[r];
         __syncthreads();
     }
 }
@@ -502,6 +612,9 @@ Pauli2Desc make_pauli2(const PauliTileDesc &src) {
             d.P.cim[t] = src.cim[j];
             d.P.idx[t] = src.idx[j];
         }
+        bool real = true;
+        for (int j = a; j < b; ++j) real = real && d.P.cim[j] == 0.0;
+        if (real) d.real_groups |= 1u << g;
         int k = a;
         for (int m = 0; m <= 16; ++m) {
             while (m < 16 && k < b && (d.P.zl[k] >> 8) < m) ++k;

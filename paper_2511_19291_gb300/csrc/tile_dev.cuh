@@ -112,30 +112,6 @@ __device__ __forceinline__ void tma_store(int rank, const void *map, uint32_t sr
     }
 }
 
-// Packed pairs of float (Blackwell's f32x2 pipe): one instruction does the
-// real and imaginary parts of a complex64 amplitude.
-__device__ __forceinline__ uint64_t f2_pack(float2 v) {
-    uint64_t u;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(v.x), "f"(v.y));
-    return u;
-}
-__device__ __forceinline__ float2 f2_unpack(uint64_t u) {
-    float2 v;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(u));
-    return v;
-}
-// a * b + c, lane by lane
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
-    return f2_unpack(d);
-}
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
-    return f2_unpack(d);
-}
-
 // 128-byte swizzle of the TMA box, in amplitude units: the 16-byte chunk index
 // inside a 128-byte row is XORed with the row index modulo 8.
 template <typename V> __device__ __forceinline__ uint32_t swz(uint32_t l) {
