@@ -276,6 +276,7 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
                 emit_apply(o, D, D.ops[k], true);
             }
         }
+        if (st.sync_mid) o += "tile_sync(c);\n";
         o += "const uint32_t bs = stage_base_st<KADJ>(tl, c.lane, c.warp);\n";
         emit_access(o, "tile_st", "bs", adj ? st.ld_lo : st.st_lo, adj ? st.ld_hi : st.st_hi, rs);
         if (si == h.n_stages - 1) o += "fence_async_smem();\n";

@@ -322,13 +322,24 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
         // predecessors is scheduled or joined earlier in this stage and its
         // dense qubits fit in the stage's register set together with those
         // of the gates already joined.  Joined gates run in gate order.
+        // A CNOT, SWAP or X whose predecessors are all scheduled or such
+        // leading gates of this stage needs no register bit: the stage runs
+        // the leading gates first, folded into its load address map.
         std::vector<int> rs;
-        std::vector<char> fit(m, 0);
+        std::vector<char> fit(m, 0), lead(m, 0);
         for (int i = 0; i < m; ++i) {
             if (sched[i]) continue;
-            bool preds_ok = true;
-            for (int p : preds[i]) preds_ok = preds_ok && (sched[p] || fit[p]);
+            bool preds_ok = true, preds_lead = true;
+            for (int p : preds[i]) {
+                preds_ok = preds_ok && (sched[p] || fit[p]);
+                preds_lead = preds_lead && (sched[p] || lead[p]);
+            }
             if (!preds_ok) continue;
+            if (preds_lead && is_perm_gate(c->gates[P.gates[i]].kind)) {
+                lead[i] = 1;
+                fit[i] = 1;
+                continue;
+            }
             int need[2], cnt;
             dense_needs(c->gates[P.gates[i]], loc.data(), need, cnt);
             std::vector<int> u(rs);
@@ -338,14 +349,28 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
             rs = u;
             fit[i] = 1;
         }
+        // Then trailing permutation gates: a CNOT, SWAP or X that did not fit,
+        // whose predecessors are all scheduled, taken or trailing, joins the
+        // stage's end (its store address map).  Gates taken above that come
+        // later in gate order share no qubit with it (they would depend on
+        // it), so moving it after them keeps the circuit.
+        std::vector<char> trail(m, 0);
+        for (int i = 0; i < m; ++i) {
+            if (sched[i] || fit[i] || !is_perm_gate(c->gates[P.gates[i]].kind)) continue;
+            bool ok = true;
+            for (int p : preds[i]) ok = ok && (sched[p] || fit[p] || trail[p]);
+            if (ok) trail[i] = 1;
+        }
         StageH st;
         st.begin = (int)order.size();
-        for (int i = 0; i < m; ++i) {
-            if (!fit[i]) continue;
-            sched[i] = 1;
-            ++nsched;
-            order.push_back(i);
-        }
+        for (int part = 0; part < 3; ++part)  // leading, taken, trailing; each in gate order
+            for (int i = 0; i < m; ++i) {
+                const int which = lead[i] ? 0 : trail[i] ? 2 : fit[i] ? 1 : -1;
+                if (which != part) continue;
+                sched[i] = 1;
+                ++nsched;
+                order.push_back(i);
+            }
         st.end = (int)order.size();
         if (st.end == st.begin) return false;  // cannot happen: the first ready gate always fits
         // pad the register set with the highest free local bits (they do not
@@ -435,6 +460,23 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                     if ((w >> (u - 5)) & 1) o |= 1u << ts.thr[u];
                 ts.ld_hi[w] = (uint16_t)swz_host(F.lin(o), amp_bytes);
                 ts.st_hi[w] = (uint16_t)swz_host(G.lin(o), amp_bytes);
+            }
+            // Does every thread store only to addresses it loaded itself?  If
+            // not, a store could overwrite an amplitude another thread has
+            // yet to load, so the stage needs a barrier between the two.
+            ts.sync_mid = 0;
+            ts.pad0 = 0;
+            for (int t = 0; t < TILE_THREADS && !ts.sync_mid; ++t) {
+                uint32_t ld[1 << TILE_R], st[1 << TILE_R];
+                const uint32_t bl = ts.ld_lo[t & 31] ^ ts.ld_hi[t >> 5], bs = ts.st_lo[t & 31] ^ ts.st_hi[t >> 5];
+                for (int j = 0; j < (1 << TILE_R); ++j) {
+                    ld[j] = bl ^ ts.ld_roff[j];
+                    st[j] = bs ^ ts.st_roff[j];
+                }
+                std::sort(ld, ld + (1 << TILE_R));
+                std::sort(st, st + (1 << TILE_R));
+                for (int j = 0; j < (1 << TILE_R); ++j)
+                    if (ld[j] != st[j]) ts.sync_mid = 1;
             }
             auto pos = [&](int lb) -> uint8_t {
                 for (int r = 0; r < TILE_R; ++r)

@@ -531,7 +531,7 @@ __host__ __device__ inline TileSmem tile_smem_n(const TileHead &h, int nbuf, int
     s.gacc = (s.gacc + 15) & ~15u;
     s.dgt = (uint32_t)(n_dg * NR * sizeof(V));
     s.tbt = (uint32_t)((n_stages * TILE_TB * sizeof(uint16_t) + 15) & ~15u);
-    s.stages = (uint32_t)(n_stages * sizeof(TileStage));
+    s.stages = (uint32_t)((n_stages * sizeof(TileStage) + 15) & ~15u);
     s.ops = (uint32_t)((h.n_ops * sizeof(TileOp) + 15) & ~15u);
     s.subs = (uint32_t)((h.n_subs * sizeof(TileSub) + 15) & ~15u);
     s.total = 1024 + s.tiles + s.pool + s.gacc + s.dgt + s.tbt + s.stages + s.ops + s.subs + 16;
@@ -681,6 +681,7 @@ template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
                     apply_op<V, true, true>(op, a, b, c.pool, c.tid, c.subs, c.dgt);
                 }
             }
+            if (st.sync_mid) tile_sync(c);
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
                 const uint32_t ad = base_st ^ roff_st[j];
