@@ -162,6 +162,25 @@ tqd_status tqd_circuit_free(tqd_circuit *circuit);
 tqd_status tqd_jit_check(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
                          const double *matrices, size_t n_matrix_entries, int arch, int *n_kernels);
 
+/* Diagnostics that need no GPU: plans the circuit into fused passes as
+ * tqd_circuit_create does (12 <= n_qubits <= 20), then runs the encoded plan
+ * on the host on a random state drawn from `seed`: every tile gathered by its
+ * pass's qubit set, every stage's amplitudes loaded and stored through the
+ * address tables the kernels read, every op applied at the register and
+ * thread positions it encodes (params: host array of n_params angles).  It
+ * compares the result with the gates applied one by one
+ * (*err_forward: largest amplitude difference), runs the reverse sweep's
+ * stages and inverse ops back to the start state (*err_reverse), and does
+ * this for the complex64 and complex128 descriptors.  *n_passes and
+ * *n_stages (may be NULL) receive the plan's size.  TQD_ERR_NUMERIC when a
+ * stage moves amplitudes between threads without the barrier between its
+ * loads and stores.  The paper has no counterpart: this checks the library's
+ * own planner. */
+tqd_status tqd_plan_check(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
+                          const double *matrices, size_t n_matrix_entries, const double *params,
+                          uint64_t seed, double *err_forward, double *err_reverse, int *n_passes,
+                          int *n_stages);
+
 /* Number of device launches one tqd_apply_circuit enqueues (for accounting). */
 tqd_status tqd_circuit_info(const tqd_circuit *circuit, int *n_passes, int *n_launches_apply,
                             int *n_launches_backward);

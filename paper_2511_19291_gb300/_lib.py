@@ -28,6 +28,7 @@ PLAN_PLAIN, PLAN_FUSED, PLAN_TC = 0, 1, 2
 EXPORTS = (
     "tqd_state_alloc", "tqd_state_reset", "tqd_state_free",
     "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_jit_check",
+    "tqd_plan_check",
     "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
     "tqd_backward", "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info", "tqd_batch_free",
@@ -106,6 +107,8 @@ def load(path: str | None = None):
         L.tqd_circuit_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.tqd_circuit_check.argtypes = [vp, C.POINTER(i32)]
         L.tqd_jit_check.argtypes = [i32, vp, sz, i32, vp, sz, i32, C.POINTER(i32)]
+        L.tqd_plan_check.argtypes = [i32, vp, sz, i32, vp, sz, vp, u64, C.POINTER(dbl), C.POINTER(dbl),
+                                     C.POINTER(i32), C.POINTER(i32)]
         L.tqd_apply_circuit.argtypes = [vp, vp, vp, vp]
         L.tqd_expval.argtypes = [vp, vp, sz, vp, vp]
         L.tqd_expval_terms.argtypes = [vp, vp, sz, vp, vp]
@@ -123,7 +126,7 @@ def load(path: str | None = None):
                      "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit", "tqd_expval",
                      "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable", "tqd_backward",
                      "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info",
-                     "tqd_batch_free", "tqd_profile_enable",
+                     "tqd_batch_free", "tqd_profile_enable", "tqd_jit_check", "tqd_plan_check",
                      "tqd_profile_read"):
             getattr(L, name).restype = st
         L.tqd_last_error.restype = C.c_char_p

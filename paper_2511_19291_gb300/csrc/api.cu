@@ -12,6 +12,7 @@
 #include "jit.h"
 #include "launch.h"
 #include "plan.h"
+#include "tile_plan.h"
 
 namespace tqd {
 
@@ -261,6 +262,28 @@ tqd_status tqd_jit_check(int n_qubits, const tqd_gate *gates, size_t n_gates, in
     c.opts = o;
     c.gates = std::move(gs);
     return jit_check_host(&c, arch, n_kernels);
+}
+
+tqd_status tqd_plan_check(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params, const double *matrices,
+                          size_t n_matrix_entries, const double *params, uint64_t seed, double *err_forward,
+                          double *err_reverse, int *n_passes, int *n_stages) {
+    CHECK_ARG(err_forward != nullptr && err_reverse != nullptr, "tqd_plan_check: NULL error output");
+    tqd_plan_opts o;
+    std::vector<GateH> gs;
+    const tqd_status vs = validate_circuit(n_qubits, gates, n_gates, n_params, matrices, n_matrix_entries, nullptr, &o,
+                                           &gs);
+    if (vs != TQD_OK) return vs;
+    CHECK_ARG(n_qubits >= TILE_K && n_qubits <= 20 && n_gates > 0,
+              "tqd_plan_check: needs %d..20 qubits and a gate", TILE_K);
+    CHECK_ARG(n_params == 0 || params != nullptr, "tqd_plan_check: params is NULL");
+    tqd_circuit c;
+    c.n = n_qubits;
+    c.n_params = n_params;
+    c.opts = o;
+    c.gates = std::move(gs);
+    c.table.assign(matrices ? matrices : (const double *)nullptr,
+                   matrices ? matrices + 2 * n_matrix_entries : (const double *)nullptr);
+    return tqd::plan_check_host(&c, params, seed, err_forward, err_reverse, n_passes, n_stages);
 }
 
 tqd_status tqd_circuit_info(const tqd_circuit *c, int *n_passes, int *n_launches_apply, int *n_launches_backward) {

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include "common.cuh"
+#include "gate_mat.h"
 #include "launch.h"
 #include "prof.h"
 
@@ -44,49 +45,7 @@ __global__ void k_prep(const GateDev *__restrict__ gates, int ng, const double *
     const GateDev gd = gates[g];
     const double th = gd.param >= 0 ? params[gd.param] : gd.fixed;
     double m[MAT_STRIDE];
-#pragma unroll
-    for (int i = 0; i < MAT_STRIDE; ++i) m[i] = 0.0;
-    const int d = gate_arity(gd.kind) == 2 ? 4 : 2;
-    auto set = [&](int r, int c, double re, double im) {
-        m[2 * (r * d + c)] = re;
-        m[2 * (r * d + c) + 1] = im;
-    };
-    double s, c;
-    sincos(0.5 * th, &s, &c);
-    const double r2 = 0.70710678118654752440;
-    switch (gd.kind) {
-    case TQD_H: set(0, 0, r2, 0); set(0, 1, r2, 0); set(1, 0, r2, 0); set(1, 1, -r2, 0); break;
-    case TQD_X: set(0, 1, 1, 0); set(1, 0, 1, 0); break;
-    case TQD_Y: set(0, 1, 0, -1); set(1, 0, 0, 1); break;
-    case TQD_Z: set(0, 0, 1, 0); set(1, 1, -1, 0); break;
-    case TQD_S: set(0, 0, 1, 0); set(1, 1, 0, 1); break;
-    case TQD_T: set(0, 0, 1, 0); set(1, 1, r2, r2); break;
-    case TQD_RX: set(0, 0, c, 0); set(0, 1, 0, -s); set(1, 0, 0, -s); set(1, 1, c, 0); break;
-    case TQD_RY: set(0, 0, c, 0); set(0, 1, -s, 0); set(1, 0, s, 0); set(1, 1, c, 0); break;
-    case TQD_RZ: set(0, 0, c, -s); set(1, 1, c, s); break;
-    case TQD_PHASE: {
-        double s1, c1;
-        sincos(th, &s1, &c1);
-        set(0, 0, 1, 0); set(1, 1, c1, s1);
-        break;
-    }
-    case TQD_UNITARY1:
-        for (int i = 0; i < 8; ++i) m[i] = table[2 * gd.mat + i];
-        break;
-    case TQD_CNOT: set(0, 0, 1, 0); set(1, 1, 1, 0); set(2, 3, 1, 0); set(3, 2, 1, 0); break;
-    case TQD_CZ: set(0, 0, 1, 0); set(1, 1, 1, 0); set(2, 2, 1, 0); set(3, 3, -1, 0); break;
-    case TQD_CPHASE: {
-        double s1, c1;
-        sincos(th, &s1, &c1);
-        set(0, 0, 1, 0); set(1, 1, 1, 0); set(2, 2, 1, 0); set(3, 3, c1, s1);
-        break;
-    }
-    case TQD_SWAP: set(0, 0, 1, 0); set(1, 2, 1, 0); set(2, 1, 1, 0); set(3, 3, 1, 0); break;
-    case TQD_UNITARY2:
-        for (int i = 0; i < 32; ++i) m[i] = table[2 * gd.mat + i];
-        break;
-    default: break;
-    }
+    gate_matrix(gd.kind, th, table, gd.mat, m);
 #pragma unroll
     for (int i = 0; i < MAT_STRIDE; ++i) {
         m64[(size_t)g * MAT_STRIDE + i] = m[i];

@@ -19,4 +19,9 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P);
 cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s);
 int tile_grid(const tqd_circuit *c, int dtype, bool adj);
 
+// Host execution of circuit c's fused plan from its descriptors against the
+// gates applied one by one (tqd_plan_check).
+tqd_status plan_check_host(tqd_circuit *c, const double *params, uint64_t seed, double *err_fwd, double *err_rev,
+                           int *n_passes, int *n_stages);
+
 }  // namespace tqd

@@ -145,6 +145,22 @@ def jit_check(circuit: W.Circuit, arch: int = 103) -> int:
     return n.value
 
 
+def plan_check(circuit: W.Circuit, params=None, seed: int = 1) -> dict:
+    """Runs the circuit's fused plan on the host from its encoded descriptors
+    and compares it with the gates applied one by one (tqd_plan_check, no
+    GPU): largest amplitude error after the forward passes and after the
+    reverse sweep, and the plan's pass and stage counts."""
+    arr, mats, n_entries = _gate_array(circuit)
+    p = np.ascontiguousarray(np.zeros(max(1, circuit.n_params)) if params is None else params, dtype=np.float64)
+    ef, er = C.c_double(), C.c_double()
+    npass, nstage = C.c_int32(), C.c_int32()
+    _lib.check(_L().tqd_plan_check(
+        circuit.n_qubits, C.cast(arr, C.c_void_p), len(circuit.gates), circuit.n_params,
+        mats.ctypes.data_as(C.c_void_p) if n_entries else None, n_entries, p.ctypes.data_as(C.c_void_p),
+        seed, C.byref(ef), C.byref(er), C.byref(npass), C.byref(nstage)))
+    return {"err_forward": ef.value, "err_reverse": er.value, "passes": npass.value, "stages": nstage.value}
+
+
 class Circuit:
     """A gate list planned by the library (plain gate-by-gate or fused passes)."""
 

@@ -1,0 +1,64 @@
+"""The fused planner on the host: every circuit's encoded passes, executed
+from their descriptors (tile gathering, stage address tables, op positions,
+forward and reverse), against the gates applied one by one, for both
+precisions' descriptors.  No GPU: tqd_plan_check runs on the CPU.  Also
+checks that every stage that moves amplitudes between threads carries the
+barrier between its loads and stores."""
+import numpy as np
+import pytest
+
+from paper_2511_19291_gb300 import sim as S
+from paper_2511_19291_gb300 import workloads as W
+
+TOL = 1e-12
+
+
+def check(circ, params, seed=1):
+    r = S.plan_check(circ, params, seed)
+    assert r["err_forward"] < TOL, r
+    assert r["err_reverse"] < TOL, r
+    assert r["passes"] >= 1 and r["stages"] >= r["passes"]
+    return r
+
+
+@pytest.mark.parametrize("n,layers", [(12, 4), (13, 3), (14, 5), (16, 4), (18, 3)])
+def test_ansatz_plans(n, layers):
+    circ = W.hea_ansatz(n, layers)
+    check(circ, W.config_rng(2).angles(circ.n_params))
+
+
+@pytest.mark.parametrize("n,ng,seed", [(12, 150, 1), (13, 200, 2), (14, 300, 3), (16, 250, 4), (17, 120, 5)])
+def test_random_plans_every_gate_kind(n, ng, seed):
+    rng = W.SplitMix64(9100 + seed)
+    circ, params = W.random_circuit(rng, n, ng, n_params=max(2, ng // 3))
+    check(circ, params, seed)
+
+
+@pytest.mark.parametrize("n", [12, 15])
+def test_qft_then_ansatz_plan(n):
+    circ = W.qft_then_hea(n, 2)
+    check(circ, W.config_rng(5).angles(circ.n_params))
+
+
+def test_ladder_plan():
+    circ = W.ladder_ansatz(14, 4)
+    check(circ, W.config_rng(4).angles(circ.n_params))
+
+
+def test_permutation_only_plan():
+    # CNOT rings and SWAPs only: whole passes are address maps (stages
+    # without ops, folded loads and stores)
+    n = 14
+    gates = []
+    for r in range(3):
+        gates += [W.Gate("CNOT", (q, (q + 1 + r) % n)) for q in range(n)]
+        gates += [W.Gate("SWAP", (q, (q + 5) % n)) for q in range(0, n, 3)]
+        gates += [W.Gate("X", (q,)) for q in range(r, n, 4)]
+    check(W.Circuit(n, gates, 0), np.zeros(1))
+
+
+def test_plan_check_rejects_small_and_large():
+    with pytest.raises(Exception):
+        S.plan_check(W.hea_ansatz(8, 1), np.zeros(16))
+    with pytest.raises(Exception):
+        S.plan_check(W.hea_ansatz(21, 1), np.zeros(42))
