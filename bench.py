@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--sweep-n", type=int, default=30, help="qubits of the plain gate-sweep measurement (0 = skip)")
     ap.add_argument("--batch-count", type=int, default=512, help="circuits of the batched measurement (0 = skip)")
     ap.add_argument("--tc-gates", type=int, default=200, help="gates of the tensor-core block measurement (0 = skip)")
+    ap.add_argument("--qft-n", type=int, default=32, help="qubits of the QFT + ansatz measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -348,6 +349,52 @@ def tc_bench(S, torch, dev, n, n_gates, barrier, reps=5):
     return out
 
 
+# ------------------------------------------------ QFT + ansatz at 32 qubits
+def qft_bench(S, torch, dev, n, barrier, layers=8):
+    """One gradient evaluation of the QFT followed by `layers` ansatz layers
+    (Ising H) on an n-qubit complex64 state: psi and lambda (2 x 2^n x 8 B,
+    64 GiB at 32 qubits) resident in HBM.  Reports the step time and the
+    fused passes' achieved bandwidth (algorithmic bytes over CUDA-event time)."""
+    from paper_2511_19291_gb300 import workloads as W
+    w = W.workload_qft(n, layers)
+    c = S.Circuit(w.circuit, device=dev)
+    obs = S.Observable(w.terms)
+    psi = S.State(n, torch.complex64, dev)
+    lam = S.State(n, torch.complex64, dev)
+    p = torch.tensor(w.params, dtype=torch.float64, device=dev)
+    g = torch.zeros(w.circuit.n_params, dtype=torch.float64, device=dev)
+    e = torch.zeros((), dtype=torch.float64, device=dev)
+
+    def step():
+        psi.reset(0)
+        S.apply(psi, c, p)
+        S.expval(psi, obs, out=e)
+        S.backward(psi, lam, c, p, obs, g)
+
+    step()  # compiles the pass kernels
+    barrier()
+    S.profile_enable(True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    step()
+    b.record()
+    barrier()
+    ms = a.elapsed_time(b)
+    prof = {q["name"]: q for q in S.profile_read()}
+    S.profile_enable(False)
+    peak, src = peaks()
+    out = {"n_qubits": n, "layers": layers, "gates": len(w.circuit.gates), "n_params": w.circuit.n_params,
+           "ms_per_grad_eval": ms, "energy": float(e.item()), "peak": peak, "peak_source": f"{src} hbm_gbs"}
+    for k in ("tile_fwd", "tile_adj"):
+        if k in prof and prof[k]["ms"] > 0:
+            gbs = prof[k]["bytes"] / (prof[k]["ms"] / 1000.0) / 1e9
+            out[k] = {"launches": prof[k]["launches"], "ms": prof[k]["ms"], "gbs": gbs, "frac": gbs / peak}
+    del psi, lam
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------- our path
 def main():
     args = parse()
@@ -460,6 +507,13 @@ def main():
     if args.batch_count > 0:
         batched = batch_bench(S, torch, dev, args.batch_count, barrier)
 
+    qft = None
+    if args.qft_n > 0:
+        del psi, lam
+        torch.cuda.empty_cache()
+        qft = qft_bench(S, torch, dev, args.qft_n, barrier)
+        psi = S.State(n, torch.complex64, dev)
+
     # sanity of the numbers being timed: E of this step against a fresh forward
     psi.reset(0)
     S.apply(psi, circ, params)
@@ -509,6 +563,7 @@ def main():
         "sweep": sweep,
         "batched": batched,
         "tc_block": tcb,
+        "qft32": qft,
         "clocks": clk.summary(),
         "kernels": kernels,
         "energy": e_check,

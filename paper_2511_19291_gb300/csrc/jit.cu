@@ -227,11 +227,18 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
 // the index is (base ^ u) + (roff[j] & ~TB): the sum of a per-thread value and
 // a constant with disjoint bits.  Each distinct u gets one XOR; the constant
 // becomes the access's immediate offset.
+//
+// complex64: when every lane and warp entry is even and registers j and j ^ 1
+// sit at offsets r and r ^ 1 with r even (local bit 0 is register bit 0 and
+// the map keeps it), the pair is one 16-byte access (tile_ld2 / tile_st2).
 void emit_access(std::string &o, const char *fn, const char *base, const uint16_t *lo, const uint16_t *hi,
-                 const uint16_t *roff) {
+                 const uint16_t *roff, int dt) {
     uint32_t tb = 0;
     for (int l = 0; l < 32; ++l) tb |= lo[l];
     for (int w = 0; w < TILE_THREADS / 32; ++w) tb |= hi[w];
+    bool pair = dt == 0 && !(tb & 1u);
+    for (int j = 0; j < (1 << TILE_R) && pair; j += 2)
+        pair = !(roff[j] & 1u) && roff[j + 1] == (roff[j] ^ 1u);
     std::vector<uint32_t> us;
     int idx[1 << TILE_R];
     for (int j = 0; j < (1 << TILE_R); ++j) {
@@ -243,6 +250,12 @@ void emit_access(std::string &o, const char *fn, const char *base, const uint16_
             put(o, "const uint32_t %s%d = %s ^ %uu;\n", base, k, base, u);
         }
         idx[j] = k;
+    }
+    if (pair) {
+        for (int j = 0; j < (1 << TILE_R); j += 2)
+            put(o, "%s2<TV, KADJ>(c, a, b, %d, %d, %s%d + %uu);\n", fn, j, j + 1, base, idx[j],
+                (unsigned)(roff[j] & ~tb));
+        return;
     }
     for (int j = 0; j < (1 << TILE_R); ++j)
         put(o, "%s<TV, KADJ>(c, a, b, %d, %s%d + %uu);\n", fn, j, base, idx[j], (unsigned)(roff[j] & ~tb));
@@ -267,7 +280,7 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
         // the reverse sweep loads through the store map and stores through the load map
         const uint16_t *rl = adj ? st.st_roff : st.ld_roff;
         const uint16_t *rs = adj ? st.ld_roff : st.st_roff;
-        emit_access(o, "tile_ld", "bl", adj ? st.st_lo : st.ld_lo, adj ? st.st_hi : st.ld_hi, rl);
+        emit_access(o, "tile_ld", "bl", adj ? st.st_lo : st.ld_lo, adj ? st.st_hi : st.ld_hi, rl, dt);
         if (!adj) {
             for (int k = st.op_begin; k < st.op_end; ++k) emit_apply(o, D, D.ops[k], false);
         } else {
@@ -278,7 +291,7 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
         }
         if (st.sync_mid) o += "tile_sync(c);\n";
         o += "const uint32_t bs = stage_base_st<KADJ>(tl, c.lane, c.warp);\n";
-        emit_access(o, "tile_st", "bs", adj ? st.ld_lo : st.st_lo, adj ? st.ld_hi : st.st_hi, rs);
+        emit_access(o, "tile_st", "bs", adj ? st.ld_lo : st.st_lo, adj ? st.ld_hi : st.st_hi, rs, dt);
         if (si == h.n_stages - 1) o += "fence_async_smem();\n";
         o += "tile_sync(c);\n}\n";
     }

@@ -373,8 +373,11 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
             }
         st.end = (int)order.size();
         if (st.end == st.begin) return false;  // cannot happen: the first ready gate always fits
-        // pad the register set with the highest free local bits (they do not
-        // help bank spreading as lane bits)
+        // pad the register set: local bit 0 first (registers j and j ^ 1 then
+        // hold adjacent amplitudes, one 16-byte access for complex64), then
+        // the highest free local bits (they do not help bank spreading as
+        // lane bits)
+        if ((int)rs.size() < TILE_R && std::find(rs.begin(), rs.end(), 0) == rs.end()) rs.push_back(0);
         for (int b = TILE_K - 1; b >= 0 && (int)rs.size() < TILE_R; --b)
             if (std::find(rs.begin(), rs.end(), b) == rs.end()) rs.push_back(b);
         std::sort(rs.begin(), rs.end());

@@ -636,6 +636,37 @@ __device__ __forceinline__ void tile_st(const TileCtx<V> &c, const V (&a)[NR], c
     }
 }
 
+// Registers j0 and j1 of a stage whose amplitudes are adjacent in the tile
+// (indices ad and ad + 1, ad even: one 16-byte chunk of complex64 values)
+// with one 16-byte shared-memory access per state.
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_ld2(const TileCtx<V> &c, V (&a)[NR], V (&b)[NR], int j0, int j1, uint32_t ad) {
+    static_assert(sizeof(V) == 8, "pairs of complex64 amplitudes");
+    int *err = c.err;
+    (void)err;
+    if (TQD_IDX_OK(ad + 1, (uint32_t)(1 << TILE_K))) {
+        const float4 x = *reinterpret_cast<const float4 *>(c.tile_a + ad);
+        a[j0] = make_float2(x.x, x.y);
+        a[j1] = make_float2(x.z, x.w);
+        if (ADJ) {
+            const float4 y = *reinterpret_cast<const float4 *>(c.tile_b + ad);
+            b[j0] = make_float2(y.x, y.y);
+            b[j1] = make_float2(y.z, y.w);
+        }
+    }
+}
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_st2(const TileCtx<V> &c, const V (&a)[NR], const V (&b)[NR], int j0, int j1,
+                                         uint32_t ad) {
+    static_assert(sizeof(V) == 8, "pairs of complex64 amplitudes");
+    int *err = c.err;
+    (void)err;
+    if (TQD_IDX_OK(ad + 1, (uint32_t)(1 << TILE_K))) {
+        *reinterpret_cast<float4 *>(c.tile_a + ad) = make_float4(a[j0].x, a[j0].y, a[j1].x, a[j1].y);
+        if (ADJ) *reinterpret_cast<float4 *>(c.tile_b + ad) = make_float4(b[j0].x, b[j0].y, b[j1].x, b[j1].y);
+    }
+}
+
 // The generic stage runner: interprets the pass's stage and op lists.
 template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
     __device__ __forceinline__ void init(const TileCtx<V> &) {}
