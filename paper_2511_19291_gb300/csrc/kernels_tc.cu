@@ -30,7 +30,7 @@ constexpr int TC_N = 64;                   // columns per tile
 constexpr int TC_KB = TC_K / 32;           // 128-byte K blocks
 constexpr int TC_A_BYTES = 128 * TC_K * 4; // 64 KiB
 constexpr int TC_B_BYTES = TC_N * TC_K * 4;  // 32 KiB
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 
 // Byte offset of element (row, k) of a K-major operand with `rows` rows:
 // K blocks of 128 bytes, 8-row swizzle atoms of 1024 bytes, 16-byte chunk
@@ -124,6 +124,13 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Pipelined over the block's tiles (one block per SM): two TMA buffers for
+// the state tiles and two TMEM accumulators.  Iteration i: wait for tile i,
+// split it (lo half into Blo), issue tile i's 48 MMAs into accumulator i % 2,
+// write tile i - 1's result from the other accumulator to HBM while they
+// run, wait for them, then refill tile i's buffer with tile i + 2.  So the
+// MMAs of one tile overlap the previous tile's epilogue and the loads of the
+// next two tiles.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_apply(const __grid_constant__ CUtensorMap map, float *__restrict__ state, const float *__restrict__ a_hi,
                const float *__restrict__ a_lo, uint64_t n_tiles, int *__restrict__ err) {
@@ -132,11 +139,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *sm = tc_raw + pad;
     float *Ahi = reinterpret_cast<float *>(sm);
     float *Alo = reinterpret_cast<float *>(sm + TC_A_BYTES);
-    float *B = reinterpret_cast<float *>(sm + 2 * TC_A_BYTES);
-    float *Blo = reinterpret_cast<float *>(sm + 2 * TC_A_BYTES + TC_B_BYTES);
-    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + 2 * TC_A_BYTES + 2 * TC_B_BYTES);
-    uint64_t *bar_mma = bar_ld + 1;
-    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_ld + 2);
+    float *Bbuf = reinterpret_cast<float *>(sm + 2 * TC_A_BYTES);                  // 2 tiles
+    float *Blo = reinterpret_cast<float *>(sm + 2 * TC_A_BYTES + 2 * TC_B_BYTES);  // 1 tile
+    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + 2 * TC_A_BYTES + 3 * TC_B_BYTES);  // [2]
+    uint64_t *bar_mma = bar_ld + 2;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_ld + 3);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     {
@@ -149,6 +156,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_ld)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_ld + 1)));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_mma)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -156,7 +164,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_sptr(slot)),
-                     "r"(TC_N));
+                     "r"(2 * TC_N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -165,68 +173,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t taddr = *slot;
     // instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    uint32_t ph_ld = 0, ph_mma = 0;
-    bool failed = false;
-
-    for (uint64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-        if (tid == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_sptr(bar_ld)),
-                         "r"((uint32_t)TC_B_BYTES)
-                         : "memory");
-            const uint64_t m = reinterpret_cast<uint64_t>(&map);
-            for (int kb = 0; kb < TC_KB; ++kb) {
-                const int c0 = kb * 32, c1 = (int)(tile * TC_N);
-                asm volatile(
-                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                    ::"r"(tc_sptr(B) + kb * TC_N * 128), "l"(m), "r"(c0), "r"(c1), "r"(tc_sptr(bar_ld))
-                    : "memory");
-            }
+    // this block's tiles: blockIdx.x + k * gridDim.x, k < n_local
+    const uint64_t n_local = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto issue_load = [&](uint64_t k) {
+        const int b = (int)(k & 1);
+        const uint64_t tile = blockIdx.x + k * gridDim.x;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_sptr(bar_ld + b)),
+                     "r"((uint32_t)TC_B_BYTES)
+                     : "memory");
+        const uint64_t m = reinterpret_cast<uint64_t>(&map);
+        for (int kb = 0; kb < TC_KB; ++kb) {
+            const int c0 = kb * 32, c1 = (int)(tile * TC_N);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                ::"r"(tc_sptr(Bbuf + b * (TC_B_BYTES / 4)) + kb * TC_N * 128), "l"(m), "r"(c0), "r"(c1),
+                "r"(tc_sptr(bar_ld + b))
+                : "memory");
         }
-        if (!tc_wait(bar_ld, ph_ld)) {
-            if (tid == 0) atomicExch(err, 1);
-            failed = true;
-            break;
-        }
-        ph_ld ^= 1u;
-        // lo half of the state tile (same positions as B)
-        for (int i = tid; i < TC_B_BYTES / 4; i += TC_THREADS) {
-            const float x = B[i];
-            Blo[i] = x - tf32_hi(x);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            int issued = 0;
-            for (int p = 0; p < 3; ++p) {  // hi*hi, hi*lo, lo*hi
-                const float *a = p == 2 ? Alo : Ahi;
-                const float *b = p == 1 ? Blo : B;
-                for (int s = 0; s < TC_K / 8; ++s) {
-                    const uint64_t ad = tc_desc(tc_sptr(a) + (s >> 2) * 128 * 128 + (s & 3) * 32);
-                    const uint64_t bd = tc_desc(tc_sptr(b) + (s >> 2) * TC_N * 128 + (s & 3) * 32);
-                    const uint32_t acc = issued > 0;
-                    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}" ::"r"(taddr),
-                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-                    ++issued;
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                tc_sptr(bar_mma)));
-        }
-        if (!tc_wait(bar_mma, ph_mma)) {
-            if (tid == 0) atomicExch(err, 1);
-            failed = true;
-            break;
-        }
-        ph_mma ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // epilogue: warp w holds rows 32w..32w+31 (floats of a column) of every column
+    };
+    // result of tile k (accumulator k % 2) to HBM: warp w reads TMEM lanes
+    // 32 (w % 4) .. 32 (w % 4) + 31 (floats of a column) of columns
+    // 32 (w / 4) .. 32 (w / 4) + 31
+    auto epilogue = [&](uint64_t k) {
+        const uint64_t tile = blockIdx.x + k * gridDim.x;
         float *out = state + tile * TC_N * TC_K;
-#pragma unroll
-        for (int c = 0; c < TC_N / 32; ++c) {
+        const uint32_t tcol = taddr + (uint32_t)(k & 1) * TC_N;
+        const int q = warp & 3;
+        {
+            const int c = warp >> 2;
             uint32_t r[32];
-            const uint32_t ta = taddr + ((uint32_t)(warp * 32) << 16) + c * 32;
+            const uint32_t ta = tcol + ((uint32_t)(q * 32) << 16) + c * 32;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -238,14 +214,88 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) out[(c * 32 + j) * TC_K + warp * 32 + lane] = __uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) out[(c * 32 + j) * TC_K + q * 32 + lane] = __uint_as_float(r[j]);
         }
+    };
+
+    if (tid == 0) {
+        if (n_local > 0) issue_load(0);
+        if (n_local > 1) issue_load(1);
+    }
+    uint32_t ph_ld = 0, ph_mma = 0;  // bit b: phase parity of load barrier b
+    bool failed = false;
+    // Thread 0 waits (bounded) and the block learns the outcome at the
+    // barrier, so every thread takes the same branch; the others then acquire
+    // the completed phase themselves.
+    // (one flag per barrier kind: a flag is rewritten only after two more
+    // block barriers, so every thread has read it by then)
+    __shared__ int s_ok[2];
+    auto wait_all = [&](uint64_t *bar, uint32_t parity, int which) -> bool {
+        if (tid == 0) s_ok[which] = tc_wait(bar, parity) ? 1 : 0;
+        __syncthreads();
+        const bool ok = s_ok[which] != 0;
+        if (ok && tid != 0) tc_wait(bar, parity);
+        return ok;
+    };
+    for (uint64_t k = 0; k < n_local; ++k) {
+        const int b = (int)(k & 1);
+        const float *B = Bbuf + b * (TC_B_BYTES / 4);
+        if (!wait_all(bar_ld + b, (ph_ld >> b) & 1u, 0)) {
+            failed = true;
+            break;
+        }
+        ph_ld ^= 1u << b;
+        // lo half of the state tile (same positions as B, 16 bytes at a
+        // time); Blo is free: the previous tile's MMAs completed before the
+        // last iteration ended
+        for (int i = tid; i < TC_B_BYTES / 16; i += TC_THREADS) {
+            const float4 x = reinterpret_cast<const float4 *>(B)[i];
+            reinterpret_cast<float4 *>(Blo)[i] =
+                make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z), x.w - tf32_hi(x.w));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const uint32_t dcol = taddr + (uint32_t)b * TC_N;
+            // operand descriptors: the start-address field (bits 0..13, in
+            // 16-byte units) of each K step is the base plus a constant
+            const uint64_t dahi = tc_desc(tc_sptr(Ahi)), dalo = tc_desc(tc_sptr(Alo));
+            const uint64_t dbhi = tc_desc(tc_sptr(B)), dblo = tc_desc(tc_sptr(Blo));
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {  // hi*hi, hi*lo, lo*hi
+                const uint64_t da = p == 2 ? dalo : dahi;
+                const uint64_t db = p == 1 ? dblo : dbhi;
+#pragma unroll
+                for (int s = 0; s < TC_K / 8; ++s) {
+                    const uint64_t ad = da + (uint64_t)(((s >> 2) * 128 * 128 + (s & 3) * 32) >> 4);
+                    const uint64_t bd = db + (uint64_t)(((s >> 2) * TC_N * 128 + (s & 3) * 32) >> 4);
+                    const uint32_t acc = (p | s) != 0;
+                    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}" ::"r"(dcol),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc_sptr(bar_mma)));
+        }
+        // the previous tile's result leaves while these MMAs run
+        if (k > 0) epilogue(k - 1);
+        if (!wait_all(bar_mma, ph_mma, 1)) {
+            failed = true;
+            break;
+        }
+        ph_mma ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // tile k's buffer (read by the MMAs just completed) takes tile k + 2
+        if (tid == 0 && k + 2 < n_local) issue_load(k + 2);
     }
+    if (!failed && n_local > 0) epilogue(n_local - 1);
+    if (failed && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_N));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * TC_N));
 }
 
 // ------------------------------------------------------------------- host
@@ -287,12 +337,13 @@ cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock 
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const int smem = 2 * TC_A_BYTES + 2 * TC_B_BYTES + 1024 + 64;
+    const int smem = 2 * TC_A_BYTES + 3 * TC_B_BYTES + 1024 + 64;
     static std::once_flag once;
     std::call_once(once, [&] { cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); });
     const uint64_t tiles = cols / TC_N;
     uint64_t grid = (uint64_t)device_sm_count();
     if (grid > tiles) grid = tiles;
+    if (c->opts.max_blocks && grid > c->opts.max_blocks) grid = c->opts.max_blocks;
     ProfScope ps(PK_TC_BLOCK, (double)((uint64_t)8 << psi->n) * 2.0, s);
     k_tc_apply<<<(int)grid, TC_THREADS, smem, s>>>(map, (float *)psi->amps, blk.d_ahi, blk.d_alo, tiles, c->d_err);
     return cudaGetLastError();

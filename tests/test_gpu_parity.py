@@ -312,13 +312,25 @@ def tc_circuit(seed, n, blocks):
 
 @pytest.mark.parametrize("n,blocks,seed", [(12, 2, 1), (14, 3, 2), (17, 2, 3)])
 def test_tensor_core_blocks(n, blocks, seed):
+    tensor_core_case(n, blocks, seed)
+
+
+@pytest.mark.parametrize("n,blocks,max_blocks,seed", [(15, 2, 2, 4), (17, 3, 3, 5), (16, 1, 1, 6)])
+def test_tensor_core_blocks_pipelined(n, blocks, max_blocks, seed):
+    """Few blocks, so that each block runs many 64-column tiles through the
+    double-buffered loads and accumulators (tile k's MMAs overlapping tile
+    k - 1's epilogue and the loads of tiles k + 1, k + 2)."""
+    tensor_core_case(n, blocks, seed, max_blocks=max_blocks)
+
+
+def tensor_core_case(n, blocks, seed, **kw):
     """Fused 6-qubit blocks on the tensor cores (split-precision TF32) in the
     forward pass; the reverse sweep runs the same gates through tile passes."""
     S = sim()
     circ, params = tc_circuit(8000 + seed, n, blocks)
     terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(seed), n, 5)
     S.profile_enable(True)
-    st, c, p = gpu_state(circ, params, "tc", "c64")
+    st, c, p = gpu_state(circ, params, "tc", "c64", **kw)
     torch.cuda.synchronize()
     prof = {q["name"]: q for q in S.profile_read()}
     S.profile_enable(False)
@@ -333,5 +345,5 @@ def test_tensor_core_blocks(n, blocks, seed):
     ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4, hnorm=W.observable_l1(terms))
     assert ok, worst
     # complex128 states take the tile path for the same plan
-    st2, _, _ = gpu_state(circ, params, "tc", "c128")
+    st2, _, _ = gpu_state(circ, params, "tc", "c128", **kw)
     np.testing.assert_allclose(to_numpy(st2), ref, atol=1e-12, rtol=0)
