@@ -3,8 +3,9 @@
 
 One step = one gradient evaluation of the 26-qubit, 20-layer hardware-efficient
 ansatz (1040 angles, complex64 amplitudes) with the open-chain Ising
-observable: reset |0...0>, apply the circuit, E = <H>, lambda = H psi, reverse
-sweep with the angle derivatives.  Inputs (angles) are resident in HBM during
+observable, through tqd_value_and_grad: reset |0...0>, apply the circuit,
+lambda = H psi with E = Re <psi|lambda> read off its last pass, reverse sweep
+with the angle derivatives.  Inputs (angles) are resident in HBM during
 the timed region; the 512 MiB state is larger than L2, so no flush is needed.
 
 The JSON line reports grad-evals/s of the fused plan (value), the
@@ -367,9 +368,7 @@ def qft_bench(S, torch, dev, n, barrier, layers=8):
 
     def step():
         psi.reset(0)
-        S.apply(psi, c, p)
-        S.expval(psi, obs, out=e)
-        S.backward(psi, lam, c, p, obs, g)
+        S.value_and_grad(psi, lam, c, p, obs, e, g)
 
     step()  # compiles the pass kernels
     barrier()
@@ -426,10 +425,10 @@ def main():
     e_out = torch.zeros((), dtype=torch.float64, device=dev)
 
     def step(c):
+        # one gradient evaluation: psi <- U|0...0>, E = <H>, dE/dtheta (the
+        # energy read off lambda = H psi, which the reverse sweep needs)
         psi.reset(0)
-        S.apply(psi, c, params)
-        S.expval(psi, obs, out=e_out)
-        S.backward(psi, lam, c, params, obs, grads)
+        S.value_and_grad(psi, lam, c, params, obs, e_out, grads)
 
     def barrier():
         if world > 1:

@@ -257,6 +257,18 @@ tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *ci
 tqd_status tqd_expval_noalloc(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms,
                               double *dev_out, void *stream);
 
+/* One gradient evaluation in one call: psi <- U psi (as tqd_apply_circuit),
+ * E = <psi_L|H|psi_L> for H = sum_j coeff_j P_j written to dev_energy[0]
+ * (device, FP64), and the adjoint gradient of E added to dev_grads (as
+ * tqd_backward with unit weights and grad_scale 1); on return psi holds its
+ * input state again and lambda holds U^dagger H psi_L.  E is read off
+ * lambda = H psi_L as Re <psi_L|lambda>, the seed the reverse sweep needs
+ * anyway (Sec. 2.2.1, Sec. 4.4), so no separate expectation pass runs; it
+ * equals tqd_expval's value up to rounding. */
+tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circuit *circuit,
+                              const double *dev_params, const tqd_pauli_term *terms, size_t n_terms,
+                              double *dev_energy, double *dev_grads, void *stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent circuits of uneven width and depth (the batch dimension of

@@ -393,4 +393,24 @@ tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *c,
     return TQD_OK;
 }
 
+tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circuit *c, const double *dev_params,
+                              const tqd_pauli_term *terms, size_t n_terms, double *dev_energy, double *dev_grads,
+                              void *stream) {
+    CHECK_ARG(psi != nullptr && lambda != nullptr && c != nullptr, "tqd_value_and_grad: NULL handle");
+    CHECK_ARG(psi != lambda && psi->amps != lambda->amps, "tqd_value_and_grad: lambda must not alias psi");
+    CHECK_ARG(psi->n == c->n && lambda->n == c->n, "tqd_value_and_grad: qubit counts differ");
+    CHECK_ARG(psi->dtype == lambda->dtype, "tqd_value_and_grad: psi and lambda dtypes differ");
+    CHECK_ARG(c->n_params == 0 || dev_params != nullptr, "tqd_value_and_grad: dev_params is NULL");
+    CHECK_ARG(c->n_params == 0 || dev_grads != nullptr, "tqd_value_and_grad: dev_grads is NULL");
+    CHECK_ARG(dev_energy != nullptr, "tqd_value_and_grad: dev_energy is NULL");
+    tqd_status st = check_terms(psi, terms, n_terms, "tqd_value_and_grad");
+    if (st != TQD_OK) return st;
+    GUARD(psi->device);
+    const cudaStream_t s = (cudaStream_t)stream;
+    CHECK_CUDA(run_forward(psi, c, dev_params, s));
+    CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(terms, n_terms), nullptr, 1.0, dev_grads, s,
+                            dev_energy, true));
+    return TQD_OK;
+}
+
 }  // extern "C"

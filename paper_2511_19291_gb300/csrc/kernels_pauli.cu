@@ -328,17 +328,39 @@ cudaError_t launch_expval(const tqd_state *st, const std::vector<PauliGroup> &gr
     return expval_t<double2>(w, groups, n_terms, mode, dev_out, s);
 }
 
+// Re <psi|lam> per block (FP64), for the expectation value taken from
+// lambda = H psi.
+template <typename V>
+__global__ void __launch_bounds__(PT) k_re_dot(const V *__restrict__ psi, const V *__restrict__ lam, uint64_t N,
+                                               double *__restrict__ partials) {
+    __shared__ double sh[PT / 32];
+    double acc = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)PT + threadIdx.x; i < N; i += (uint64_t)gridDim.x * PT)
+        acc += (double)re_cdot(psi[i], lam[i]);
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
 template <typename V>
 static cudaError_t apply_obs_t(const tqd_state *psi, const std::vector<PauliGroup> &groups,
-                               const double *weights, double scale, tqd_state *out, cudaStream_t s) {
+                               const double *weights, double scale, tqd_state *out, double *dev_energy,
+                               cudaStream_t s) {
     const int n = psi->n;
     const uint64_t N = (uint64_t)1 << n;
     const int grid = stream_grid(N / 2 > 0 ? N / 2 : 1, PT);
     int accumulate = 0;
     std::vector<int> left;
     const std::vector<PauliTileDesc> tiles = plan_pauli_tiles(groups, n, &left);
+    // E = Re <psi|out> from the last tile launch (complex64, nothing after it)
+    // or from a separate pass over both states
+    const bool fused_e = dev_energy && sizeof(V) == 8 && left.empty() && !tiles.empty();
+    const int egrid = fused_e ? pauli_tile_grid(n, psi->dtype) : grid;
+    if (dev_energy) {
+        cudaError_t e = ensure_work(out, (size_t)egrid, s);
+        if (e != cudaSuccess) return e;
+    }
     if (!tiles.empty()) {
-        cudaError_t e = launch_pauli_tile_apply(psi, tiles, weights, scale, out, false, s);
+        cudaError_t e = launch_pauli_tile_apply(psi, tiles, weights, scale, out, false, fused_e ? out->work : nullptr, s);
         if (e != cudaSuccess) return e;
         accumulate = 1;
     }
@@ -357,13 +379,22 @@ static cudaError_t apply_obs_t(const tqd_state *psi, const std::vector<PauliGrou
         cudaError_t e = cudaMemsetAsync(out->amps, 0, N * sizeof(V), s);
         if (e != cudaSuccess) return e;
     }
+    if (dev_energy) {
+        if (!fused_e) {
+            ProfScope ps(PK_EXPVAL, 2.0 * (double)N * sizeof(V), s);
+            k_re_dot<V><<<egrid, PT, 0, s>>>((const V *)psi->amps, (const V *)out->amps, N, out->work);
+        }
+        ProfScope ps(PK_REDUCE, 0.0, s);
+        k_sum_rows<<<1, PT, 0, s>>>(out->work, egrid, egrid, dev_energy);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_apply_observable(const tqd_state *psi, const std::vector<PauliGroup> &groups,
-                                    const double *dev_weights, double scale, tqd_state *out, cudaStream_t s) {
-    if (psi->dtype == TQD_C64) return apply_obs_t<float2>(psi, groups, dev_weights, scale, out, s);
-    return apply_obs_t<double2>(psi, groups, dev_weights, scale, out, s);
+                                    const double *dev_weights, double scale, tqd_state *out, cudaStream_t s,
+                                    double *dev_energy) {
+    if (psi->dtype == TQD_C64) return apply_obs_t<float2>(psi, groups, dev_weights, scale, out, dev_energy, s);
+    return apply_obs_t<double2>(psi, groups, dev_weights, scale, out, dev_energy, s);
 }
 
 }  // namespace tqd

@@ -460,11 +460,15 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
 
 // out (+)= scale * sum_j w_j c_j P_j psi over the launch's groups (complex64):
 // out_b += D_x(b ^ x) psi_{b ^ x} per group.
+// eparts (may be null): the launch completes the output, and each block also
+// writes its share of Re <psi|out> (the expectation value when out = H psi).
 __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restrict__ psi, float2 *__restrict__ out,
                                                           const Pauli2Desc Dg, const double *__restrict__ weights,
-                                                          double scale, int accumulate) {
+                                                          double scale, int accumulate, double *__restrict__ eparts) {
     __shared__ Pauli2Smem S;
     __shared__ P2Origin O;
+    __shared__ double sh[PTHR / 32];
+    double eacc = 0;
     extern __shared__ __align__(16) unsigned char pt_dyn[];
     float2 *bufs = reinterpret_cast<float2 *>(pt_dyn);
     p2_origin_tables(O, Dg.P);
@@ -578,7 +582,17 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
         float2 *wrow = out + (origin | (tid & 15u));
 #pragma unroll
         for (int r = 0; r < PPER; ++r) wrow[S.hoff[(r * PTHR + tid) >> 4]] = o[r];
+        if (eparts) {
+            float2 e2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < PPER; ++r) e2 = f2_fma(tile[r * PTHR + tid], o[r], e2);  // Re(conj(psi) out)
+            eacc += (double)e2.x + (double)e2.y;
+        }
         __syncthreads();
+    }
+    if (eparts) {
+        const double tot = block_sum(eacc, sh);
+        if (threadIdx.x == 0) eparts[blockIdx.x] = tot;
     }
 }
 
@@ -761,7 +775,7 @@ int pauli_tile_grid(int n, int dtype) { return tile_grid_pauli(n, dtype); }
 
 static cudaError_t tile_apply_c64(const tqd_state *psi, const std::vector<PauliTileDesc> &launches,
                                   const double *weights, double scale, tqd_state *out, bool accumulate,
-                                  cudaStream_t s) {
+                                  double *eparts, cudaStream_t s) {
     const int grid = tile_grid_pauli(psi->n, TQD_C64);
     allow_tile_smem(k_pauli2_apply, 2 * PTS * sizeof(float2));
     const double N = (double)((uint64_t)1 << psi->n) * sizeof(float2);
@@ -769,8 +783,9 @@ static cudaError_t tile_apply_c64(const tqd_state *psi, const std::vector<PauliT
         const Pauli2Desc d = make_pauli2(launches[i]);
         const int acc = (accumulate || i > 0) ? 1 : 0;
         ProfScope ps(PK_APPLY_OBS, N * (acc ? 3 : 2), s);
+        double *ep = i + 1 == launches.size() ? eparts : nullptr;
         k_pauli2_apply<<<grid, PTHR, 2 * PTS * sizeof(float2), s>>>((const float2 *)psi->amps, (float2 *)out->amps, d,
-                                                                    weights, scale, acc);
+                                                                    weights, scale, acc, ep);
     }
     return cudaGetLastError();
 }
@@ -794,8 +809,8 @@ static cudaError_t tile_apply_t(const tqd_state *psi, const std::vector<PauliTil
 
 cudaError_t launch_pauli_tile_apply(const tqd_state *psi, const std::vector<PauliTileDesc> &launches,
                                     const double *weights, double scale, tqd_state *out, bool accumulate,
-                                    cudaStream_t s) {
-    if (psi->dtype == TQD_C64) return tile_apply_c64(psi, launches, weights, scale, out, accumulate, s);
+                                    double *eparts, cudaStream_t s) {
+    if (psi->dtype == TQD_C64) return tile_apply_c64(psi, launches, weights, scale, out, accumulate, eparts, s);
     return tile_apply_t<double2>(psi, launches, weights, scale, out, accumulate, s);
 }
 

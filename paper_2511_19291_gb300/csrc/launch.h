@@ -35,10 +35,12 @@ cudaError_t launch_grad_finalize(const tqd_circuit *c, int nblk, double *dev_gra
 // Pauli sums.  mode 0: total E; mode 1: per-term values.
 cudaError_t launch_expval(const tqd_state *st, const std::vector<PauliGroup> &groups, int n_terms,
                           int mode, double *dev_out, cudaStream_t s);
-// out = scale * sum_j w_j c_j P_j psi.
+// out = scale * sum_j w_j c_j P_j psi.  dev_energy (may be null): also
+// Re <psi|out> into dev_energy[0] (the expectation value when the weights
+// and scale are 1); uses out's workspace.
 cudaError_t launch_apply_observable(const tqd_state *psi, const std::vector<PauliGroup> &groups,
                                     const double *dev_weights, double scale, tqd_state *out,
-                                    cudaStream_t s);
+                                    cudaStream_t s, double *dev_energy = nullptr);
 
 // Grows st->work to at least `len` doubles (stream-ordered).
 cudaError_t ensure_work(tqd_state *st, size_t len, cudaStream_t s);

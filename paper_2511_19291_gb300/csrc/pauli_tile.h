@@ -40,8 +40,10 @@ int pauli_tile_grid(int n, int dtype);
 cudaError_t launch_pauli_tile_expval(const tqd_state *st, const std::vector<PauliTileDesc> &launches,
                                      double *partials, int pblk, cudaStream_t s);
 // out = (accumulate ? out : 0) + scale * sum w_j c_j P_j psi over the launches' groups.
+// eparts (complex64 only, else ignored; may be null): the last launch also
+// writes each block's share of Re <psi|out> to eparts[block].
 cudaError_t launch_pauli_tile_apply(const tqd_state *psi, const std::vector<PauliTileDesc> &launches,
                                     const double *weights, double scale, tqd_state *out, bool accumulate,
-                                    cudaStream_t s);
+                                    double *eparts, cudaStream_t s);
 
 }  // namespace tqd

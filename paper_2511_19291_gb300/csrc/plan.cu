@@ -205,10 +205,10 @@ cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_
 
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
-                         double *dev_grads, cudaStream_t s) {
-    cudaError_t e = launch_prep(c, dev_params, s);
+                         double *dev_grads, cudaStream_t s, double *dev_energy, bool prepared) {
+    cudaError_t e = prepared ? cudaSuccess : launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
-    e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s);
+    e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s, dev_energy);
     if (e != cudaSuccess) return e;
     if (c->fused) {
         for (int p = (int)c->tile_passes.size() - 1; p >= 0; --p) {

@@ -19,8 +19,10 @@ void release_circuit(tqd_circuit *c);
 cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s);
 
 // lambda = scale * H psi, reverse sweep, gradients accumulated into dev_grads.
+// dev_energy (may be null): Re <psi|lambda> before the sweep.  prepared: the
+// gate matrices of dev_params are already on the device (skip the prep).
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
-                         double *dev_grads, cudaStream_t s);
+                         double *dev_grads, cudaStream_t s, double *dev_energy = nullptr, bool prepared = false);
 
 }  // namespace tqd

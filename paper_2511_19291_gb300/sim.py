@@ -286,6 +286,24 @@ def backward(psi: State, lam: State, circuit: Circuit, params: torch.Tensor | No
     return grads
 
 
+def value_and_grad(psi: State, lam: State, circuit: Circuit, params: torch.Tensor | None, obs,
+                   energy: torch.Tensor | None = None, grads: torch.Tensor | None = None):
+    """One gradient evaluation (tqd_value_and_grad): psi <- U psi, energy =
+    <psi|H|psi> (a float64 scalar tensor on the device), grads += dE/dparams;
+    psi is restored to its input state.  Returns (energy, grads)."""
+    obs = as_observable(obs)
+    if energy is None:
+        energy = torch.zeros((), dtype=torch.float64, device=psi.device)
+    if grads is None:
+        grads = torch.zeros(max(circuit.n_params, 0), dtype=torch.float64, device=psi.device)
+    gptr = C.c_void_p(grads.data_ptr()) if circuit.n_params else None
+    with torch.cuda.device(psi.device):
+        _lib.check(_L().tqd_value_and_grad(psi.handle, lam.handle, circuit.handle,
+                                           _params_ptr(params, circuit.n_params), obs.ptr, len(obs),
+                                           C.c_void_p(energy.data_ptr()), gptr, _stream(psi.device)))
+    return energy, grads
+
+
 # ------------------------------------------------------------------ autograd
 class _ExpvalFn(torch.autograd.Function):
     """E(theta) = <psi_L|H|psi_L>.  Forward keeps only theta and psi_L; backward

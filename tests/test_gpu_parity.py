@@ -347,3 +347,38 @@ def tensor_core_case(n, blocks, seed, **kw):
     # complex128 states take the tile path for the same plan
     st2, _, _ = gpu_state(circ, params, "tc", "c128", **kw)
     np.testing.assert_allclose(to_numpy(st2), ref, atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n,layers,extra", [(13, 3, False), (15, 2, True)])
+def test_value_and_grad(mode, dtype, n, layers, extra):
+    """tqd_value_and_grad (E read off lambda = H psi) against the oracle's
+    energy and parameter-shift gradient, and psi restored.  `extra` adds
+    Pauli strings that flip more than 8 qubits above qubit 3 (groups outside
+    the 12-qubit tiles: E then comes from a separate pass over psi and
+    lambda)."""
+    S = sim()
+    circ = W.hea_ansatz(n, layers)
+    params = W.config_rng(3).angles(circ.n_params)
+    terms = W.ising(n)
+    if extra:
+        wide = tuple((q, "X") for q in range(4, n)) + ((0, "Y"),)
+        terms = terms + [W.PauliTerm(0.3, wide)] + W.random_pauli_terms(W.SplitMix64(77), n, 4)
+    e_ref = oracle.energy(circ, params, terms)
+    g_ref = oracle.grad_param_shift(circ, params, terms)
+    c = S.Circuit(circ, mode=mode)
+    psi = S.State(n, DTYPES[dtype]).reset(0)
+    lam = S.State(n, DTYPES[dtype])
+    p = params_tensor(params)
+    for rep in range(2):  # twice in a row: the state comes back to |0...0>
+        e, g = S.value_and_grad(psi, lam, c, p, terms)
+        torch.cuda.synchronize()
+        assert abs(e.item() - e_ref) < E_TOL[dtype], (rep, e.item(), e_ref)
+        ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype],
+                               hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+        assert ok, worst
+    back = to_numpy(psi)
+    e0 = np.zeros(1 << n, dtype=complex)
+    e0[0] = 1
+    np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 200, rtol=0)
