@@ -407,6 +407,16 @@ tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circu
     if (st != TQD_OK) return st;
     GUARD(psi->device);
     const cudaStream_t s = (cudaStream_t)stream;
+    if (c->fused && c->prefix_passes < (int)c->tile_passes.size()) {
+        // the circuit ends with a permutation P (its tail passes): E and its
+        // gradient from psi' = U' psi (the gates before P) with
+        // H' = P^dagger H P; the tail passes never run
+        const std::vector<tqd_pauli_term> hp = conjugate_by_tail(c, terms, n_terms);
+        CHECK_CUDA(run_forward(psi, c, dev_params, s, c->prefix_passes));
+        CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(hp.data(), hp.size()), nullptr, 1.0,
+                                dev_grads, s, dev_energy, true, c->prefix_passes));
+        return TQD_OK;
+    }
     CHECK_CUDA(run_forward(psi, c, dev_params, s));
     CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(terms, n_terms), nullptr, 1.0, dev_grads, s,
                             dev_energy, true));

@@ -486,7 +486,8 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
     }
     c->opts.mode = TQD_PLAN_FUSED;
     assign_grad_slots(c);
-    std::vector<TilePlanPass> passes = plan_tile_passes(c);
+    int prefix = 0;
+    std::vector<TilePlanPass> passes = plan_fused(c, &prefix);
     for (auto &p : passes)
         if (!encode_tile_pass(c, p)) {
             set_error("tqd_jit_check: a pass could not be encoded");

@@ -61,6 +61,8 @@ tqd_status build_circuit(tqd_circuit *c) {
     c->d_err = nullptr;
     c->d_tile_desc = nullptr;
     c->fused = false;
+    c->prefix_passes = 0;
+    c->tail_gate = (int)c->gates.size();
 
     std::vector<std::vector<int>> by_param = assign_grad_slots(c);
     std::vector<int> ptr(c->n_params + 1, 0), slots;
@@ -105,7 +107,8 @@ tqd_status build_circuit(tqd_circuit *c) {
 
     // fused plan: tile passes, when the state holds at least one full tile
     if ((c->opts.mode == TQD_PLAN_FUSED || c->opts.mode == TQD_PLAN_TC) && c->n >= TILE_K && ng > 0) {
-        std::vector<TilePlanPass> passes = plan_tile_passes(c);
+        int prefix = 0;
+        std::vector<TilePlanPass> passes = plan_fused(c, &prefix);
         bool ok = !passes.empty();
         for (auto &p : passes) ok = ok && encode_tile_pass(c, p);
         if (ok) {
@@ -139,6 +142,8 @@ tqd_status build_circuit(tqd_circuit *c) {
                 p.tc = (int)c->tc_blocks.size() - 1;
             }
             c->tile_passes = std::move(passes);
+            c->prefix_passes = prefix;
+            c->tail_gate = permutation_tail(c);
             c->fused = true;
             c->n_passes = (int)c->tile_passes.size();
             c->launches_apply = c->n_passes + 1;
@@ -182,11 +187,13 @@ void release_circuit(tqd_circuit *c) {
     c->tc_blocks.clear();
 }
 
-cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s) {
+cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s,
+                        int pass_end) {
     cudaError_t e = launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
     if (c->fused) {
-        for (int p = 0; p < (int)c->tile_passes.size(); ++p) {
+        const int np = pass_end < 0 ? (int)c->tile_passes.size() : pass_end;
+        for (int p = 0; p < np; ++p) {
             const TilePlanPass &pp = c->tile_passes[p];
             if (pp.tc >= 0 && psi->dtype == TQD_C64)
                 e = launch_tc_block(psi, c, *(const TcBlock *)c->tc_blocks[pp.tc], s);
@@ -205,13 +212,14 @@ cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_
 
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
-                         double *dev_grads, cudaStream_t s, double *dev_energy, bool prepared) {
+                         double *dev_grads, cudaStream_t s, double *dev_energy, bool prepared, int pass_end) {
     cudaError_t e = prepared ? cudaSuccess : launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
     e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s, dev_energy);
     if (e != cudaSuccess) return e;
     if (c->fused) {
-        for (int p = (int)c->tile_passes.size() - 1; p >= 0; --p) {
+        const int np = pass_end < 0 ? (int)c->tile_passes.size() : pass_end;
+        for (int p = np - 1; p >= 0; --p) {
             e = launch_tile_pass(psi, lam, c, p, s);
             if (e != cudaSuccess) return e;
         }
@@ -225,6 +233,45 @@ cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, c
         if (e != cudaSuccess) return e;
     }
     return launch_grad_finalize(c, nblk, dev_grads, s);
+}
+
+std::vector<tqd_pauli_term> conjugate_by_tail(const tqd_circuit *c, const tqd_pauli_term *terms, size_t n_terms) {
+    std::vector<tqd_pauli_term> out(terms, terms + n_terms);
+    const int L = (int)c->gates.size();
+    for (auto &t : out) {
+        uint64_t x = t.xmask, z = t.zmask;
+        double coeff = t.coeff;
+        // P^dagger Q P with P = G_L ... G_tail: conjugate by the last gate first
+        for (int g = L - 1; g >= c->tail_gate; --g) {
+            const GateH &h = c->gates[g];
+            const int y0 = __builtin_popcountll(x & z);
+            if (h.kind == TQD_CNOT) {
+                // X_c -> X_c X_t, Z_t -> Z_c Z_t
+                const uint64_t cb = 1ull << h.w[0], tb = 1ull << h.w[1];
+                if (x & cb) x ^= tb;
+                if (z & tb) z ^= cb;
+            } else if (h.kind == TQD_SWAP) {
+                const uint64_t pb = 1ull << h.w[0], qb = 1ull << h.w[1];
+                auto sw = [&](uint64_t v) {
+                    const bool a = v & pb, b = v & qb;
+                    v &= ~(pb | qb);
+                    return v | (a ? qb : 0) | (b ? pb : 0);
+                };
+                x = sw(x);
+                z = sw(z);
+            } else {  // X_q: X_q Z^z X_q = (-1)^{z_q} Z^z
+                if ((z >> h.w[0]) & 1) coeff = -coeff;
+            }
+            // X^x Z^z keeps its order under these maps; the term's phase
+            // i^{|x & z|} becomes i^{|x' & z'|} times i^{d}, d even
+            const int d = (y0 - __builtin_popcountll(x & z)) & 3;
+            if (d == 2) coeff = -coeff;
+        }
+        t.xmask = x;
+        t.zmask = z;
+        t.coeff = coeff;
+    }
+    return out;
 }
 
 }  // namespace tqd

@@ -15,14 +15,23 @@ std::vector<std::vector<int>> assign_grad_slots(tqd_circuit *c);
 tqd_status build_circuit(tqd_circuit *c);
 void release_circuit(tqd_circuit *c);
 
-// psi <- U psi (prep + plain or fused passes).
-cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s);
+// psi <- U psi (prep + plain or fused passes); pass_end >= 0: only the fused
+// passes [0, pass_end).
+cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s,
+                        int pass_end = -1);
 
 // lambda = scale * H psi, reverse sweep, gradients accumulated into dev_grads.
 // dev_energy (may be null): Re <psi|lambda> before the sweep.  prepared: the
 // gate matrices of dev_params are already on the device (skip the prep).
+// pass_end >= 0: the sweep starts at fused pass pass_end - 1.
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
-                         double *dev_grads, cudaStream_t s, double *dev_energy = nullptr, bool prepared = false);
+                         double *dev_grads, cudaStream_t s, double *dev_energy = nullptr, bool prepared = false,
+                         int pass_end = -1);
+
+// The Pauli terms of P^dagger H P for the circuit's permutation tail P
+// (gates tail_gate.. in order): masks and signs after conjugation by each
+// CNOT, SWAP and X.  E = <P psi|H|P psi> = <psi|H'|psi>.
+std::vector<tqd_pauli_term> conjugate_by_tail(const tqd_circuit *c, const tqd_pauli_term *terms, size_t n_terms);
 
 }  // namespace tqd

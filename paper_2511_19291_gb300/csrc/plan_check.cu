@@ -178,7 +178,8 @@ tqd_status plan_check_host(tqd_circuit *c, const double *params, uint64_t seed, 
                            int *n_passes, int *n_stages) {
     c->opts.mode = TQD_PLAN_FUSED;
     assign_grad_slots(c);
-    std::vector<TilePlanPass> passes = plan_tile_passes(c);
+    int prefix = 0;
+    std::vector<TilePlanPass> passes = plan_fused(c, &prefix);
     if (passes.empty()) {
         set_error("tqd_plan_check: the circuit could not be planned into fused passes");
         return TQD_ERR_UNSUPPORTED;

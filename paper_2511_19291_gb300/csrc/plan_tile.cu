@@ -171,12 +171,16 @@ bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L) {
     return true;
 }
 
-std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c) {
+std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, int g_end) {
     const int n = c->n;
     const int L = (int)c->gates.size();
+    if (g_end < 0 || g_end > L) g_end = L;
     std::vector<TilePlanPass> passes;
+    // gates outside [g_begin, g_end) count as done
     std::vector<char> done(L, 0);
-    int first = 0;
+    for (int g = 0; g < L; ++g) done[g] = g < g_begin || g >= g_end;
+    int first = g_begin;
+    while (first < L && done[first]) ++first;
     while (first < L) {
         // --- tensor-core block: a long run of gates on qubits 0..5
         if (c->opts.mode == TQD_PLAN_TC) {
@@ -285,6 +289,28 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c) {
         }
         passes.push_back(P);
         while (first < L && done[first]) ++first;
+    }
+    return passes;
+}
+
+int permutation_tail(const tqd_circuit *c) {
+    int t = (int)c->gates.size();
+    while (t > 0 && is_perm_gate(c->gates[t - 1].kind)) --t;
+    return t;
+}
+
+std::vector<TilePlanPass> plan_fused(const tqd_circuit *c, int *prefix_passes) {
+    const int tail = permutation_tail(c), L = (int)c->gates.size();
+    std::vector<TilePlanPass> passes;
+    if (tail > 0) {
+        passes = plan_tile_passes(c, 0, tail);
+        if (passes.empty()) return passes;
+    }
+    *prefix_passes = (int)passes.size();
+    if (tail < L) {
+        std::vector<TilePlanPass> t = plan_tile_passes(c, tail, L);
+        if (t.empty()) return t;
+        for (auto &p : t) passes.push_back(std::move(p));
     }
     return passes;
 }

@@ -10,8 +10,17 @@ namespace tqd {
 
 bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L);
 // Empty result: the circuit cannot be planned into tiles (the caller falls
-// back to the gate-by-gate plan).
-std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c);
+// back to the gate-by-gate plan).  Plans gates [g_begin, g_end) (g_end < 0:
+// to the end).
+std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin = 0, int g_end = -1);
+
+// First gate of the circuit's permutation tail: the longest suffix of CNOT,
+// SWAP and X gates (gates.size() when the circuit does not end with one).
+int permutation_tail(const tqd_circuit *c);
+
+// The fused plan: the gates before the permutation tail, then the tail on
+// its own passes (*prefix_passes: the passes of the first part).
+std::vector<TilePlanPass> plan_fused(const tqd_circuit *c, int *prefix_passes);
 bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P);
 
 // Launch one pass (forward: lam == nullptr; reverse sweep with gradients

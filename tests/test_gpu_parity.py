@@ -382,3 +382,31 @@ def test_value_and_grad(mode, dtype, n, layers, extra):
     e0 = np.zeros(1 << n, dtype=complex)
     e0[0] = 1
     np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 200, rtol=0)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_value_and_grad_permutation_tail(dtype):
+    """A circuit ending in CNOT, SWAP and X gates: tqd_value_and_grad skips
+    the tail passes and conjugates the observable through them (Pauli
+    strings with X, Y and Z, so every sign rule is used)."""
+    S = sim()
+    n = 14
+    circ = W.hea_ansatz(n, 2)
+    tail = [W.Gate("SWAP", (0, 5)), W.Gate("X", (3,)), W.Gate("CNOT", (2, 7)), W.Gate("SWAP", (4, 13)),
+            W.Gate("X", (12,)), W.Gate("CNOT", (13, 1)), W.Gate("CNOT", (6, 11)), W.Gate("X", (6,))]
+    circ = W.Circuit(n, list(circ.gates) + tail, circ.n_params)
+    params = W.config_rng(4).angles(circ.n_params)
+    terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(91), n, 8)
+    e_ref = oracle.energy(circ, params, terms)
+    g_ref = oracle.grad_param_shift(circ, params, terms)
+    c = S.Circuit(circ, mode="fused")
+    psi = S.State(n, DTYPES[dtype]).reset(0)
+    lam = S.State(n, DTYPES[dtype])
+    e, g = S.value_and_grad(psi, lam, c, params_tensor(params), terms)
+    torch.cuda.synchronize()
+    assert abs(e.item() - e_ref) < E_TOL[dtype], (e.item(), e_ref)
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype],
+                           hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+    assert ok, worst
+    back = to_numpy(psi)
+    assert abs(back[0] - 1) < AMP_TOL[dtype] * 200
