@@ -269,6 +269,47 @@ tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circu
                               const double *dev_params, const tqd_pauli_term *terms, size_t n_terms,
                               double *dev_energy, double *dev_grads, void *stream);
 
+/* The reverse sweep of tqd_backward from a seed the caller placed in lambda:
+ * lambda must hold dL/d conj(psi_L) for a real loss L of the final state
+ * (so that dL/dtheta = 2 Re <lambda| d psi_L/dtheta>); psi holds psi_L.
+ * Adds dL/dtheta to dev_grads; on return psi holds psi_0 again.  With
+ * lambda = H psi_L this is tqd_backward; tqd_shots_gaussian_backward writes
+ * the seed of a loss of the Gaussian shots (Sec. 4.4 with a general seed). */
+tqd_status tqd_backward_seeded(tqd_state *psi, tqd_state *lambda, const tqd_circuit *circuit,
+                               const double *dev_params, double *dev_grads, void *stream);
+
+/* ------------------------------------------------------------ shot noise */
+
+/* p_b = |psi_b|^2 for every outcome b, FP64, to dev_p (2^n doubles)
+ * (measurement in the Z basis, Sec. 2.2.1). */
+tqd_status tqd_probabilities(const tqd_state *state, double *dev_p, void *stream);
+
+/* Exact sampling of measurement outcomes (Sec. 4.3.2, "Exact"): shot s is
+ * the outcome b with CDF(b-1) <= u_s < CDF(b) for the normalised cumulative
+ * distribution of p = |psi|^2 (inverse transform), u_s = dev_uniforms[s] in
+ * [0, 1) drawn by the caller; the outcome indices go to dev_samples
+ * (n_shots int64, device).  Two-level cumulative sums (chunk totals, then
+ * outcomes within the chunk), the single-device form of the paper's
+ * hierarchical scheme.  Uses the state's workspace. */
+tqd_status tqd_sample(tqd_state *state, const double *dev_uniforms, size_t n_shots, int64_t *dev_samples,
+                      void *stream);
+
+/* Approximate, differentiable shots (Sec. 4.3.2, "Approximate"):
+ * y = n p + sqrt(n) D S z with p = |psi|^2, D = diag(sqrt(p)),
+ * S = I - 2 v v^T, v = (e_{N-1} - sqrt(p)) / |e_{N-1} - sqrt(p)| (v = 0 in
+ * the degenerate case) and z = (z_0, ..., z_{N-2}, 0): dev_z holds N - 1 or N
+ * unit normals drawn by the caller (entry N - 1 is not read); y (N doubles)
+ * sums to n sum(p).  The printed S = I - v v^T lacks the factor 2 of the
+ * Householder reflection that gives the multinomial covariance. */
+tqd_status tqd_shots_gaussian(tqd_state *state, double n_shots, const double *dev_z, double *dev_y, void *stream);
+
+/* The seed of the reverse sweep for L = sum_i ybar_i y_i:
+ * lambda_b = dL/d conj(psi_b) = (dL/du_b) psi_b / (2 |psi_b|) with
+ * u = |psi| (0 where psi_b = 0), written to lambda (same qubits and dtype
+ * as state).  Follow with tqd_backward_seeded for dL/dtheta. */
+tqd_status tqd_shots_gaussian_backward(tqd_state *state, double n_shots, const double *dev_z,
+                                       const double *dev_ybar, tqd_state *lambda, void *stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* Many independent circuits of uneven width and depth (the batch dimension of

@@ -31,7 +31,8 @@ EXPORTS = (
     "tqd_plan_check",
     "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
-    "tqd_backward", "tqd_value_and_grad", "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info", "tqd_batch_free",
+    "tqd_backward", "tqd_value_and_grad", "tqd_backward_seeded", "tqd_probabilities", "tqd_sample",
+    "tqd_shots_gaussian", "tqd_shots_gaussian_backward", "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info", "tqd_batch_free",
     "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
 )
 
@@ -116,6 +117,11 @@ def load(path: str | None = None):
         L.tqd_apply_observable.argtypes = [vp, vp, sz, vp, vp, vp]
         L.tqd_backward.argtypes = [vp, vp, vp, vp, vp, sz, vp, dbl, vp, vp]
         L.tqd_value_and_grad.argtypes = [vp, vp, vp, vp, vp, sz, vp, vp, vp]
+        L.tqd_backward_seeded.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.tqd_probabilities.argtypes = [vp, vp, vp]
+        L.tqd_sample.argtypes = [vp, vp, sz, vp, vp]
+        L.tqd_shots_gaussian.argtypes = [vp, dbl, vp, vp, vp]
+        L.tqd_shots_gaussian_backward.argtypes = [vp, dbl, vp, vp, vp, vp]
         L.tqd_batch_create.argtypes = [i32, vp, vp, vp, vp, C.POINTER(vp)]
         L.tqd_batch_buffers.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
         L.tqd_batch_run.argtypes = [vp, vp]
@@ -126,6 +132,8 @@ def load(path: str | None = None):
         for name in ("tqd_state_alloc", "tqd_state_reset", "tqd_state_free", "tqd_circuit_create",
                      "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit", "tqd_expval",
                      "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable", "tqd_backward", "tqd_value_and_grad",
+                     "tqd_backward_seeded", "tqd_probabilities", "tqd_sample", "tqd_shots_gaussian",
+                     "tqd_shots_gaussian_backward",
                      "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info",
                      "tqd_batch_free", "tqd_profile_enable", "tqd_jit_check", "tqd_plan_check",
                      "tqd_profile_read"):

@@ -393,6 +393,57 @@ tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *c,
     return TQD_OK;
 }
 
+tqd_status tqd_backward_seeded(tqd_state *psi, tqd_state *lambda, const tqd_circuit *c, const double *dev_params,
+                               double *dev_grads, void *stream) {
+    CHECK_ARG(psi != nullptr && lambda != nullptr && c != nullptr, "tqd_backward_seeded: NULL handle");
+    CHECK_ARG(psi != lambda && psi->amps != lambda->amps, "tqd_backward_seeded: lambda must not alias psi");
+    CHECK_ARG(psi->n == c->n && lambda->n == c->n, "tqd_backward_seeded: qubit counts differ");
+    CHECK_ARG(psi->dtype == lambda->dtype, "tqd_backward_seeded: psi and lambda dtypes differ");
+    CHECK_ARG(c->n_params == 0 || dev_params != nullptr, "tqd_backward_seeded: dev_params is NULL");
+    CHECK_ARG(c->n_params == 0 || dev_grads != nullptr, "tqd_backward_seeded: dev_grads is NULL");
+    GUARD(psi->device);
+    CHECK_CUDA(run_backward(psi, lambda, c, dev_params, {}, nullptr, 1.0, dev_grads, (cudaStream_t)stream, nullptr,
+                            false, -1, true));
+    return TQD_OK;
+}
+
+tqd_status tqd_probabilities(const tqd_state *state, double *dev_p, void *stream) {
+    CHECK_ARG(state != nullptr && dev_p != nullptr, "tqd_probabilities: NULL argument");
+    GUARD(state->device);
+    CHECK_CUDA(launch_probabilities(state, dev_p, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+tqd_status tqd_sample(tqd_state *state, const double *dev_uniforms, size_t n_shots, int64_t *dev_samples,
+                      void *stream) {
+    CHECK_ARG(state != nullptr, "tqd_sample: state is NULL");
+    CHECK_ARG(n_shots == 0 || (dev_uniforms != nullptr && dev_samples != nullptr), "tqd_sample: NULL buffer");
+    GUARD(state->device);
+    CHECK_CUDA(launch_sample(state, dev_uniforms, n_shots, dev_samples, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+tqd_status tqd_shots_gaussian(tqd_state *state, double n_shots, const double *dev_z, double *dev_y, void *stream) {
+    CHECK_ARG(state != nullptr && dev_z != nullptr && dev_y != nullptr, "tqd_shots_gaussian: NULL argument");
+    CHECK_ARG(isfinite(n_shots) && n_shots >= 0, "tqd_shots_gaussian: n_shots must be finite and >= 0");
+    GUARD(state->device);
+    CHECK_CUDA(launch_shots_gaussian(state, n_shots, dev_z, nullptr, dev_y, nullptr, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
+tqd_status tqd_shots_gaussian_backward(tqd_state *state, double n_shots, const double *dev_z,
+                                       const double *dev_ybar, tqd_state *lambda, void *stream) {
+    CHECK_ARG(state != nullptr && lambda != nullptr && dev_z != nullptr && dev_ybar != nullptr,
+              "tqd_shots_gaussian_backward: NULL argument");
+    CHECK_ARG(state != lambda && state->amps != lambda->amps, "tqd_shots_gaussian_backward: lambda must not alias psi");
+    CHECK_ARG(state->n == lambda->n && state->dtype == lambda->dtype,
+              "tqd_shots_gaussian_backward: lambda differs from psi in qubits or dtype");
+    CHECK_ARG(isfinite(n_shots) && n_shots >= 0, "tqd_shots_gaussian_backward: n_shots must be finite and >= 0");
+    GUARD(state->device);
+    CHECK_CUDA(launch_shots_gaussian(state, n_shots, dev_z, dev_ybar, nullptr, lambda, (cudaStream_t)stream));
+    return TQD_OK;
+}
+
 tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circuit *c, const double *dev_params,
                               const tqd_pauli_term *terms, size_t n_terms, double *dev_energy, double *dev_grads,
                               void *stream) {

@@ -42,6 +42,14 @@ cudaError_t launch_apply_observable(const tqd_state *psi, const std::vector<Paul
                                     const double *dev_weights, double scale, tqd_state *out,
                                     cudaStream_t s, double *dev_energy = nullptr);
 
+// Shot noise (shots.cu): p = |psi|^2 (FP64); exact samples from the caller's
+// uniforms; the Gaussian sample y (ybar == null) or, with ybar, the seed
+// lambda = d(sum ybar y)/d conj(psi).  Use st's workspace.
+cudaError_t launch_probabilities(const tqd_state *st, double *p, cudaStream_t s);
+cudaError_t launch_sample(tqd_state *st, const double *uniforms, uint64_t n_shots, int64_t *out, cudaStream_t s);
+cudaError_t launch_shots_gaussian(tqd_state *st, double n_shots, const double *z, const double *ybar, double *y,
+                                  tqd_state *lam, cudaStream_t s);
+
 // Grows st->work to at least `len` doubles (stream-ordered).
 cudaError_t ensure_work(tqd_state *st, size_t len, cudaStream_t s);
 

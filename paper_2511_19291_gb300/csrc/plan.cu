@@ -212,10 +212,11 @@ cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_
 
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
-                         double *dev_grads, cudaStream_t s, double *dev_energy, bool prepared, int pass_end) {
+                         double *dev_grads, cudaStream_t s, double *dev_energy, bool prepared, int pass_end,
+                         bool seeded) {
     cudaError_t e = prepared ? cudaSuccess : launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
-    e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s, dev_energy);
+    if (!seeded) e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s, dev_energy);
     if (e != cudaSuccess) return e;
     if (c->fused) {
         const int np = pass_end < 0 ? (int)c->tile_passes.size() : pass_end;

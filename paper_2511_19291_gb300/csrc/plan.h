@@ -23,11 +23,12 @@ cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_
 // lambda = scale * H psi, reverse sweep, gradients accumulated into dev_grads.
 // dev_energy (may be null): Re <psi|lambda> before the sweep.  prepared: the
 // gate matrices of dev_params are already on the device (skip the prep).
-// pass_end >= 0: the sweep starts at fused pass pass_end - 1.
+// pass_end >= 0: the sweep starts at fused pass pass_end - 1.  seeded: lam
+// already holds the seed (groups, weights and scale are not used).
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
                          double *dev_grads, cudaStream_t s, double *dev_energy = nullptr, bool prepared = false,
-                         int pass_end = -1);
+                         int pass_end = -1, bool seeded = false);
 
 // The Pauli terms of P^dagger H P for the circuit's permutation tail P
 // (gates tail_gate.. in order): masks and signs after conjugation by each

@@ -13,7 +13,7 @@ namespace tqd {
 static const char *kNames[PK_NKINDS] = {
     "prep", "reset", "dense1", "diag1", "perm2", "phase11", "dense2", "small",
     "adj1", "adj_phase11", "adj_small", "expval", "expval_terms", "apply_obs", "reduce",
-    "tile_fwd", "tile_adj", "diag_run", "pauli_tile", "batch", "tc_block",
+    "tile_fwd", "tile_adj", "diag_run", "pauli_tile", "batch", "tc_block", "shots",
 };
 
 struct Rec {

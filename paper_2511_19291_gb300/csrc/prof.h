@@ -8,7 +8,7 @@ namespace tqd {
 enum ProfKind {
     PK_PREP = 0, PK_RESET, PK_DENSE1, PK_DIAG1, PK_PERM2, PK_PHASE11, PK_DENSE2, PK_SMALL,
     PK_ADJ1, PK_ADJ_PHASE11, PK_ADJ_SMALL, PK_EXPVAL, PK_EXPVAL_TERMS, PK_APPLY_OBS, PK_REDUCE,
-    PK_TILE_FWD, PK_TILE_ADJ, PK_DIAG_RUN, PK_PAULI_TILE, PK_BATCH, PK_TC_BLOCK, PK_NKINDS
+    PK_TILE_FWD, PK_TILE_ADJ, PK_DIAG_RUN, PK_PAULI_TILE, PK_BATCH, PK_TC_BLOCK, PK_SHOTS, PK_NKINDS
 };
 
 bool prof_on();

@@ -304,7 +304,103 @@ def value_and_grad(psi: State, lam: State, circuit: Circuit, params: torch.Tenso
     return energy, grads
 
 
+def backward_seeded(psi: State, lam: State, circuit: Circuit, params: torch.Tensor | None,
+                    grads: torch.Tensor | None = None) -> torch.Tensor:
+    """Reverse sweep from the seed in lam (dL/d conj(psi_L)): grads += dL/dparams;
+    psi is restored to the circuit's input state (tqd_backward_seeded)."""
+    if grads is None:
+        grads = torch.zeros(max(circuit.n_params, 0), dtype=torch.float64, device=psi.device)
+    gptr = C.c_void_p(grads.data_ptr()) if circuit.n_params else None
+    with torch.cuda.device(psi.device):
+        _lib.check(_L().tqd_backward_seeded(psi.handle, lam.handle, circuit.handle,
+                                            _params_ptr(params, circuit.n_params), gptr, _stream(psi.device)))
+    return grads
+
+
+# --------------------------------------------------------------- shot noise
+def probabilities(state: State) -> torch.Tensor:
+    """p_b = |psi_b|^2 (FP64, 2^n values) (tqd_probabilities)."""
+    p = torch.empty(1 << state.n, dtype=torch.float64, device=state.device)
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_probabilities(state.handle, C.c_void_p(p.data_ptr()), _stream(state.device)))
+    return p
+
+
+def sample(state: State, uniforms: torch.Tensor) -> torch.Tensor:
+    """Exact measurement samples: one outcome index per uniform in [0, 1)
+    (inverse transform of |psi|^2's cumulative distribution; tqd_sample)."""
+    u = uniforms.to(device=state.device, dtype=torch.float64).contiguous()
+    out = torch.empty(u.numel(), dtype=torch.int64, device=state.device)
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_sample(state.handle, C.c_void_p(u.data_ptr()), u.numel(), C.c_void_p(out.data_ptr()),
+                                   _stream(state.device)))
+    return out
+
+
+def _normals(z: torch.Tensor, n: int, device) -> torch.Tensor:
+    z = z.to(device=device, dtype=torch.float64).contiguous()
+    if z.numel() not in ((1 << n) - 1, 1 << n):
+        raise ValueError(f"z needs 2^n - 1 or 2^n entries, got {z.numel()}")
+    return z
+
+
+def shots_gaussian(state: State, n_shots: float, z: torch.Tensor) -> torch.Tensor:
+    """Approximate shots y = n p + sqrt(n) D S z (tqd_shots_gaussian); z: unit normals."""
+    z = _normals(z, state.n, state.device)
+    y = torch.empty(1 << state.n, dtype=torch.float64, device=state.device)
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_shots_gaussian(state.handle, float(n_shots), C.c_void_p(z.data_ptr()),
+                                           C.c_void_p(y.data_ptr()), _stream(state.device)))
+    return y
+
+
+def shots_gaussian_backward(state: State, n_shots: float, z: torch.Tensor, ybar: torch.Tensor,
+                            lam: State) -> State:
+    """lam = d(sum ybar y)/d conj(psi), the seed of backward_seeded."""
+    z = _normals(z, state.n, state.device)
+    yb = ybar.to(device=state.device, dtype=torch.float64).contiguous()
+    with torch.cuda.device(state.device):
+        _lib.check(_L().tqd_shots_gaussian_backward(state.handle, float(n_shots), C.c_void_p(z.data_ptr()),
+                                                    C.c_void_p(yb.data_ptr()), lam.handle, _stream(state.device)))
+    return lam
+
+
 # ------------------------------------------------------------------ autograd
+class _ShotsGaussFn(torch.autograd.Function):
+    """Gaussian shots of the circuit's output state, differentiable in the
+    angles (the reparameterisation of Sec. 4.3.2 with the reverse sweep of
+    Sec. 4.4 seeded by the shots' cotangent)."""
+
+    @staticmethod
+    def forward(ctx, params, circuit, n_shots, z, dtype, basis_index):
+        psi = State(circuit.n, dtype, params.device).reset(basis_index)
+        apply(psi, circuit, params)
+        y = shots_gaussian(psi, n_shots, z)
+        ctx.save_for_backward(params)
+        ctx.psi, ctx.circuit, ctx.n_shots, ctx.z = psi, circuit, n_shots, z
+        return y
+
+    @staticmethod
+    def backward(ctx, ybar):
+        (params,) = ctx.saved_tensors
+        psi = ctx.psi
+        if psi is None:
+            raise RuntimeError("these shots' backward already ran (the saved state is consumed)")
+        lam = State(psi.n, psi.tensor.dtype, psi.device)
+        shots_gaussian_backward(psi, ctx.n_shots, ctx.z, ybar.contiguous(), lam)
+        grads = torch.zeros_like(params)
+        backward_seeded(psi, lam, ctx.circuit, params, grads)
+        ctx.psi = None
+        return grads, None, None, None, None, None
+
+
+def shots_gaussian_fn(params: torch.Tensor, circuit: Circuit, n_shots: float, z: torch.Tensor,
+                      dtype=torch.complex64, basis_index: int = 0) -> torch.Tensor:
+    """Differentiable approximate shots y (2^n values) of the circuit's
+    output state for unit normals z."""
+    return _ShotsGaussFn.apply(params, circuit, float(n_shots), z, dtype, basis_index)
+
+
 class _ExpvalFn(torch.autograd.Function):
     """E(theta) = <psi_L|H|psi_L>.  Forward keeps only theta and psi_L; backward
     recomputes earlier states by un-applying the circuit (Sec. 4.4)."""
