@@ -410,3 +410,47 @@ def test_value_and_grad_permutation_tail(dtype):
     assert ok, worst
     back = to_numpy(psi)
     assert abs(back[0] - 1) < AMP_TOL[dtype] * 200
+
+
+@pytest.mark.parametrize("nq,dtype", [(6, "c128"), (12, "c64")])
+def test_main_example_ladder_encoder_batch(nq, dtype):
+    """The appendix's main example: a batch of 16 inputs x[b, i] fed to RY
+    encoders, three CNOT-ladder + RY layers, out = measure_allZ per sample,
+    loss = sum |out|, gradient with respect to the inputs; against the
+    oracle (per-term values; parameter shift with the terms weighted by
+    sign(out)), then three Adam steps that lower the loss."""
+    S = sim()
+    batch, layers = 16, 3
+    circ = W.ladder_ansatz(nq, layers)
+    rng = np.random.default_rng(nq)
+    weights = rng.random(circ.n_params - nq) * np.pi
+    x = torch.nn.Parameter(torch.tensor(rng.random((batch, nq)) * np.pi / 3, device="cuda"))
+    c = S.Circuit(circ)
+    w_dev = torch.tensor(weights, device="cuda")
+    tol_e = 1e-10 if dtype == "c128" else 2e-5
+
+    def forward(xv):
+        outs = [S.measure_allz_fn(torch.cat([xv[b], w_dev]), c, dtype=DTYPES[dtype]) for b in range(batch)]
+        return torch.stack(outs)
+
+    out = forward(x)
+    loss = out.abs().sum()
+    loss.backward()
+    g = x.grad.detach().cpu().numpy()
+    xs = x.detach().cpu().numpy()
+    for b in (0, 7, 15):
+        params = np.concatenate([xs[b], weights])
+        _, ref = oracle.expval(nq, oracle.run(circ, params), W.all_z_terms(nq))
+        np.testing.assert_allclose(out[b].detach().cpu().numpy(), ref, atol=tol_e)
+        terms = [W.PauliTerm(float(np.sign(r)), t.ops) for t, r in zip(W.all_z_terms(nq), ref)]
+        gref = oracle.grad_param_shift(circ, params, terms)[:nq]
+        np.testing.assert_allclose(g[b], gref, atol=1e-9 if dtype == "c128" else 1e-4)
+    opt = torch.optim.Adam([x], lr=0.05)
+    losses = [loss.item()]
+    for _ in range(3):
+        opt.zero_grad()
+        l2 = forward(x).abs().sum()
+        l2.backward()
+        opt.step()
+        losses.append(l2.item())
+    assert losses[-1] < losses[0]
