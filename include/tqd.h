@@ -114,8 +114,17 @@ typedef struct {
     uint32_t max_blocks;  /* cap on the blocks of a fused pass launch (0 = no cap: one per SM for
                              the ring, the occupancy limit otherwise); a smaller grid gives each
                              block more tiles */
-    uint32_t reserved[2]; /* must be zero */
+    uint32_t checkpoints; /* forward checkpoints of tqd_value_and_grad (fused plan): the states
+                             after the last K passes are kept in device memory the circuit owns,
+                             so the reverse sweep reads psi there instead of writing it back
+                             (3 instead of 4 state transfers per reverse pass).  0 = default: as
+                             many passes as fit in half the device memory free at the first
+                             call; TQD_CHECKPOINTS_NONE = none (psi recomputed in place all the
+                             way); other values = at most that many passes */
+    uint32_t reserved[1]; /* must be zero */
 } tqd_plan_opts;
+
+#define TQD_CHECKPOINTS_NONE 0xFFFFFFFFu
 
 typedef struct tqd_state tqd_state;
 typedef struct tqd_circuit tqd_circuit;
@@ -264,7 +273,15 @@ tqd_status tqd_expval_noalloc(const tqd_state *state, const tqd_pauli_term *term
  * input state again and lambda holds U^dagger H psi_L.  E is read off
  * lambda = H psi_L as Re <psi_L|lambda>, the seed the reverse sweep needs
  * anyway (Sec. 2.2.1, Sec. 4.4), so no separate expectation pass runs; it
- * equals tqd_expval's value up to rounding. */
+ * equals tqd_expval's value up to rounding.
+ *
+ * Fused plans keep forward checkpoints (tqd_plan_opts.checkpoints): the
+ * states after the last K passes go to device memory the circuit owns, the
+ * reverse sweep reads psi there, and psi itself is only read when K covers
+ * every pass.  The first call for a state size allocates that memory
+ * (cudaMemGetInfo, cudaMalloc): make it outside any stream capture.  Calls on
+ * one circuit whose GPU work overlaps race on it (as on its gradient
+ * partials). */
 tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circuit *circuit,
                               const double *dev_params, const tqd_pauli_term *terms, size_t n_terms,
                               double *dev_energy, double *dev_grads, void *stream);

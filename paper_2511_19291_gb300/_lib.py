@@ -23,6 +23,7 @@ KIND_CODES = {
 }
 C64, C128 = 0, 1
 PLAN_PLAIN, PLAN_FUSED, PLAN_TC = 0, 1, 2
+CHECKPOINTS_NONE = 0xFFFFFFFF
 
 # Every symbol include/tqd.h declares (checked by the ABI test).
 EXPORTS = (
@@ -76,7 +77,7 @@ class BatchOpts(C.Structure):
 class PlanOpts(C.Structure):
     _fields_ = [("mode", C.c_uint32), ("tile_qubits", C.c_uint32), ("low_qubits", C.c_uint32),
                 ("buffers", C.c_uint32), ("jit", C.c_uint32), ("max_blocks", C.c_uint32),
-                ("reserved", C.c_uint32 * 2)]
+                ("checkpoints", C.c_uint32), ("reserved", C.c_uint32 * 1)]
 
 
 _lock = threading.Lock()

@@ -163,7 +163,7 @@ static tqd_status validate_circuit(int n_qubits, const tqd_gate *gates, size_t n
                   "tqd_circuit_create: unknown plan mode");
         CHECK_ARG(o.buffers <= 4, "tqd_circuit_create: buffers %u not in {0, ..., 4}", o.buffers);
         CHECK_ARG(o.jit <= 2, "tqd_circuit_create: jit %u not in {0, 1, 2}", o.jit);
-        for (int i = 0; i < 2; ++i) CHECK_ARG(o.reserved[i] == 0, "tqd_circuit_create: reserved opts not zero");
+        CHECK_ARG(o.reserved[0] == 0, "tqd_circuit_create: reserved opts not zero");
     }
     std::vector<GateH> &gs = *gs_out;
     gs.assign(n_gates, GateH());
@@ -458,19 +458,23 @@ tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circu
     if (st != TQD_OK) return st;
     GUARD(psi->device);
     const cudaStream_t s = (cudaStream_t)stream;
-    if (c->fused && c->prefix_passes < (int)c->tile_passes.size()) {
+    const bool tail = c->fused && c->prefix_passes < (int)c->tile_passes.size();
+    // forward checkpoints of the passes that run (the last ones that fit)
+    Checkpoints ck;
+    CHECK_CUDA(checkpoints_for(c, psi, tail ? c->prefix_passes : (int)c->tile_passes.size(), &ck));
+    if (tail) {
         // the circuit ends with a permutation P (its tail passes): E and its
         // gradient from psi' = U' psi (the gates before P) with
         // H' = P^dagger H P; the tail passes never run
         const std::vector<tqd_pauli_term> hp = conjugate_by_tail(c, terms, n_terms);
-        CHECK_CUDA(run_forward(psi, c, dev_params, s, c->prefix_passes));
+        CHECK_CUDA(run_forward(psi, c, dev_params, s, c->prefix_passes, &ck));
         CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(hp.data(), hp.size()), nullptr, 1.0,
-                                dev_grads, s, dev_energy, true, c->prefix_passes));
+                                dev_grads, s, dev_energy, true, c->prefix_passes, false, &ck));
         return TQD_OK;
     }
-    CHECK_CUDA(run_forward(psi, c, dev_params, s));
+    CHECK_CUDA(run_forward(psi, c, dev_params, s, -1, &ck));
     CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(terms, n_terms), nullptr, 1.0, dev_grads, s,
-                            dev_energy, true));
+                            dev_energy, true, -1, false, &ck));
     return TQD_OK;
 }
 

@@ -121,4 +121,9 @@ struct tqd_circuit {
     mutable std::mutex jit_mu;
     mutable std::vector<void *> jit_fn[2][2];
     mutable bool jit_ready[2][2] = {{false, false}, {false, false}};
+    // forward checkpoints of tqd_value_and_grad (device memory, sized on first use)
+    mutable std::mutex ck_mu;
+    mutable void *ck_buf = nullptr;
+    mutable size_t ck_bytes = 0;        // allocated
+    mutable size_t ck_state_bytes = 0;  // state size the allocation was sized for
 };

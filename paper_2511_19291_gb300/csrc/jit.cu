@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <thread>
 #include <unordered_map>
@@ -116,6 +117,9 @@ void put(std::string &o, const char *fmt, ...) {
 
 const char *tf(bool b) { return b ? "true" : "false"; }
 
+// Registers per thread a TMA-warpgroup ring kernel launches with.
+int tmaw_launch_regs(bool adj) { return adj ? RingCfg<true>::REGS_LAUNCH : RingCfg<false>::REGS_LAUNCH; }
+
 // Whether a diagonal run has gates on thread bits (a per-thread factor).
 bool dg_has_thread_subs(const TilePassDev &D, const TileOp &op) {
     for (int q = op.sub0; q < op.sub0 + op.nsub; ++q)
@@ -203,12 +207,33 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
         bool need = false;
         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) need |= D.subs[q].gslot >= 0;
         if (!need) return;
-        o += "{\nTT w[NR];\nfor (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);\n";
+        // Every derivative of the run is a signed sum of w: from the total wt
+        // and the per-register-bit sums ws[r] each costs at most one fma.
+        o += "{\nTT w[NR];\nfor (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);\n"
+             "TT wt, ws[TILE_R];\ndiag_sums<TT>(w, wt, ws);\n";
+        auto bit = [](uint8_t p, char *buf, size_t len) {
+            if (p & 0x80) snprintf(buf, len, "((tid >> %d) & 1u)", p & 0x7f);
+            else buf[0] = 0;
+        };
         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
             const TileSub &sb = D.subs[q];
             if (sb.gslot < 0) continue;
-            put(o, "gacc_add<KRING>(c.gacc, %d, tid, grad_diag<TV>(%d, %d, %d, %d, w, tid));\n", sb.gslot, sb.type,
-                sb.a, sb.b, sb.gen);
+            char ta[32], tb[32], e[160];
+            bit(sb.a, ta, sizeof ta);
+            if (sb.type == TOP_D1 && (sb.gen == GEN_Z || sb.gen == GEN_P1)) {
+                const bool z = sb.gen == GEN_Z;
+                if (ta[0]) snprintf(e, sizeof e, z ? "(%s ? -wt : wt)" : "(%s ? TT(-2) * wt : TT(0))", ta);
+                else snprintf(e, sizeof e, z ? "fma(TT(-2), ws[%d], wt)" : "TT(-2) * ws[%d]", sb.a);
+            } else if (sb.type == TOP_D2) {
+                bit(sb.b, tb, sizeof tb);
+                if (ta[0] && tb[0]) snprintf(e, sizeof e, "((%s & %s) ? TT(-2) * wt : TT(0))", ta, tb);
+                else if (ta[0] || tb[0])
+                    snprintf(e, sizeof e, "(%s ? TT(-2) * ws[%d] : TT(0))", ta[0] ? ta : tb, ta[0] ? sb.b : sb.a);
+                else snprintf(e, sizeof e, "grad_diag<TV>(%d, %d, %d, %d, w, tid)", sb.type, sb.a, sb.b, sb.gen);
+            } else {
+                snprintf(e, sizeof e, "grad_diag<TV>(%d, %d, %d, %d, w, tid)", sb.type, sb.a, sb.b, sb.gen);
+            }
+            put(o, "gacc_add<KRING>(c.gacc, %d, tid, %s);\n", sb.gslot, e);
         }
         o += "}\n";
         return;
@@ -302,13 +327,13 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
         "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
         "tqd_pass(const __grid_constant__ tqd::TmaDesc mp, const __grid_constant__ tqd::TmaDesc ml,\n"
         "         const tqd::TilePassDev *__restrict__ Pg, const tqd::TT *__restrict__ mats,\n"
-        "         double *__restrict__ partials, int pblk, int *__restrict__ err) {\n",
+        "         double *__restrict__ partials, int pblk, int *__restrict__ err, int flags) {\n",
         ring ? (adj ? (tmaw ? RingCfg<true>::THREADS_TMAW : RingCfg<true>::THREADS) : (tmaw ? RingCfg<false>::THREADS_TMAW : RingCfg<false>::THREADS)) : TILE_THREADS, ring ? 1 : minb);
     if (ring)
         put(o, "    tqd::tile_pass_ring<tqd::TV, tqd::KADJ, tqd::RingCfg<tqd::KADJ>::G, tqd::RingCfg<tqd::KADJ>::B, %s,\n"
-               "                        tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n}\n", tf(tmaw));
+               "                        tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err, flags);\n}\n", tf(tmaw));
     else
-        o += "    tqd::tile_pass_body<tqd::TV, tqd::KADJ, 1, tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err);\n}\n";
+        o += "    tqd::tile_pass_body<tqd::TV, tqd::KADJ, 1, tqd::PassRunner>(&mp, &ml, Pg, mats, partials, pblk, err, flags);\n}\n";
     return o;
 }
 
@@ -320,8 +345,10 @@ int device_arch(int dev) {
     return mj * 10 + mn;
 }
 
-// Source -> cubin; empty with the log in *log on failure.
-std::string compile_cubin(const std::string &src, int arch, std::string *log) {
+// Source -> cubin; empty with the log in *log on failure.  info: ptxas
+// reports resources (registers, spills) and the log is returned in *log on
+// success too.
+std::string compile_cubin(const std::string &src, int arch, std::string *log, bool info = false) {
     const Nvrtc &N = nvrtc();
     nvrtcProgram prog;
     if (N.create(&prog, src.c_str(), "tqd_pass.cu", k_jit_n_headers, k_jit_header_srcs, k_jit_header_names) !=
@@ -333,7 +360,7 @@ std::string compile_cubin(const std::string &src, int arch, std::string *log) {
     snprintf(archopt, sizeof(archopt), "--gpu-architecture=sm_%da", arch);
     // TQD_JIT_VERBOSE=1: ptxas reports registers and spills into the log
     const bool verbose = getenv("TQD_JIT_VERBOSE") && getenv("TQD_JIT_VERBOSE")[0] == '1';
-    const char *opts[] = {archopt, "-std=c++17", "-DNDEBUG", verbose ? "--ptxas-options=-v" : "-DTQD_QUIET",
+    const char *opts[] = {archopt, "-std=c++17", "-DNDEBUG", (verbose || info) ? "--ptxas-options=-v" : "-DTQD_QUIET",
 #ifdef TQD_CHECKED
                           "-DTQD_CHECKED",
 #endif
@@ -347,12 +374,13 @@ std::string compile_cubin(const std::string &src, int arch, std::string *log) {
         if (n) N.log(prog, &lg[0]);
         fprintf(stderr, "[tqd jit] %s\n", lg.c_str());
     }
-    if (r != NVRTC_SUCCESS) {
+    if (r != NVRTC_SUCCESS || info) {
         size_t n = 0;
         N.log_size(prog, &n);
         log->assign(n, '\0');
         if (n) N.log(prog, &(*log)[0]);
-    } else {
+    }
+    if (r == NVRTC_SUCCESS) {
         size_t n = 0;
         N.cubin_size(prog, &n);
         out.assign(n, '\0');
@@ -465,12 +493,18 @@ cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool 
     return cudaSuccess;
 }
 
+int jit_num_regs(CUfunction f) {
+    int v = -1;
+    if (!driver().ok || driver().get_attr(&v, CU_FUNC_ATTRIBUTE_NUM_REGS, f) != CUDA_SUCCESS) return -1;
+    return v;
+}
+
 cudaError_t jit_launch(CUfunction f, const CUtensorMap &ma, const CUtensorMap &mb, const TilePassDev *desc,
-                       const void *mats, double *partials, int pblk, int *err, int grid, int threads,
+                       const void *mats, double *partials, int pblk, int *err, int flags, int grid, int threads,
                        uint32_t smem, cudaStream_t s) {
     CUtensorMap a = ma, b = mb;
     const void *m = mats;
-    void *args[] = {&a, &b, (void *)&desc, (void *)&m, (void *)&partials, (void *)&pblk, (void *)&err};
+    void *args[] = {&a, &b, (void *)&desc, (void *)&m, (void *)&partials, (void *)&pblk, (void *)&err, (void *)&flags};
     const CUresult r = driver().launch(f, (unsigned)grid, 1, 1, (unsigned)threads, 1, 1, smem, (CUstream)s, args, nullptr);
     if (r == CUDA_SUCCESS) return cudaSuccess;
     // a launch the driver refused (nothing ran); the code names the reason
@@ -494,6 +528,7 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
             return TQD_ERR_INVALID_ARG;
         }
     std::vector<std::string> srcs;
+    std::vector<int> launch_regs;  // registers the kernel must launch with (TMA warpgroup), else 0
     {
         std::unordered_map<std::string, int> seen;
         for (auto &p : passes)
@@ -501,7 +536,10 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
                 for (int adj = 0; adj < 2; ++adj)
                     for (int ring = 0; ring < (dt == 0 ? 3 : 1); ++ring) {
                         std::string src = generate(p.dev[dt], dt, adj != 0, ring != 0, ring == 2);
-                        if (seen.emplace(src, 1).second) srcs.push_back(std::move(src));
+                        if (seen.emplace(src, 1).second) {
+                            srcs.push_back(std::move(src));
+                            launch_regs.push_back(ring == 2 ? tmaw_launch_regs(adj != 0) : 0);
+                        }
                     }
     }
     std::vector<std::string> logs(srcs.size());
@@ -512,14 +550,24 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
     for (int t = 0; t < nt; ++t)
         th.emplace_back([&] {
             for (int i; (i = next.fetch_add(1)) < (int)srcs.size();)
-                ok[i] = !compile_cubin(srcs[i], arch, &logs[i]).empty();
+                ok[i] = !compile_cubin(srcs[i], arch, &logs[i], true).empty();
         });
     for (auto &t : th) t.join();
-    for (size_t i = 0; i < srcs.size(); ++i)
+    for (size_t i = 0; i < srcs.size(); ++i) {
         if (!ok[i]) {
             set_error("tqd_jit_check: kernel %zu of %zu failed to compile: %.400s", i, srcs.size(), logs[i].c_str());
             return TQD_ERR_CUDA;
         }
+        // the register shares of a TMA-warpgroup kernel assume it launches
+        // with exactly REGS_LAUNCH registers per thread
+        const char *u = strstr(logs[i].c_str(), "Used ");
+        const int regs = u ? atoi(u + 5) : -1;
+        if (launch_regs[i] && regs != launch_regs[i]) {
+            set_error("tqd_jit_check: TMA-warpgroup kernel %zu launches with %d registers per thread, not %d", i,
+                      regs, launch_regs[i]);
+            return TQD_ERR_CUDA;
+        }
+    }
     *n_kernels = (int)srcs.size();
     return TQD_OK;
 }

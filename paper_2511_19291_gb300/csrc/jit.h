@@ -36,9 +36,12 @@ std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ri
 cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, cudaStream_t s,
                          CUfunction *out);
 
+// Registers per thread kernel f launches with (-1 when unknown).
+int jit_num_regs(CUfunction f);
+
 // Launches a specialised kernel with the generic kernel's arguments.
 cudaError_t jit_launch(CUfunction f, const CUtensorMap &ma, const CUtensorMap &mb, const TilePassDev *desc,
-                       const void *mats, double *partials, int pblk, int *err, int grid, int threads,
+                       const void *mats, double *partials, int pblk, int *err, int flags, int grid, int threads,
                        uint32_t smem, cudaStream_t s);
 
 // Host only (no GPU): plans circuit c's fused passes, generates every

@@ -22,8 +22,8 @@ template <typename V, bool ADJ, int NB>
 __global__ void __launch_bounds__(TILE_THREADS, tile_min_blocks<V, ADJ, NB>())
     k_tile(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam,
            const TilePassDev *__restrict__ Pg, const RT<V> *__restrict__ mats, double *__restrict__ partials,
-           int pblk, int *__restrict__ err) {
-    tile_pass_body<V, ADJ, NB, InterpRunner<V, ADJ>>(&map_psi, &map_lam, Pg, mats, partials, pblk, err);
+           int pblk, int *__restrict__ err, int flags) {
+    tile_pass_body<V, ADJ, NB, InterpRunner<V, ADJ>>(&map_psi, &map_lam, Pg, mats, partials, pblk, err, flags);
 }
 
 // The generic pass on a ring of tile buffers (one block per SM, G groups,
@@ -32,9 +32,9 @@ template <typename V, bool ADJ, bool TMAW>
 __global__ void __launch_bounds__((TMAW ? RingCfg<ADJ>::THREADS_TMAW : RingCfg<ADJ>::THREADS), 1)
     k_tile_ring(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam,
                 const TilePassDev *__restrict__ Pg, const RT<V> *__restrict__ mats, double *__restrict__ partials,
-                int pblk, int *__restrict__ err) {
+                int pblk, int *__restrict__ err, int flags) {
     tile_pass_ring<V, ADJ, RingCfg<ADJ>::G, RingCfg<ADJ>::B, TMAW, InterpRunner<V, ADJ, true>>(
-        &map_psi, &map_lam, Pg, mats, partials, pblk, err);
+        &map_psi, &map_lam, Pg, mats, partials, pblk, err, flags);
 }
 
 // ------------------------------------------------------------------- host
@@ -179,24 +179,44 @@ int tile_grid(const tqd_circuit *c, int dt, bool adj) {
     return adj ? grid_for<double2, true>(c, 1) : grid_for<double2, false>(c, 1);
 }
 
+// Bytes a pass moves: psi read and written; in the reverse sweep lambda too,
+// and psi only read when it comes from a forward checkpoint.
+template <typename V, bool ADJ>
+static double pass_bytes(const tqd_circuit *c, int flags) {
+    const double state = (double)((uint64_t)1 << c->n) * sizeof(V);
+    return state * (ADJ ? ((flags & TILE_PSI_RO) ? 3.0 : 4.0) : 2.0);
+}
+
 template <typename V, bool ADJ, int NB>
 static cudaError_t launch_nb(const CUtensorMap &ma, const CUtensorMap &mb, const tqd_circuit *c, int pass,
-                             cudaStream_t s) {
+                             int flags, cudaStream_t s) {
     const int dt = sizeof(V) == 8 ? 0 : 1;
     const TilePlanPass &pp = c->tile_passes[pass];
     const TileSmem sm = tile_smem<V, ADJ, NB>(pp.dev[dt].h);
     const int grid = grid_nb<V, ADJ, NB>(c, dt);
-    const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
-    ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
+    ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, pass_bytes<V, ADJ>(c, flags), s);
     const RT<V> *mats = dt == 0 ? (const RT<V> *)c->d_mats32 : (const RT<V> *)c->d_mats64;
     k_tile<V, ADJ, NB><<<grid, TILE_THREADS, sm.total, s>>>(ma, mb, c->d_tile_desc + 2 * pass + dt, mats,
-                                                            c->d_partials, c->pblk, c->d_err);
+                                                            c->d_partials, c->pblk, c->d_err, flags);
     return cudaGetLastError();
+}
+
+// Registers per thread of the generic ring kernel with the TMA warpgroup.
+template <typename V, bool ADJ>
+static int ring_tmaw_regs() {
+    if constexpr (sizeof(V) == 8) {
+        static int regs = [] {
+            cudaFuncAttributes a;
+            return cudaFuncGetAttributes(&a, k_tile_ring<V, ADJ, true>) == cudaSuccess ? a.numRegs : -1;
+        }();
+        return regs;
+    }
+    return -1;
 }
 
 template <typename V, bool ADJ, bool TMAW>
 static cudaError_t launch_ring_generic(const CUtensorMap &ma, const CUtensorMap &mb, const tqd_circuit *c, int pass,
-                                       cudaStream_t s) {
+                                       int flags, cudaStream_t s) {
     const int dt = sizeof(V) == 8 ? 0 : 1;
     static std::mutex mu;
     static uint32_t set_to = 0;
@@ -210,56 +230,72 @@ static cudaError_t launch_ring_generic(const CUtensorMap &ma, const CUtensorMap 
     }
     const TilePlanPass &pp = c->tile_passes[pass];
     const TileSmem sm = tile_smem_ring<V, ADJ, RingCfg<ADJ>::B>(pp.dev[dt].h);
-    const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
-    ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
+    ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, pass_bytes<V, ADJ>(c, flags), s);
     const RT<V> *mats = dt == 0 ? (const RT<V> *)c->d_mats32 : (const RT<V> *)c->d_mats64;
     k_tile_ring<V, ADJ, TMAW><<<grid_ring(c), (TMAW ? RingCfg<ADJ>::THREADS_TMAW : RingCfg<ADJ>::THREADS), sm.total, s>>>(
-        ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials, c->pblk, c->d_err);
+        ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials, c->pblk, c->d_err, flags);
     return cudaGetLastError();
 }
 
+// Tensor maps: forward, ma = psi_src (loads) and mb = psi_dst (stores); the
+// reverse sweep, ma = psi_src (loads, and stores unless TILE_PSI_RO) and mb
+// = lambda.
 template <typename V, bool ADJ>
-static cudaError_t launch_t(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s) {
+static cudaError_t launch_t(const void *psi_src, void *psi_dst, tqd_state *lam, const tqd_circuit *c, int pass,
+                            int flags, cudaStream_t s) {
     const int dt = sizeof(V) == 8 ? 0 : 1;
     const TilePlanPass &pp = c->tile_passes[pass];
     CUtensorMap ma, mb;
-    cudaError_t e = make_map(&ma, psi->amps, pp, dt);
+    cudaError_t e = make_map(&ma, const_cast<void *>(psi_src), pp, dt);
     if (e != cudaSuccess) return e;
-    if (ADJ) {
-        e = make_map(&mb, lam->amps, pp, dt);
-        if (e != cudaSuccess) return e;
-    } else {
-        mb = ma;
-    }
+    if (ADJ) e = make_map(&mb, lam->amps, pp, dt);
+    else if (psi_dst != psi_src) e = make_map(&mb, psi_dst, pp, dt);
+    else mb = ma;
+    if (e != cudaSuccess) return e;
     const int tb = buffers_for<V, ADJ>(c, dt);
-    if (tb == TB_TWO) return launch_nb<V, ADJ, 2>(ma, mb, c, pass, s);
+    if (tb == TB_TWO) return launch_nb<V, ADJ, 2>(ma, mb, c, pass, flags, s);
     // the pass-specialised kernel when the circuit has one: same descriptor,
     // shared memory and grid as the generic kernel of the same kind
-    const bool ring = tb == TB_RING || tb == TB_RING_TMAW, tmaw = tb == TB_RING_TMAW;
+    const bool ring = tb == TB_RING || tb == TB_RING_TMAW;
+    bool tmaw = tb == TB_RING_TMAW;
     CUfunction f = nullptr;
     e = jit_function(c, pass, dt, ADJ, ring, tmaw, s, &f);
     if (e != cudaSuccess) return e;
+    if (tmaw && (f ? jit_num_regs(f) : ring_tmaw_regs<V, ADJ>()) != RingCfg<ADJ>::REGS_LAUNCH) {
+        // the TMA warpgroup's register shares add up only for a launch with
+        // REGS_LAUNCH registers per thread: the ring without it instead
+        tmaw = false;
+        f = nullptr;
+        e = jit_function(c, pass, dt, ADJ, ring, false, s, &f);
+        if (e != cudaSuccess) return e;
+    }
     if (!f) {
         if constexpr (sizeof(V) == 8) {
-            if (tmaw) return launch_ring_generic<V, ADJ, true>(ma, mb, c, pass, s);
-            if (ring) return launch_ring_generic<V, ADJ, false>(ma, mb, c, pass, s);
+            if (tmaw) return launch_ring_generic<V, ADJ, true>(ma, mb, c, pass, flags, s);
+            if (ring) return launch_ring_generic<V, ADJ, false>(ma, mb, c, pass, flags, s);
         }
-        return launch_nb<V, ADJ, 1>(ma, mb, c, pass, s);
+        return launch_nb<V, ADJ, 1>(ma, mb, c, pass, flags, s);
     }
     const TileSmem sm = ring ? tile_smem_ring<V, ADJ, RingCfg<ADJ>::B>(pp.dev[dt].h) : tile_smem<V, ADJ, 1>(pp.dev[dt].h);
     const int grid = ring ? grid_ring(c) : grid_nb<V, ADJ, 1>(c, dt);
     const int threads = ring ? (tmaw ? RingCfg<ADJ>::THREADS_TMAW : RingCfg<ADJ>::THREADS) : TILE_THREADS;
-    const double bytes = (double)((uint64_t)1 << c->n) * sizeof(V) * 2.0 * (ADJ ? 2.0 : 1.0);
-    ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, bytes, s);
+    ProfScope ps(ADJ ? PK_TILE_ADJ : PK_TILE_FWD, pass_bytes<V, ADJ>(c, flags), s);
     const void *mats = dt == 0 ? (const void *)c->d_mats32 : (const void *)c->d_mats64;
-    return jit_launch(f, ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials, c->pblk, c->d_err, grid,
+    return jit_launch(f, ma, mb, c->d_tile_desc + 2 * pass + dt, mats, c->d_partials, c->pblk, c->d_err, flags, grid,
                       threads, sm.total, s);
 }
 
-cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s) {
+cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s,
+                             const void *psi_src, void *psi_dst) {
+    const void *src = psi_src ? psi_src : psi->amps;
+    void *dst = psi_dst ? psi_dst : psi->amps;
+    // a reverse pass whose psi comes from elsewhere leaves it as it is
+    const int flags = (lam && psi_src) ? TILE_PSI_RO : 0;
     if (psi->dtype == TQD_C64)
-        return lam ? launch_t<float2, true>(psi, lam, c, pass, s) : launch_t<float2, false>(psi, lam, c, pass, s);
-    return lam ? launch_t<double2, true>(psi, lam, c, pass, s) : launch_t<double2, false>(psi, lam, c, pass, s);
+        return lam ? launch_t<float2, true>(src, dst, lam, c, pass, flags, s)
+                   : launch_t<float2, false>(src, dst, lam, c, pass, flags, s);
+    return lam ? launch_t<double2, true>(src, dst, lam, c, pass, flags, s)
+               : launch_t<double2, false>(src, dst, lam, c, pass, flags, s);
 }
 
 }  // namespace tqd

@@ -1,8 +1,8 @@
 // plan.cu -- circuit planning (host) and the forward / backward executors.
 #include <string.h>
 
+#include <algorithm>
 #include <new>
-
 #include <vector>
 
 #include "jit.h"
@@ -185,20 +185,72 @@ void release_circuit(tqd_circuit *c) {
         delete b;
     }
     c->tc_blocks.clear();
+    cudaFree(c->ck_buf);
+    c->ck_buf = nullptr;
+    c->ck_bytes = c->ck_state_bytes = 0;
+}
+
+cudaError_t checkpoints_for(const tqd_circuit *c, const tqd_state *psi, int np, Checkpoints *out) {
+    *out = Checkpoints();
+    const uint32_t opt = c->opts.checkpoints;
+    if (!c->fused || np <= 0 || opt == TQD_CHECKPOINTS_NONE) return cudaSuccess;
+    const size_t sb = ((size_t)1 << c->n) * (psi->dtype == TQD_C64 ? 8 : 16);
+    int want = np;
+    if (opt != 0 && opt < (uint32_t)np) want = (int)opt;
+    std::lock_guard<std::mutex> lk(c->ck_mu);
+    if (c->ck_state_bytes != sb) {
+        // sized once per state size: up to `want` states in half the free memory
+        if (c->ck_buf) {
+            cudaError_t e = cudaFree(c->ck_buf);
+            if (e != cudaSuccess) return e;
+            c->ck_buf = nullptr;
+            c->ck_bytes = 0;
+        }
+        size_t fr = 0, tot = 0;
+        cudaError_t e = cudaMemGetInfo(&fr, &tot);
+        if (e != cudaSuccess) return e;
+        size_t k = std::min<size_t>((size_t)want, fr / 2 / sb);
+        // a budget the allocator cannot meet in one piece: fewer passes
+        for (; k > 0; k /= 2) {
+            if (cudaMalloc(&c->ck_buf, k * sb) == cudaSuccess) break;
+            (void)cudaGetLastError();
+            c->ck_buf = nullptr;
+        }
+        c->ck_bytes = k * sb;
+        c->ck_state_bytes = sb;
+    }
+    out->base = (char *)c->ck_buf;
+    out->stride = sb;
+    out->count = (int)std::min<size_t>((size_t)want, c->ck_buf ? c->ck_bytes / sb : 0);
+    return cudaSuccess;
 }
 
 cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_params, cudaStream_t s,
-                        int pass_end) {
+                        int pass_end, const Checkpoints *ck) {
     cudaError_t e = launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
     if (c->fused) {
         const int np = pass_end < 0 ? (int)c->tile_passes.size() : pass_end;
+        const int first = ck ? np - ck->count : np;  // first checkpointed pass
         for (int p = 0; p < np; ++p) {
             const TilePlanPass &pp = c->tile_passes[p];
-            if (pp.tc >= 0 && psi->dtype == TQD_C64)
-                e = launch_tc_block(psi, c, *(const TcBlock *)c->tc_blocks[pp.tc], s);
-            else
-                e = launch_tile_pass(psi, nullptr, c, p, s);
+            const bool tc = pp.tc >= 0 && psi->dtype == TQD_C64;
+            if (p < first) {
+                e = tc ? launch_tc_block(psi, c, *(const TcBlock *)c->tc_blocks[pp.tc], s)
+                       : launch_tile_pass(psi, nullptr, c, p, s);
+            } else {
+                const void *src = p == first ? psi->amps : ck->at(p - first - 1);
+                void *dst = ck->at(p - first);
+                if (tc) {
+                    // the tensor-core kernel works in place: on a copy
+                    e = cudaMemcpyAsync(dst, src, ck->stride, cudaMemcpyDeviceToDevice, s);
+                    tqd_state v = *psi;
+                    v.amps = dst;
+                    if (e == cudaSuccess) e = launch_tc_block(&v, c, *(const TcBlock *)c->tc_blocks[pp.tc], s);
+                } else {
+                    e = launch_tile_pass(psi, nullptr, c, p, s, src, dst);
+                }
+            }
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -213,15 +265,22 @@ cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
                          double *dev_grads, cudaStream_t s, double *dev_energy, bool prepared, int pass_end,
-                         bool seeded) {
+                         bool seeded, const Checkpoints *ck) {
     cudaError_t e = prepared ? cudaSuccess : launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
-    if (!seeded) e = launch_apply_observable(psi, groups, dev_weights, scale, lam, s, dev_energy);
+    const bool use_ck = c->fused && ck && ck->count > 0;
+    if (!seeded) {
+        // the final state: psi, or the last checkpoint
+        tqd_state fin = *psi;
+        if (use_ck) fin.amps = ck->at(ck->count - 1);
+        e = launch_apply_observable(&fin, groups, dev_weights, scale, lam, s, dev_energy);
+    }
     if (e != cudaSuccess) return e;
     if (c->fused) {
         const int np = pass_end < 0 ? (int)c->tile_passes.size() : pass_end;
+        const int first = use_ck ? np - ck->count : np;
         for (int p = np - 1; p >= 0; --p) {
-            e = launch_tile_pass(psi, lam, c, p, s);
+            e = p >= first ? launch_tile_pass(psi, lam, c, p, s, ck->at(p - first)) : launch_tile_pass(psi, lam, c, p, s);
             if (e != cudaSuccess) return e;
         }
         return launch_grad_finalize(c, tile_grid(c, psi->dtype == TQD_C64 ? 0 : 1, true), dev_grads, s);

@@ -43,6 +43,10 @@ constexpr int TILE_MAX_STAGES = 40;
 constexpr int TILE_MAX_OPS = 240;
 constexpr int TILE_MAX_DIMS = 5;  // TMA tensor rank limit
 
+// Launch flags of a tile pass.  TILE_PSI_RO (reverse sweep): psi is read from
+// a forward checkpoint and only lambda is written back.
+constexpr int TILE_PSI_RO = 1;
+
 // Op types.  Positions are resolved per stage: `pos` < 0x80 is a register
 // position (bit of the register index), `pos` >= 0x80 is thread-index bit
 // (pos & 0x7f).
@@ -110,10 +114,25 @@ constexpr int TILE_MAX_GRAD = 32;                        // gradient ops per pas
 template <bool ADJ> struct RingCfg {
     static constexpr int G = ADJ ? 2 : 3;
     static constexpr int B = ADJ ? 3 : 6;
-    // threads of a block: the groups, and the TMA warp when there is one
+    // threads of a block: the groups, and the TMA warpgroup when there is one
     static constexpr int THREADS = G * TILE_THREADS;
-    static constexpr int THREADS_TMAW = G * TILE_THREADS + 32;
+    static constexpr int THREADS_TMAW = G * TILE_THREADS + 128;
+    // With the TMA warpgroup: registers per thread at launch (the most the
+    // launch bounds allow with THREADS_TMAW threads: five or seven warps per
+    // scheduler), then moved from the TMA warpgroup (setmaxnreg.dec to
+    // REGS_TMA) to the groups (setmaxnreg.inc to REGS_GROUP).  The two shares
+    // add up to the launch's registers exactly:
+    //   G * 256 * REGS_GROUP + 128 * REGS_TMA == THREADS_TMAW * REGS_LAUNCH.
+    static constexpr int REGS_LAUNCH = ADJ ? 96 : 72;
+    static constexpr int REGS_TMA = ADJ ? 32 : 24;
+    static constexpr int REGS_GROUP = ADJ ? 112 : 80;
 };
+static_assert(RingCfg<true>::G * TILE_THREADS * RingCfg<true>::REGS_GROUP + 128 * RingCfg<true>::REGS_TMA ==
+                  RingCfg<true>::THREADS_TMAW * RingCfg<true>::REGS_LAUNCH,
+              "register shares of the reverse ring");
+static_assert(RingCfg<false>::G * TILE_THREADS * RingCfg<false>::REGS_GROUP + 128 * RingCfg<false>::REGS_TMA ==
+                  RingCfg<false>::THREADS_TMAW * RingCfg<false>::REGS_LAUNCH,
+              "register shares of the forward ring");
 // Gradient-partial columns of a ring kernel (threads t and t + 128 of every
 // group share one).
 constexpr int GACC_RING_COLS = TILE_THREADS / 2;

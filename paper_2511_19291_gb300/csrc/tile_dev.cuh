@@ -478,6 +478,28 @@ __device__ __forceinline__ RT<V> grad_diag(uint8_t type, uint8_t pa, uint8_t pb,
     return T(-2) * s;
 }
 
+// Total of w and its sums over the registers whose bit r is set, for every
+// register bit r: halving the array by pair sums at each level costs
+// 2^(R-1) + ... adds for the totals and 2^(R-1) - 1 + ... for the odd
+// entries, 26 adds at R = 4 instead of 15 per gate of a diagonal run.
+template <typename T>
+__device__ __forceinline__ void diag_sums(const T (&w)[NR], T &tot, T (&S)[TILE_R]) {
+    T cur[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) cur[j] = w[j];
+#pragma unroll
+    for (int r = 0; r < TILE_R; ++r) {
+        const int m = NR >> r;
+        T s = cur[1];
+#pragma unroll
+        for (int k = 3; k < m; k += 2) s += cur[k];
+        S[r] = s;
+#pragma unroll
+        for (int k = 0; k < m / 2; ++k) cur[k] = cur[2 * k] + cur[2 * k + 1];
+    }
+    tot = cur[0];
+}
+
 // Share of a diagonal op's derivative (D1 or D2 outside a run).
 template <typename V>
 __device__ __forceinline__ RT<V> grad_diag_op(uint8_t type, uint8_t pa, uint8_t pb, uint8_t gen, const V (&a)[NR],
@@ -847,17 +869,25 @@ __device__ __forceinline__ void tile_issue_load(const TileHead &P, const void *m
     }
 }
 
-// One thread: TMA stores of the tile in `src`, as one bulk group.
+// One thread: TMA stores of the tile in `src`, as one bulk group.  The
+// forward pass stores psi through map_lam (its destination: the source map
+// itself in place, another state for a checkpoint); the reverse sweep stores
+// psi through map_psi unless flags has TILE_PSI_RO (psi read from a forward
+// checkpoint and not needed again) and lambda through map_lam.
 template <typename V, bool ADJ>
 __device__ __forceinline__ void tile_issue_store(const TileHead &P, const void *map_psi, const void *map_lam,
-                                                 V *src, uint64_t tile) {
+                                                 V *src, uint64_t tile, int flags) {
     constexpr int TS = 1 << TILE_K;
     const uint32_t box_bytes = (TS * (uint32_t)sizeof(V)) >> P.n_extra;
     for (int e = 0; e < (1 << P.n_extra); ++e) {
         int c[TILE_MAX_DIMS];
         tile_coords(P, tile, e, c);
-        tma_store(P.rank, map_psi, sptr(src) + e * box_bytes, c);
-        if (ADJ) tma_store(P.rank, map_lam, sptr(src + TS) + e * box_bytes, c);
+        if (!ADJ) {
+            tma_store(P.rank, map_lam, sptr(src) + e * box_bytes, c);
+        } else {
+            if (!(flags & TILE_PSI_RO)) tma_store(P.rank, map_psi, sptr(src) + e * box_bytes, c);
+            tma_store(P.rank, map_lam, sptr(src + TS) + e * box_bytes, c);
+        }
     }
     bulk_commit();
 }
@@ -872,10 +902,11 @@ __device__ __forceinline__ int mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 
 // Gradient partials of the block (gcols columns per gradient op, state
 // precision) added in FP64, one warp per gradient op.  Ends the pass.
+// nw: the warps taking part (the block's first nw).
 template <typename T>
 __device__ __forceinline__ void tile_write_partials(const TileHead &P, const TilePassDev *Pg, const T *gacc, int gcols,
-                                                    double *partials, int pblk) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                                                    double *partials, int pblk, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = warp; k < P.n_grad; k += nw) {
         double t = 0;
         for (int i = lane; i < gcols; i += 32) t += (double)gacc[k * gcols + i];
@@ -892,7 +923,8 @@ __device__ __forceinline__ void tile_write_partials(const TileHead &P, const Til
 // with tile_sync(ctx) (the last one after fence.proxy.async).
 template <typename V, bool ADJ, int NB, typename Runner>
 __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
-                                               const RT<V> *mats, double *partials, int pblk, int *err) {
+                                               const RT<V> *mats, double *partials, int pblk, int *err,
+                                               int flags) {
     __shared__ TileHead P;
     __shared__ int s_timeout;
     copy_words(&P, &Pg->h, sizeof(TileHead));
@@ -971,23 +1003,33 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
         ctx.tile_a = S.tiles + (size_t)cur * NSTATE * TS;
         ctx.tile_b = ctx.tile_a + TS;
         runner.run(ctx);
-        if (tid == 0) tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile);
+        if (tid == 0) tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile, flags);
     }
     if (tid == 0) bulk_wait0();
     if (ADJ) {
         __syncthreads();
         // per-thread partial sums (state precision, about 16 amplitudes x
         // the block's tiles each) are added in FP64, one warp per gradient op
-        tile_write_partials(P, Pg, S.gacc, TILE_THREADS, partials, pblk);
+        tile_write_partials(P, Pg, S.gacc, TILE_THREADS, partials, pblk, TILE_THREADS / 32);
     }
 }
 
+// Register shares of warp-specialised blocks (setmaxnreg, per warpgroup;
+// every warp of the warpgroup executes it).
+template <int N> __device__ __forceinline__ void reg_dealloc() {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <int N> __device__ __forceinline__ void reg_alloc() {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
+
 // The whole pass for one block of G groups of 256 threads sharing a ring of
-// B tile buffers, plus (TMAW) one TMA warp (one block per SM).  Tile k of the
+// B tile buffers, plus (TMAW) one TMA warpgroup (one block per SM).  Tile k of the
 // block's sequence (global tile blockIdx.x + k * gridDim.x) goes through
 // buffer k mod B and is computed by group k mod G.
-//  - TMAW: the TMA warp's first thread issues every copy: it loads the first B
-//    tiles, then for k = 0, 1, ...: waits until tile k is computed
+//  - TMAW: the TMA warpgroup hands most of its registers to the groups
+//    (setmaxnreg; RingCfg's shares) and its first thread issues every copy:
+//    it loads the first B tiles, then for k = 0, 1, ...: waits until tile k is computed
 //    (done[buffer]), stores it, waits until the store has read the buffer and
 //    loads tile k + B into it.  The compute groups never wait for a store.
 //  - A group's first thread waits (bounded) for its tile's load (full[buffer]);
@@ -1000,8 +1042,10 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
 // from each buffer), so the barrier parity it waits on is never a phase stale.
 template <typename V, bool ADJ, int G, int B, bool TMAW, typename Runner>
 __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
-                                               const RT<V> *mats, double *partials, int pblk, int *err) {
+                                               const RT<V> *mats, double *partials, int pblk, int *err,
+                                               int flags) {
     static_assert(B >= G, "a ring needs a buffer per group");
+    static_assert(!TMAW || G == RingCfg<ADJ>::G, "the register shares are set for RingCfg's groups");
     __shared__ TileHead P;
     __shared__ uint64_t fullb[B];
     __shared__ uint64_t doneb[B];
@@ -1032,6 +1076,9 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
             tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
                                     blockIdx.x + (uint64_t)k * gridDim.x);
     if (TMAW && grp == G) {
+        // the TMA warpgroup gives registers to the groups and leaves when its
+        // copies are done (the groups write the gradient partials)
+        reg_dealloc<RingCfg<ADJ>::REGS_TMA>();
         if (tid == (uint32_t)G * TILE_THREADS) {
             for (int k = 0; k < B && (uint64_t)k < n_local; ++k)
                 tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
@@ -1044,7 +1091,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
                     break;
                 }
                 const uint64_t tile = blockIdx.x + k * gridDim.x;
-                tile_issue_store<V, ADJ>(P, map_psi, map_lam, buf, tile);
+                tile_issue_store<V, ADJ>(P, map_psi, map_lam, buf, tile, flags);
                 if (k + B < n_local) {
                     bulk_wait_read0();
                     tile_issue_load<V, ADJ>(P, map_psi, map_lam, buf, fullb + slot, tile + (uint64_t)B * gridDim.x);
@@ -1052,7 +1099,9 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
             }
             bulk_wait0();
         }
+        return;
     } else {
+        if (TMAW) reg_alloc<RingCfg<ADJ>::REGS_GROUP>();
         const uint32_t gtid = tid & (TILE_THREADS - 1);
         TileCtx<V> ctx;
         ctx.pool = S.pool;
@@ -1109,7 +1158,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
                 // without a TMA warp the group's first thread stores the tile,
                 // waits until the store has read the buffer and refills it
                 const uint64_t tile = blockIdx.x + k * gridDim.x;
-                tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile);
+                tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile, flags);
                 if (k + B < n_local) {
                     bulk_wait_read0();
                     tile_issue_load<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, fullb + slot,
@@ -1120,8 +1169,9 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
         if (!TMAW && gtid == 0) bulk_wait0();
     }
     if (ADJ) {
-        __syncthreads();
-        tile_write_partials(P, Pg, S.gacc, GACC_RING_COLS, partials, pblk);
+        // the groups only (the TMA warpgroup has left): named barrier 15
+        asm volatile("bar.sync 15, %0;" ::"n"(G * TILE_THREADS) : "memory");
+        tile_write_partials(P, Pg, S.gacc, GACC_RING_COLS, partials, pblk, G * TILE_THREADS / 32);
     }
 }
 

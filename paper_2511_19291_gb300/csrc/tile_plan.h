@@ -24,8 +24,13 @@ std::vector<TilePlanPass> plan_fused(const tqd_circuit *c, int *prefix_passes);
 bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P);
 
 // Launch one pass (forward: lam == nullptr; reverse sweep with gradients
-// into the circuit's partials when lam != nullptr).
-cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s);
+// into the circuit's partials when lam != nullptr).  Forward: psi is read
+// from psi_src and written to psi_dst (each psi->amps when NULL; both hold
+// psi's qubit count and dtype and do not overlap unless equal).  Reverse: psi
+// is read from psi_src when given and then not written (a forward
+// checkpoint), otherwise read and written in place.
+cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s,
+                             const void *psi_src = nullptr, void *psi_dst = nullptr);
 int tile_grid(const tqd_circuit *c, int dtype, bool adj);
 
 // Host execution of circuit c's fused plan from its descriptors against the

@@ -165,7 +165,10 @@ class Circuit:
     """A gate list planned by the library (plain gate-by-gate or fused passes)."""
 
     def __init__(self, circuit: W.Circuit, mode: str = "fused", tile_qubits: int = 0, low_qubits: int = 0,
-                 device=None, buffers: int = 0, jit: int = 0, max_blocks: int = 0):
+                 device=None, buffers: int = 0, jit: int = 0, max_blocks: int = 0, checkpoints: int | None = None):
+        """checkpoints: forward checkpoints of value_and_grad; None = as many
+        passes as fit in half the free device memory, 0 = none, k = at most k
+        passes."""
         self.spec = circuit
         self.n = circuit.n_qubits
         self.n_params = circuit.n_params
@@ -179,6 +182,9 @@ class Circuit:
         opts.buffers = buffers
         opts.jit = jit
         opts.max_blocks = max_blocks
+        if checkpoints is not None and checkpoints < 0:
+            raise ValueError("checkpoints must be None or >= 0")
+        opts.checkpoints = 0 if checkpoints is None else (_lib.CHECKPOINTS_NONE if checkpoints == 0 else checkpoints)
         h = C.c_void_p()
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(dev):

@@ -102,7 +102,10 @@ def test_gradient_parity_random(mode, dtype, n, ng, seed):
 
 TILE_VARIANTS = {"generic": dict(jit=1), "generic_2buf": dict(jit=1, buffers=2), "specialised": dict(jit=2),
                  "generic_ring": dict(jit=1, buffers=3, max_blocks=2),
-                 "specialised_ring": dict(jit=2, buffers=3, max_blocks=2)}
+                 "specialised_ring": dict(jit=2, buffers=3, max_blocks=2),
+                 # the ring with a TMA warpgroup whose registers go to the groups
+                 "generic_ring_tma": dict(jit=1, buffers=4, max_blocks=2),
+                 "specialised_ring_tma": dict(jit=2, buffers=4, max_blocks=3)}
 
 
 @pytest.mark.parametrize("variant", list(TILE_VARIANTS))
@@ -132,8 +135,9 @@ def test_fused_tile_variants_random(variant, dtype, n, ng, seed):
 
 
 @pytest.mark.parametrize("jit", [1, 2])
+@pytest.mark.parametrize("buffers", [3, 4])
 @pytest.mark.parametrize("n,layers,max_blocks", [(15, 2, 1), (17, 2, 3)])
-def test_ring_many_tiles_per_block(jit, n, layers, max_blocks):
+def test_ring_many_tiles_per_block(jit, buffers, n, layers, max_blocks):
     """Ring kernels with few blocks, so that each block cycles through many
     tiles: buffers are refilled after their stores and (reverse sweep: 3
     buffers, 2 groups) handed from one group to the other.  The ansatz with
@@ -143,7 +147,7 @@ def test_ring_many_tiles_per_block(jit, n, layers, max_blocks):
     terms = W.ising(n)
     ref = oracle.grad_param_shift(circ, params, terms)
     e_ref = oracle.energy(circ, params, terms)
-    kw = dict(jit=jit, buffers=3, max_blocks=max_blocks)
+    kw = dict(jit=jit, buffers=buffers, max_blocks=max_blocks)
     st, _, _ = gpu_state(circ, params, "fused", "c64", **kw)
     assert abs(sim().expval(st, terms).item() - e_ref) < E_TOL["c64"]
     np.testing.assert_allclose(to_numpy(st), oracle.run(circ, params), atol=AMP_TOL["c64"] * 4, rtol=0)
@@ -385,7 +389,8 @@ def test_value_and_grad(mode, dtype, n, layers, extra):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_value_and_grad_permutation_tail(dtype):
+@pytest.mark.parametrize("checkpoints", [None, 0, 2])
+def test_value_and_grad_permutation_tail(dtype, checkpoints):
     """A circuit ending in CNOT, SWAP and X gates: tqd_value_and_grad skips
     the tail passes and conjugates the observable through them (Pauli
     strings with X, Y and Z, so every sign rule is used)."""
@@ -399,7 +404,7 @@ def test_value_and_grad_permutation_tail(dtype):
     terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(91), n, 8)
     e_ref = oracle.energy(circ, params, terms)
     g_ref = oracle.grad_param_shift(circ, params, terms)
-    c = S.Circuit(circ, mode="fused")
+    c = S.Circuit(circ, mode="fused", checkpoints=checkpoints)
     psi = S.State(n, DTYPES[dtype]).reset(0)
     lam = S.State(n, DTYPES[dtype])
     e, g = S.value_and_grad(psi, lam, c, params_tensor(params), terms)
@@ -410,6 +415,107 @@ def test_value_and_grad_permutation_tail(dtype):
     assert ok, worst
     back = to_numpy(psi)
     assert abs(back[0] - 1) < AMP_TOL[dtype] * 200
+
+
+def _adj_bytes_expected(n, dtype, n_passes, k):
+    """Algorithmic bytes of a reverse sweep whose last k passes read psi from
+    forward checkpoints (psi read, lambda read and written) and whose others
+    recompute psi in place (psi and lambda read and written)."""
+    sb = (1 << n) * (8 if dtype == "c64" else 16)
+    return sb * (3 * k + 4 * (n_passes - k))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("checkpoints", [None, 0, 1, 3])
+def test_value_and_grad_checkpoints(dtype, checkpoints):
+    """Forward checkpoints (all passes, none, the last one, the last three):
+    the same energy and gradient as the oracle; psi is never written when
+    every pass has a checkpoint and comes back by recomputation otherwise;
+    the reverse passes that read a checkpoint move 3 states, the others 4."""
+    S = sim()
+    n = 14
+    circ = W.hea_ansatz(n, 3)
+    params = W.config_rng(6).angles(circ.n_params)
+    terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(17), n, 4)
+    e_ref = oracle.energy(circ, params, terms)
+    g_ref = oracle.grad_param_shift(circ, params, terms)
+    c = S.Circuit(circ, mode="fused", checkpoints=checkpoints)
+    psi = S.State(n, DTYPES[dtype]).reset(0)
+    lam = S.State(n, DTYPES[dtype])
+    for rep in range(2):
+        S.profile_enable(True)
+        e, g = S.value_and_grad(psi, lam, c, params_tensor(params), terms)
+        torch.cuda.synchronize()
+        prof = {q["name"]: q for q in S.profile_read()}
+        S.profile_enable(False)
+        assert abs(e.item() - e_ref) < E_TOL[dtype], (rep, e.item(), e_ref)
+        ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype],
+                               hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+        assert ok, worst
+        # the passes that run: those before the ansatz's closing CNOT ladder
+        # (a permutation the observable is conjugated through)
+        n_passes = prof["tile_adj"]["launches"]
+        assert prof["tile_fwd"]["launches"] == n_passes <= c.info()["passes"]
+        k = n_passes if checkpoints is None else min(checkpoints, n_passes)
+        assert prof["tile_adj"]["bytes"] == _adj_bytes_expected(n, dtype, n_passes, k)
+        back = to_numpy(psi)
+        if k == n_passes:
+            assert back[0] == 1 and np.count_nonzero(back) == 1  # untouched
+        else:
+            e0 = np.zeros(1 << n, dtype=complex)
+            e0[0] = 1
+            np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 200, rtol=0)
+
+
+@pytest.mark.parametrize("kw", [dict(max_blocks=5), dict(buffers=4, jit=2), dict(buffers=1, jit=1)])
+def test_value_and_grad_checkpoints_ring(kw):
+    """21 qubits (ring kernels by default; here also the ring with a TMA warp
+    for both directions and the one-buffer generic kernel): checkpoints for
+    the last 5 passes against none, energy against the oracle."""
+    S = sim()
+    n = 21
+    circ = W.hea_ansatz(n, 2)
+    params = W.config_rng(7).angles(circ.n_params)
+    terms = W.ising(n)
+    e_ref = oracle.energy(circ, params, terms)
+    out = {}
+    for ck in (0, 5):
+        c = S.Circuit(circ, mode="fused", checkpoints=ck, **kw)
+        psi = S.State(n, torch.complex64).reset(0)
+        lam = S.State(n, torch.complex64)
+        e, g = S.value_and_grad(psi, lam, c, params_tensor(params), terms)
+        torch.cuda.synchronize()
+        # complex64 rounding over ~100 gates: a few 1e-7 of the observable's norm
+        assert abs(e.item() - e_ref) < 2e-6 * W.observable_l1(terms), (ck, e.item(), e_ref)
+        assert abs(to_numpy(psi)[0] - 1) < 1e-4
+        out[ck] = (g.cpu().numpy(), to_numpy(lam))
+    scale = np.abs(out[0][0]).max()
+    np.testing.assert_allclose(out[5][0], out[0][0], atol=1e-4 * scale, rtol=0)
+    np.testing.assert_allclose(out[5][1], out[0][1], atol=1e-5 * W.observable_l1(terms), rtol=0)
+
+
+def test_value_and_grad_checkpoints_tensor_core():
+    """Forward passes on the tensor cores write their checkpoint through a copy
+    of the previous state (the kernel works in place)."""
+    S = sim()
+    n = 14
+    circ, params = tc_circuit(8100, n, 2)
+    terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(5), n, 3)
+    e_ref, g_ref = oracle.grad_stored(circ, params, terms)
+    c = S.Circuit(circ, mode="tc")
+    psi = S.State(n, torch.complex64).reset(0)
+    lam = S.State(n, torch.complex64)
+    S.profile_enable(True)
+    e, g = S.value_and_grad(psi, lam, c, params_tensor(params), terms)
+    torch.cuda.synchronize()
+    prof = {q["name"]: q for q in S.profile_read()}
+    S.profile_enable(False)
+    assert prof.get("tc_block", {}).get("launches", 0) >= 1
+    assert abs(e.item() - e_ref) < 1e-5
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4, hnorm=W.observable_l1(terms))
+    assert ok, worst
+    back = to_numpy(psi)
+    assert back[0] == 1 and np.count_nonzero(back) == 1
 
 
 @pytest.mark.parametrize("nq,dtype", [(6, "c128"), (12, "c64")])
