@@ -102,9 +102,9 @@ typedef struct {
                              one block per SM whose groups of 256 threads share a ring of tile
                              buffers, each refilled by TMA as soon as its tile is stored
                              (complex64 only; complex128 uses 1); 4 = the ring with one more
-                             warp that issues every store and refill, so the groups never wait
-                             for a store; 0 = default: a ring for complex64 states of 21 qubits
-                             and more, else 1 */
+                             warpgroup that issues every store and refill, so the groups never
+                             wait for a store, and hands most of its registers to the groups;
+                             0 = default: 4 for complex64 states of 21 qubits and more, else 1 */
     uint32_t jit;         /* fused passes run 1 = the generic pass kernel, which reads positions,
                              addresses and matrices from the pass descriptor; 2 = kernels
                              specialised per pass (straight-line code with those fixed, compiled

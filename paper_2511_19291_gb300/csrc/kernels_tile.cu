@@ -115,8 +115,9 @@ static int smem_optin_limit() {
 // the caller asks for them and one block's shared memory holds them.
 enum { TB_ONE = 1, TB_TWO = 2, TB_RING = 3, TB_RING_TMAW = 4 };
 
-// Default ring flavour per direction (set by measurement on the 26-qubit ansatz).
-static int ring_default(bool adj) { return adj ? TB_RING_TMAW : TB_RING; }
+// Default ring flavour (set by measurement on the 26-qubit ansatz): with the
+// TMA warpgroup both ways.
+static int ring_default(bool) { return TB_RING_TMAW; }
 
 template <typename V, bool ADJ>
 static uint32_t max_smem_ring(const tqd_circuit *c, int dt) {

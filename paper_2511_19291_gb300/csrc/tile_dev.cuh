@@ -1028,8 +1028,10 @@ template <int N> __device__ __forceinline__ void reg_alloc() {
 // block's sequence (global tile blockIdx.x + k * gridDim.x) goes through
 // buffer k mod B and is computed by group k mod G.
 //  - TMAW: the TMA warpgroup hands most of its registers to the groups
-//    (setmaxnreg; RingCfg's shares) and its first thread issues every copy:
-//    it loads the first B tiles, then for k = 0, 1, ...: waits until tile k is computed
+//    (setmaxnreg; RingCfg's shares) and issues every copy, from one thread
+//    per group when B is a multiple of G (each group's copies then wait only
+//    for its own stores), else from one thread: it loads the first B tiles
+//    (its share), then for each of its k: waits until tile k is computed
 //    (done[buffer]), stores it, waits until the store has read the buffer and
 //    loads tile k + B into it.  The compute groups never wait for a store.
 //  - A group's first thread waits (bounded) for its tile's load (full[buffer]);
@@ -1079,11 +1081,19 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
         // the TMA warpgroup gives registers to the groups and leaves when its
         // copies are done (the groups write the gradient partials)
         reg_dealloc<RingCfg<ADJ>::REGS_TMA>();
-        if (tid == (uint32_t)G * TILE_THREADS) {
-            for (int k = 0; k < B && (uint64_t)k < n_local; ++k)
+        // NP copying threads, the first of warps 0 .. NP - 1 of the
+        // warpgroup: one per group (thread p copies group p's tiles, k = p
+        // mod G) when every buffer stays with one group (B a multiple of G),
+        // else one for all tiles in their order.  Either way each thread
+        // meets the tiles of a buffer in order, so done[buffer] is in tile
+        // k's phase when its parity is tested.
+        constexpr int NP = B % G == 0 ? G : 1;
+        const uint32_t pw = (tid - (uint32_t)G * TILE_THREADS) >> 5;
+        if ((tid & 31) == 0 && pw < (uint32_t)NP) {
+            for (int k = (int)pw; k < B && (uint64_t)k < n_local; k += NP)
                 tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
                                         blockIdx.x + (uint64_t)k * gridDim.x);
-            for (uint64_t k = 0; k < n_local; ++k) {
+            for (uint64_t k = pw; k < n_local; k += NP) {
                 const int slot = (int)(k % B);
                 V *buf = S.tiles + (size_t)slot * NSTATE * TS;
                 if (!mbar_wait_bounded(doneb + slot, (uint32_t)(k / B) & 1u)) {
