@@ -116,11 +116,12 @@ struct tqd_circuit {
     std::vector<void *> tc_blocks;   // tqd::TcBlock*, forward of passes whose gates all act on qubits 0..5
     tqd::TilePassDev *d_tile_desc;  // [pass][c64, c128] descriptors in device memory
     int *d_err;                  // device error word (bounded waits that gave up, failed checks)
-    // pass-specialised kernels (CUfunction) per [precision][direction][pass],
+    // pass-specialised kernels (CUfunction) per [precision][direction][kind][pass]
+    // (kind: tqd::jit_kind of the buffer layout and whether psi is read-only),
     // compiled on first use; nullptr entries run the generic kernel
     mutable std::mutex jit_mu;
-    mutable std::vector<void *> jit_fn[2][2];
-    mutable bool jit_ready[2][2] = {{false, false}, {false, false}};
+    mutable std::vector<void *> jit_fn[2][2][6];
+    mutable bool jit_ready[2][2][6] = {};
     // forward checkpoints of tqd_value_and_grad (device memory, sized on first use)
     mutable std::mutex ck_mu;
     mutable void *ck_buf = nullptr;

@@ -286,7 +286,7 @@ void emit_access(std::string &o, const char *fn, const char *base, const uint16_
         put(o, "%s<TV, KADJ>(c, a, b, %d, %s%d + %uu);\n", fn, j, base, idx[j], (unsigned)(roff[j] & ~tb));
 }
 
-std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tmaw) {
+std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tmaw, bool psi_ro) {
     const TileHead &h = D.h;
     std::string o;
     o.reserve(1 << 16);
@@ -316,7 +316,10 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
         }
         if (st.sync_mid) o += "tile_sync(c);\n";
         o += "const uint32_t bs = stage_base_st<KADJ>(tl, c.lane, c.warp);\n";
-        emit_access(o, "tile_st", "bs", adj ? st.ld_lo : st.st_lo, adj ? st.ld_hi : st.st_hi, rs, dt);
+        // psi read-only: its last stage leaves psi in registers (what it would
+        // store is never read), so the compiler drops its dead un-applications
+        const char *stfn = (adj && psi_ro && si == h.n_stages - 1) ? "tile_stl" : "tile_st";
+        emit_access(o, stfn, "bs", adj ? st.ld_lo : st.st_lo, adj ? st.ld_hi : st.st_hi, rs, dt);
         if (si == h.n_stages - 1) o += "fence_async_smem();\n";
         o += "tile_sync(c);\n}\n";
     }
@@ -401,11 +404,11 @@ bool jit_wanted(const tqd_circuit *c) {
     return c->n >= 22 && nvrtc().ok && driver().ok;
 }
 
-std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw) {
-    return generate(c->tile_passes[pass].dev[dt], dt, adj, ring, tmaw);
+std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, bool psi_ro) {
+    return generate(c->tile_passes[pass].dev[dt], dt, adj, ring, tmaw, adj && psi_ro);
 }
 
-static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bool tmaw) {
+static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bool tmaw, bool psi_ro) {
     if (!nvrtc().ok || !driver().ok) {
         set_error("specialised pass kernels: NVRTC or the CUDA driver entry points are unavailable");
         return cudaErrorNotSupported;
@@ -421,7 +424,7 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bo
         std::lock_guard<std::mutex> lk(g_cache_mu);
         for (int p = 0; p < np; ++p) {
             if (!adj && dt == 0 && c->tile_passes[p].tc >= 0) continue;  // forward runs on the tensor cores
-            srcs[p] = jit_source(c, p, dt, adj, ring, tmaw);
+            srcs[p] = jit_source(c, p, dt, adj, ring, tmaw, psi_ro);
             if (g_cache.count({dev, srcs[p]}) || first.count(srcs[p])) continue;
             first[srcs[p]] = p;
             need.push_back(p);
@@ -467,28 +470,30 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bo
         }
         g_cache[{dev, srcs[need[i]]}] = f;
     }
-    std::vector<void *> &tab = c->jit_fn[dt][adj ? 1 : 0];
+    const int kind = jit_kind(ring, tmaw, psi_ro);
+    std::vector<void *> &tab = c->jit_fn[dt][adj ? 1 : 0][kind];
     tab.assign(np, nullptr);
     for (int p = 0; p < np; ++p)
         if (!srcs[p].empty()) tab[p] = (void *)g_cache.at({dev, srcs[p]});
-    c->jit_ready[dt][adj ? 1 : 0] = true;
+    c->jit_ready[dt][adj ? 1 : 0][kind] = true;
     return cudaSuccess;
 }
 
-cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, cudaStream_t s,
-                         CUfunction *out) {
+cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, bool psi_ro,
+                         cudaStream_t s, CUfunction *out) {
     *out = nullptr;
     if (!jit_wanted(c)) return cudaSuccess;
+    psi_ro = adj && psi_ro;
     std::lock_guard<std::mutex> lk(c->jit_mu);
-    const int di = adj ? 1 : 0;
-    if (!c->jit_ready[dt][di]) {
+    const int di = adj ? 1 : 0, kind = jit_kind(ring, tmaw, psi_ro);
+    if (!c->jit_ready[dt][di][kind]) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
             return cudaSuccess;  // no module loads inside a capture: generic kernel
-        const cudaError_t e = prepare(c, dt, adj, ring, tmaw);
+        const cudaError_t e = prepare(c, dt, adj, ring, tmaw, psi_ro);
         if (e != cudaSuccess) return e;
     }
-    const std::vector<void *> &tab = c->jit_fn[dt][di];
+    const std::vector<void *> &tab = c->jit_fn[dt][di][kind];
     if (pass < (int)tab.size()) *out = (CUfunction)tab[pass];
     return cudaSuccess;
 }
@@ -534,13 +539,14 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
         for (auto &p : passes)
             for (int dt = 0; dt < 2; ++dt)
                 for (int adj = 0; adj < 2; ++adj)
-                    for (int ring = 0; ring < (dt == 0 ? 3 : 1); ++ring) {
-                        std::string src = generate(p.dev[dt], dt, adj != 0, ring != 0, ring == 2);
-                        if (seen.emplace(src, 1).second) {
-                            srcs.push_back(std::move(src));
-                            launch_regs.push_back(ring == 2 ? tmaw_launch_regs(adj != 0) : 0);
+                    for (int ring = 0; ring < (dt == 0 ? 3 : 1); ++ring)
+                        for (int ro = 0; ro < (adj ? 2 : 1); ++ro) {
+                            std::string src = generate(p.dev[dt], dt, adj != 0, ring != 0, ring == 2, ro != 0);
+                            if (seen.emplace(src, 1).second) {
+                                srcs.push_back(std::move(src));
+                                launch_regs.push_back(ring == 2 ? tmaw_launch_regs(adj != 0) : 0);
+                            }
                         }
-                    }
     }
     std::vector<std::string> logs(srcs.size());
     std::vector<char> ok(srcs.size(), 0);
@@ -574,7 +580,8 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
 
 void jit_release(tqd_circuit *c) {
     for (auto &d : c->jit_fn)
-        for (auto &v : d) v.clear();
+        for (auto &k : d)
+            for (auto &v : k) v.clear();
 }
 
 }  // namespace tqd

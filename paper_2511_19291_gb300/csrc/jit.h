@@ -24,17 +24,22 @@ bool jit_wanted(const tqd_circuit *c);
 
 // Source text of pass `pass`'s specialised kernel (dt: 0 complex64, 1 complex128).
 // `ring`: the kernel runs on a ring of tile buffers (tile_pass_ring) instead of
-// one buffer per block (tile_pass_body); `tmaw`: the ring has a TMA warp.
-std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw);
+// one buffer per block (tile_pass_body); `tmaw`: the ring has a TMA warpgroup;
+// `psi_ro` (reverse sweep): psi comes from a forward checkpoint and is not
+// written back, so the last stage stores lambda only.
+std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, bool psi_ro);
 
-// The specialised kernel of pass `pass`, compiling every pass of (dt, adj)
-// on first use.  *out = nullptr means "run the generic kernel": the circuit
+// Index of a kernel kind in tqd_circuit::jit_fn.
+inline int jit_kind(bool ring, bool tmaw, bool psi_ro) { return (ring ? (tmaw ? 2 : 1) : 0) + (psi_ro ? 3 : 0); }
+
+// The specialised kernel of pass `pass`, compiling every pass of (dt, adj,
+// kind) on first use.  *out = nullptr means "run the generic kernel": the circuit
 // does not want specialised kernels, NVRTC is unavailable in the default
 // mode, the pass is replaced by a tensor-core block, or s is capturing a
 // graph before the kernels exist.  Errors: NVRTC missing when the circuit
 // requires it (cudaErrorNotSupported) or a failed compile / module load.
-cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, cudaStream_t s,
-                         CUfunction *out);
+cudaError_t jit_function(const tqd_circuit *c, int pass, int dt, bool adj, bool ring, bool tmaw, bool psi_ro,
+                         cudaStream_t s, CUfunction *out);
 
 // Registers per thread kernel f launches with (-1 when unknown).
 int jit_num_regs(CUfunction f);

@@ -257,17 +257,17 @@ static cudaError_t launch_t(const void *psi_src, void *psi_dst, tqd_state *lam, 
     if (tb == TB_TWO) return launch_nb<V, ADJ, 2>(ma, mb, c, pass, flags, s);
     // the pass-specialised kernel when the circuit has one: same descriptor,
     // shared memory and grid as the generic kernel of the same kind
-    const bool ring = tb == TB_RING || tb == TB_RING_TMAW;
+    const bool ring = tb == TB_RING || tb == TB_RING_TMAW, ro = (flags & TILE_PSI_RO) != 0;
     bool tmaw = tb == TB_RING_TMAW;
     CUfunction f = nullptr;
-    e = jit_function(c, pass, dt, ADJ, ring, tmaw, s, &f);
+    e = jit_function(c, pass, dt, ADJ, ring, tmaw, ro, s, &f);
     if (e != cudaSuccess) return e;
     if (tmaw && (f ? jit_num_regs(f) : ring_tmaw_regs<V, ADJ>()) != RingCfg<ADJ>::REGS_LAUNCH) {
         // the TMA warpgroup's register shares add up only for a launch with
         // REGS_LAUNCH registers per thread: the ring without it instead
         tmaw = false;
         f = nullptr;
-        e = jit_function(c, pass, dt, ADJ, ring, false, s, &f);
+        e = jit_function(c, pass, dt, ADJ, ring, false, ro, s, &f);
         if (e != cudaSuccess) return e;
     }
     if (!f) {

@@ -689,6 +689,29 @@ __device__ __forceinline__ void tile_st2(const TileCtx<V> &c, const V (&a)[NR], 
     }
 }
 
+// Lambda only, as tile_st / tile_st2 (a reverse stage whose psi is not
+// needed any more: the last stage of a pass that read psi from a forward
+// checkpoint).
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_stl(const TileCtx<V> &c, const V (&a)[NR], const V (&b)[NR], int j,
+                                         uint32_t ad) {
+    static_assert(ADJ, "lambda exists in the reverse sweep only");
+    (void)a;
+    int *err = c.err;
+    (void)err;
+    if (TQD_IDX_OK(ad, (uint32_t)(1 << TILE_K))) c.tile_b[ad] = b[j];
+}
+template <typename V, bool ADJ>
+__device__ __forceinline__ void tile_stl2(const TileCtx<V> &c, const V (&a)[NR], const V (&b)[NR], int j0, int j1,
+                                          uint32_t ad) {
+    static_assert(ADJ && sizeof(V) == 8, "lambda pairs of complex64 amplitudes");
+    (void)a;
+    int *err = c.err;
+    (void)err;
+    if (TQD_IDX_OK(ad + 1, (uint32_t)(1 << TILE_K)))
+        *reinterpret_cast<float4 *>(c.tile_b + ad) = make_float4(b[j0].x, b[j0].y, b[j1].x, b[j1].y);
+}
+
 // The generic stage runner: interprets the pass's stage and op lists.
 template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
     __device__ __forceinline__ void init(const TileCtx<V> &) {}

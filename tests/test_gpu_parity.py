@@ -427,7 +427,8 @@ def _adj_bytes_expected(n, dtype, n_passes, k):
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("checkpoints", [None, 0, 1, 3])
-def test_value_and_grad_checkpoints(dtype, checkpoints):
+@pytest.mark.parametrize("jit", [1, 2])
+def test_value_and_grad_checkpoints(dtype, checkpoints, jit):
     """Forward checkpoints (all passes, none, the last one, the last three):
     the same energy and gradient as the oracle; psi is never written when
     every pass has a checkpoint and comes back by recomputation otherwise;
@@ -439,7 +440,7 @@ def test_value_and_grad_checkpoints(dtype, checkpoints):
     terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(17), n, 4)
     e_ref = oracle.energy(circ, params, terms)
     g_ref = oracle.grad_param_shift(circ, params, terms)
-    c = S.Circuit(circ, mode="fused", checkpoints=checkpoints)
+    c = S.Circuit(circ, mode="fused", checkpoints=checkpoints, jit=jit)
     psi = S.State(n, DTYPES[dtype]).reset(0)
     lam = S.State(n, DTYPES[dtype])
     for rep in range(2):
@@ -467,10 +468,13 @@ def test_value_and_grad_checkpoints(dtype, checkpoints):
             np.testing.assert_allclose(back, e0, atol=AMP_TOL[dtype] * 200, rtol=0)
 
 
-@pytest.mark.parametrize("kw", [dict(max_blocks=5), dict(buffers=4, jit=2), dict(buffers=1, jit=1)])
+@pytest.mark.parametrize("kw", [dict(max_blocks=5), dict(buffers=4, jit=2), dict(buffers=3, jit=2, max_blocks=7),
+                                dict(buffers=1, jit=1)])
 def test_value_and_grad_checkpoints_ring(kw):
-    """21 qubits (ring kernels by default; here also the ring with a TMA warp
-    for both directions and the one-buffer generic kernel): checkpoints for
+    """21 qubits: the generic ring kernels with the TMA warpgroup (default
+    below 22 qubits), the pass-specialised ones with and without it (their
+    reverse kernels for passes that read psi from a checkpoint store lambda
+    only in the last stage) and the one-buffer generic kernel: checkpoints for
     the last 5 passes against none, energy against the oracle."""
     S = sim()
     n = 21
