@@ -320,8 +320,11 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
         // store is never read), so the compiler drops its dead un-applications
         const char *stfn = (adj && psi_ro && si == h.n_stages - 1) ? "tile_stl" : "tile_st";
         emit_access(o, stfn, "bs", adj ? st.ld_lo : st.st_lo, adj ? st.ld_hi : st.st_hi, rs, dt);
+        // the ring with a TMA warpgroup: after the last stage each thread
+        // signals the tile's end itself (no barrier)
         if (si == h.n_stages - 1) o += "fence_async_smem();\n";
-        o += "tile_sync(c);\n}\n";
+        if (si < h.n_stages - 1 || !(ring && tmaw)) o += "tile_sync(c);\n";
+        o += "}\n";
     }
     o += "}\n};\n}  // namespace tqd\n";
     // the generic kernels' launch bounds (tile_min_blocks<V, ADJ, 1>; ring: one block of G groups)

@@ -605,6 +605,8 @@ template <typename V> struct TileCtx {
     uint32_t tid;            // thread index within the group of 256 that works on the tile
     int lane, warp;
     uint32_t bar_id;         // named barrier of that group (0 = the whole block of 256)
+    bool end_sync;           // the last stage ends with the group's barrier too (else each
+                             // thread signals the tile's end itself, after its fence)
     int *err;
 };
 
@@ -768,7 +770,7 @@ template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
             }
             // the last stage's writes are read next by the TMA store
             if (si == c.n_stages - 1) fence_async_smem();
-            tile_sync(c);
+            if (si < c.n_stages - 1 || c.end_sync) tile_sync(c);
         }
     }
 };
@@ -997,6 +999,7 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     ctx.lane = tid & 31;
     ctx.warp = tid >> 5;
     ctx.bar_id = 0;
+    ctx.end_sync = true;
     ctx.err = err;
     Runner runner;  // per-thread values of the pass that do not depend on the tile
     runner.init(ctx);
@@ -1058,9 +1061,11 @@ template <int N> __device__ __forceinline__ void reg_alloc() {
 //    (done[buffer]), stores it, waits until the store has read the buffer and
 //    loads tile k + B into it.  The compute groups never wait for a store.
 //  - A group's first thread waits (bounded) for its tile's load (full[buffer]);
-//    the group runs every stage, meeting on its own named barrier, and the
-//    first thread marks the buffer done (TMAW), or else stores the tile itself,
-//    waits until the store has read the buffer and loads tile k + B into it.
+//    the group runs every stage, meeting on its own named barrier after each
+//    but the last; then (TMAW) each thread fences its writes and arrives on
+//    done[buffer] (256 arrivals complete it) and goes on, or else the group
+//    meets once more and its first thread stores the tile itself, waits until
+//    the store has read the buffer and loads tile k + B into it.
 // Up to B - G tiles are on their way in while G are computed.  A buffer passes
 // between groups when B is not a multiple of G: the waiter for tile k + B
 // first waits until tile k has been taken (gen[buffer] counts the tiles taken
@@ -1081,7 +1086,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     if (tid == 0) {
         for (int i = 0; i < B; ++i) {
             mbar_init(fullb + i, 1);
-            mbar_init(doneb + i, 1);
+            mbar_init(doneb + i, TILE_THREADS);  // TMAW: every thread of the group arrives
             gen[i] = 0;
         }
         mbar_fence_init();
@@ -1149,6 +1154,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
         ctx.lane = gtid & 31;
         ctx.warp = gtid >> 5;
         ctx.bar_id = 1 + grp;
+        ctx.end_sync = !TMAW;
         ctx.err = err;
         Runner runner;
         runner.init(ctx);
@@ -1183,10 +1189,11 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
             ctx.tile_b = ctx.tile_a + TS;
             runner.run(ctx);
             if (TMAW) {
-                // every thread of the group has written the tile and fenced it
-                // for the async proxy (the last stage's barrier): hand it to
-                // the TMA warp
-                if (gtid == 0) mbar_arrive(doneb + slot);
+                // each thread has written its part of the tile and fenced it for
+                // the async proxy: its arrival hands that part to the TMA
+                // warpgroup (the tile is done when all 256 have arrived), and
+                // the thread goes on to its next tile without meeting the others
+                mbar_arrive(doneb + slot);
             } else if (gtid == 0) {
                 // without a TMA warp the group's first thread stores the tile,
                 // waits until the store has read the buffer and refills it
