@@ -15,7 +15,9 @@ same metric end to end with host buffers (e2e), and the CPU oracle timed on
 a bounded sample of the workload (cpu_baseline).
 
 Multi-GPU: the single-state path does not shard (replicas only): every rank
-runs its own replica; value = steps of all ranks / max time over ranks.
+runs its own replica; value = steps of all ranks / max time over ranks.  The
+batched measurement shards its circuits over the ranks (no collective on the
+data path) and reports all circuits / the slowest rank's time.
 
 ``--impl reference`` times the CPU oracle on the same workload (bounded
 samples extrapolated to grad-evals/s); under torchrun only rank 0 runs it.
@@ -279,32 +281,50 @@ def sweep_bench(S, torch, dev, n, barrier, reps=5):
 
 
 # ------------------------------------------------------- batched measurement
-def batch_bench(S, torch, dev, count, barrier, reps=3):
+def batch_bench(S, torch, dev, count, barrier, reps=3, rank=0, world=1):
     """512 ragged circuits (widths 10..20, depths 2..12, sum_i Z_i): forward +
     adjoint gradient of every circuit per run.  Fused: one CUDA-graph launch
-    (autotuned); plain: every gate its own launch, issued by the host."""
+    (autotuned); plain: every gate its own launch, issued by the host.  With
+    several ranks the circuits are sharded (greedy by 2^width x gates, no
+    collective on the data path); the time is the slowest rank's and the rate
+    counts all circuits (the total work is fixed: strong scaling)."""
+    from paper_2511_19291_gb300 import shard as SH
     from paper_2511_19291_gb300 import workloads as W
-    wl = W.batched_workload(count=count)
-    out = {"circuits": count, "widths": "10..20", "depths": "2..12", "observable": "sum_i Z_i"}
+    wl_all = W.batched_workload(count=count)
+    mine = SH.shard(SH.workload_costs(wl_all), world, rank)
+    wl = [wl_all[i] for i in mine]
+    out = {"circuits": count, "widths": "10..20", "depths": "2..12", "observable": "sum_i Z_i",
+           "ranks": world, "scaling": "strong" if world > 1 else None, "circuits_this_rank": len(wl)}
+
+    def slowest(ms):
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
     for mode in ("fused", "plain"):
-        circs = [S.Circuit(w.circuit, mode=mode, device=dev) for w in wl]
-        b = S.Batch(circs, [w.terms for w in wl], autotune=(mode == "fused"), plain=(mode == "plain"))
-        b.set_params([w.params for w in wl])
-        b.run()
+        k = reps if mode == "fused" else 1
+        info = {}
+        if wl:
+            circs = [S.Circuit(w.circuit, mode=mode, device=dev) for w in wl]
+            b = S.Batch(circs, [w.terms for w in wl], autotune=(mode == "fused"), plain=(mode == "plain"))
+            b.set_params([w.params for w in wl])
+            b.run()
         barrier()
         a = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
-        k = reps if mode == "fused" else 1
         a.record()
-        for _ in range(k):
+        for _ in range(k if wl else 0):
             b.run()
         e.record()
         barrier()
-        ms = a.elapsed_time(e) / k
+        ms = slowest(a.elapsed_time(e) / k)
         out[mode] = {"grad_evals_per_s": count / (ms / 1000.0), "ms_per_batch": ms, "runs": k}
-        if mode == "fused":
-            out[mode].update(b.info())
-        del b, circs
+        if wl:
+            if mode == "fused":
+                out[mode].update(b.info())
+            del b, circs
     out["fused_over_plain"] = out["fused"]["grad_evals_per_s"] / out["plain"]["grad_evals_per_s"]
     return out
 
@@ -504,7 +524,7 @@ def main():
 
     batched = None
     if args.batch_count > 0:
-        batched = batch_bench(S, torch, dev, args.batch_count, barrier)
+        batched = batch_bench(S, torch, dev, args.batch_count, barrier, rank=rank, world=world)
 
     qft = None
     if args.qft_n > 0:
