@@ -42,7 +42,8 @@ def back_to_zero(psi, tol):
 
 
 def test_main_workload_26q():
-    """26 qubits, 20 layers, Ising: fused c64, gate-by-gate c64, fused c128."""
+    """26 qubits, 20 layers, Ising: fused c64, gate-by-gate c64 and
+    tqd_value_and_grad c64 (the benchmark's call) against fused c128."""
     w = W.workload_main()
     h1 = W.observable_l1(w.terms)
     e_f, g_f, psi = energy_and_grad(w.circuit, w.params, w.terms, torch.complex64, "fused")
@@ -54,6 +55,23 @@ def test_main_workload_26q():
     back_to_zero(psi, 1e-10)
     del psi
     torch.cuda.empty_cache()
+    # the call bench.py times: tqd_value_and_grad, forward checkpoints for
+    # every pass (psi only read), reverse passes reading psi there, the
+    # closing CNOT ring folded into the observable
+    S = sim()
+    c = S.Circuit(w.circuit)
+    psi = S.State(26, torch.complex64).reset(0)
+    lam = S.State(26, torch.complex64)
+    e_v, g_v = S.value_and_grad(psi, lam, c, params_tensor(w.params), w.terms)
+    torch.cuda.synchronize()
+    e_v = e_v.item()
+    g_v = g_v.cpu().numpy()
+    t = psi.tensor
+    assert t[0].item() == 1 and int(torch.count_nonzero(t).item()) == 1  # never written
+    del psi, lam, c
+    torch.cuda.empty_cache()
+    assert abs(e_v - e_d) < 1e-5
+    assert grad_close(g_v, g_d, 1e-4, hnorm=h1)[0]
     print(f"\n26q: E c64 fused {e_f:.10f} plain {e_p:.10f} c128 {e_d:.14f}; "
           f"max|dg| fused {np.max(np.abs(g_f - g_d)):.2e} plain {np.max(np.abs(g_p - g_d)):.2e} (||H||_1 {h1})")
     assert abs(e_f - e_d) < 1e-5 and abs(e_p - e_d) < 1e-5
