@@ -314,7 +314,8 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
                 emit_apply(o, D, D.ops[k], true);
             }
         }
-        if (st.sync_mid) o += "tile_sync(c);\n";
+        if (st.sync_mid == SYNC_GROUP) o += "tile_sync(c);\n";
+        else if (st.sync_mid == SYNC_WARP) o += "__syncwarp();\n";
         o += "const uint32_t bs = stage_base_st<KADJ>(tl, c.lane, c.warp);\n";
         // psi read-only: its last stage leaves psi in registers (what it would
         // store is never read), so the compiler drops its dead un-applications
@@ -323,7 +324,14 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
         // the ring with a TMA warpgroup: after the last stage each thread
         // signals the tile's end itself (no barrier)
         if (si == h.n_stages - 1) o += "fence_async_smem();\n";
-        if (si < h.n_stages - 1 || !(ring && tmaw)) o += "tile_sync(c);\n";
+        if (si < h.n_stages - 1) {
+            // between stages s and s + 1 of either direction: sync_end[s]
+            const uint16_t lvl = D.stages[adj ? s - 1 : s].sync_end;
+            if (lvl == SYNC_GROUP) o += "tile_sync(c);\n";
+            else if (lvl == SYNC_WARP) o += "__syncwarp();\n";
+        } else if (!(ring && tmaw)) {
+            o += "tile_sync(c);\n";
+        }
         o += "}\n";
     }
     o += "}\n};\n}  // namespace tqd\n";

@@ -85,8 +85,9 @@ uint64_t splitmix(uint64_t &s) {
 }
 
 // One pass over every tile of psi, forward or reverse, from descriptor D.
-// Returns false when a stage that moves amplitudes between threads lacks
-// its mid-stage barrier flag.
+// Returns false when a barrier flag is weaker than the address tables allow
+// (a point marked SYNC_NONE where a thread meets another thread's amplitudes,
+// or SYNC_WARP where a warp meets another warp's).
 bool run_pass(const tqd_circuit *c, const TilePlanPass &P, int dt, const double *params, bool rev,
               std::vector<cplx> &psi) {
     const TilePassDev &D = P.dev[dt];
@@ -100,20 +101,30 @@ bool run_pass(const tqd_circuit *c, const TilePlanPass &P, int dt, const double 
         if (D.ops[k].type != TOP_DG && D.ops[k].type != TOP_CX && D.ops[k].type != TOP_SW)
             op_m[k] = matrix_of(c, D.op_gate[k], params);
     for (int k = 0; k < D.h.n_subs; ++k) sub_m[k] = matrix_of(c, D.sub_gate[k], params);
-    // the flag: a stage without it must store only to addresses the same thread loaded
+    // the barrier flags, from the tables: at a point marked SYNC_NONE every
+    // thread accesses the same addresses on both sides, at one marked
+    // SYNC_WARP every warp does (a warp's 512 addresses)
+    auto addr_set = [&](const TileStage &st, bool ld, int t0, int nthr) {
+        std::vector<uint32_t> v;
+        for (int t = t0; t < t0 + nthr; ++t)
+            for (int j = 0; j < (1 << TILE_R); ++j)
+                v.push_back(ld ? (st.ld_lo[t & 31] ^ st.ld_hi[t >> 5] ^ st.ld_roff[j])
+                               : (st.st_lo[t & 31] ^ st.st_hi[t >> 5] ^ st.st_roff[j]));
+        std::sort(v.begin(), v.end());
+        return v;
+    };
+    auto point_ok = [&](uint16_t lvl, const TileStage &a, bool a_ld, const TileStage &b, bool b_ld) {
+        if (lvl == SYNC_GROUP) return true;
+        if (lvl != SYNC_NONE && lvl != SYNC_WARP) return false;
+        const int width = lvl == SYNC_NONE ? 1 : 32;
+        for (int t0 = 0; t0 < TILE_THREADS; t0 += width)
+            if (addr_set(a, a_ld, t0, width) != addr_set(b, b_ld, t0, width)) return false;
+        return true;
+    };
     for (int s = 0; s < D.h.n_stages; ++s) {
         const TileStage &st = D.stages[s];
-        if (st.sync_mid) continue;
-        for (int t = 0; t < TILE_THREADS; ++t) {
-            uint32_t ld[1 << TILE_R], sv[1 << TILE_R];
-            for (int j = 0; j < (1 << TILE_R); ++j) {
-                ld[j] = st.ld_lo[t & 31] ^ st.ld_hi[t >> 5] ^ st.ld_roff[j];
-                sv[j] = st.st_lo[t & 31] ^ st.st_hi[t >> 5] ^ st.st_roff[j];
-            }
-            std::sort(ld, ld + (1 << TILE_R));
-            std::sort(sv, sv + (1 << TILE_R));
-            if (!std::equal(ld, ld + (1 << TILE_R), sv)) return false;
-        }
+        if (!point_ok(st.sync_mid, st, true, st, false)) return false;
+        if (s + 1 < D.h.n_stages && !point_ok(st.sync_end, st, false, D.stages[s + 1], true)) return false;
     }
     for (uint64_t t = 0; t < (1ull << nt); ++t) {
         uint64_t origin = 0;

@@ -11,12 +11,23 @@
 //    2^extra TMA operations per tile.
 // 3. Stages.  A stage fixes 4 register bits and takes, in gate order, every
 //    gate whose predecessors are scheduled or taken by the same stage and
-//    whose dense qubits fit in the register set.  Thread-index bits are assigned so that a
-//    half-warp's shared-memory accesses fall in different banks under the
-//    128-byte swizzle.
+//    whose dense qubits fit in the register set.  Thread-index bits are
+//    assigned so that a half-warp's shared-memory accesses fall in different
+//    banks under the 128-byte swizzle.
+// 4. Barriers.  Between a stage's loads and stores, and between one stage's
+//    stores and the next one's loads, the group of 256 threads meets unless
+//    every warp (then __syncwarp) or every thread (then nothing) accesses the
+//    same addresses on both sides, which the address tables decide exactly.
+//    Warp bits fixed to three bankless bits that are thread bits in every
+//    stage make more points warp-local; that choice is taken when it needs
+//    fewer group barriers.  (Taking warp bits among the bank-relevant bits
+//    instead made about half the stage changes of the 26-qubit ansatz
+//    warp-local but slowed its passes by about 30 %: bank conflicts cost more
+//    than the barriers saved.)
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "launch.h"
@@ -120,6 +131,85 @@ Aff perm_map(const GateH &g, const int *loc) {
         m.v = 1u << loc[g.w[0]];
     }
     return m;
+}
+
+// Lowest local bit that plays no part in the shared-memory bank of an
+// amplitude under the 128-byte swizzle (complex64: bits 0..6; complex128:
+// bits 0..5).
+int first_bankless_bit(int dt) { return dt == 0 ? 7 : 6; }
+
+// Thread bits of a stage (u -> local bit): the lane bits first, one
+// representative of each bank class under the swizzle, so that a half-warp's
+// accesses fall in different banks, then the other free bits in ascending
+// order; the last three are the warp bits.  `warp` (3 bits, free in the
+// stage, bankless) fixes the warp bits instead; the lanes are then the other
+// free bits.
+std::vector<int> thread_bits(const bool *is_reg, int dt, const std::vector<int> &warp) {
+    std::vector<int> lanes;
+    auto taken = [&](int b) {
+        return std::find(lanes.begin(), lanes.end(), b) != lanes.end() ||
+               std::find(warp.begin(), warp.end(), b) != warp.end();
+    };
+    const int classes64[4][2] = {{0, -1}, {1, 4}, {2, 5}, {3, 6}};
+    const int classes128[3][2] = {{0, 3}, {1, 4}, {2, 5}};
+    const int ncls = dt == 0 ? 4 : 3;
+    for (int k = 0; k < ncls; ++k)
+        for (int t = 0; t < 2; ++t) {
+            const int b = dt == 0 ? classes64[k][t] : classes128[k][t];
+            if (b >= 0 && !is_reg[b] && !taken(b)) {
+                lanes.push_back(b);
+                break;
+            }
+        }
+    for (int b = 0; b < TILE_K; ++b)
+        if (!is_reg[b] && !taken(b)) lanes.push_back(b);
+    if (!warp.empty()) {
+        lanes.resize(TILE_T - 3);
+        lanes.insert(lanes.end(), warp.begin(), warp.end());
+    }
+    lanes.resize(TILE_T);
+    return lanes;
+}
+
+// Local indices each thread of a stage loads or stores (through map M):
+// out[t] = the 16 indices of thread t, sorted.
+void thread_sets(const Aff &M, const int *reg, const std::vector<int> &thr,
+                 std::vector<std::array<uint32_t, 1 << TILE_R>> &out) {
+    out.resize(TILE_THREADS);
+    for (int t = 0; t < TILE_THREADS; ++t) {
+        uint32_t ot = 0;
+        for (int u = 0; u < TILE_T; ++u)
+            if ((t >> u) & 1) ot |= 1u << thr[u];
+        for (int j = 0; j < (1 << TILE_R); ++j) {
+            uint32_t o = ot;
+            for (int r = 0; r < TILE_R; ++r)
+                if ((j >> r) & 1) o |= 1u << reg[r];
+            out[t][j] = M(o);
+        }
+        std::sort(out[t].begin(), out[t].end());
+    }
+}
+
+// The barrier a point between two accesses of the tile needs, from the
+// index sets before (a) and after (b) it: SYNC_NONE when every thread's two
+// sets are equal (each thread only meets its own amplitudes), SYNC_WARP when
+// every warp's are (each warp only meets its own), else SYNC_GROUP.
+uint16_t sync_level(const std::vector<std::array<uint32_t, 1 << TILE_R>> &a,
+                    const std::vector<std::array<uint32_t, 1 << TILE_R>> &b) {
+    bool per_thread = true;
+    for (int t = 0; t < TILE_THREADS && per_thread; ++t) per_thread = a[t] == b[t];
+    if (per_thread) return SYNC_NONE;
+    for (int w = 0; w < TILE_THREADS / 32; ++w) {
+        std::vector<uint32_t> x, y;
+        for (int l = 0; l < 32; ++l) {
+            x.insert(x.end(), a[w * 32 + l].begin(), a[w * 32 + l].end());
+            y.insert(y.end(), b[w * 32 + l].begin(), b[w * 32 + l].end());
+        }
+        std::sort(x.begin(), x.end());
+        std::sort(y.begin(), y.end());
+        if (x != y) return SYNC_GROUP;
+    }
+    return SYNC_WARP;
 }
 
 }  // namespace
@@ -411,6 +501,72 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
         stages.push_back(st);
     }
     if ((int)stages.size() > TILE_MAX_STAGES) return false;
+    const int S = (int)stages.size();
+
+    // Load and store maps of every stage: the permutation gates at its start
+    // become the load map F = f1 o f2 o ..., those at its end the store map
+    // G = ... o g2 o g1.
+    std::vector<Aff> Fm(S), Gm(S);
+    std::vector<int> lead_ends(S), trail_begins(S);
+    for (int s = 0; s < S; ++s) {
+        const StageH &sh = stages[s];
+        int lead_end = sh.begin;
+        while (lead_end < sh.end && is_perm_gate(c->gates[P.gates[order[lead_end]]].kind)) ++lead_end;
+        int trail_begin = sh.end;
+        while (trail_begin > lead_end && is_perm_gate(c->gates[P.gates[order[trail_begin - 1]]].kind))
+            --trail_begin;
+        for (int q = sh.begin; q < lead_end; ++q) Fm[s] = compose(Fm[s], perm_map(c->gates[P.gates[order[q]]], loc.data()));
+        for (int q = trail_begin; q < sh.end; ++q) Gm[s] = compose(perm_map(c->gates[P.gates[order[q]]], loc.data()), Gm[s]);
+        lead_ends[s] = lead_end;
+        trail_begins[s] = trail_begin;
+    }
+
+    // Thread bits of every stage and the barriers they need, per precision.
+    // Two candidates: the bank-spreading default of each stage, and the same
+    // lanes with the warp bits fixed to three bankless bits that are thread
+    // bits in every stage (a warp then keeps its part of the tile from stage
+    // to stage unless a permutation moves it).  The one with fewer group
+    // barriers (then fewer warp barriers) wins.
+    struct ThreadPlan {
+        std::vector<std::vector<int>> thr;     // [stage][u]
+        std::vector<uint16_t> mid, end;        // sync levels
+        int cost = 0;
+    };
+    auto make_plan = [&](int dt, const std::vector<int> &warp) {
+        ThreadPlan tp;
+        tp.thr.resize(S);
+        tp.mid.resize(S);
+        tp.end.assign(S, SYNC_GROUP);
+        std::vector<std::array<uint32_t, 1 << TILE_R>> ld, st, prev_st;
+        for (int s = 0; s < S; ++s) {
+            bool is_reg[TILE_K] = {false};
+            for (int r = 0; r < TILE_R; ++r) is_reg[stages[s].reg[r]] = true;
+            tp.thr[s] = thread_bits(is_reg, dt, warp);
+            thread_sets(Fm[s], stages[s].reg, tp.thr[s], ld);
+            thread_sets(Gm[s], stages[s].reg, tp.thr[s], st);
+            tp.mid[s] = sync_level(ld, st);
+            if (s > 0) tp.end[s - 1] = sync_level(prev_st, ld);
+            prev_st.swap(st);
+        }
+        auto weight = [](uint16_t l) { return l == SYNC_GROUP ? 16 : l == SYNC_WARP ? 1 : 0; };
+        for (int s = 0; s < S; ++s) tp.cost += weight(tp.mid[s]) + (s + 1 < S ? weight(tp.end[s]) : 0);
+        return tp;
+    };
+    ThreadPlan tplan[2];
+    for (int dt = 0; dt < 2; ++dt) {
+        tplan[dt] = make_plan(dt, {});
+        std::vector<int> common;  // bankless bits that are thread bits in every stage, highest first
+        for (int b = TILE_K - 1; b >= first_bankless_bit(dt); --b) {
+            bool free_all = true;
+            for (int s = 0; s < S && free_all; ++s)
+                for (int r = 0; r < TILE_R; ++r) free_all = free_all && stages[s].reg[r] != b;
+            if (free_all) common.push_back(b);
+        }
+        if (common.size() >= 3) {
+            ThreadPlan alt = make_plan(dt, std::vector<int>(common.begin(), common.begin() + 3));
+            if (alt.cost < tplan[dt].cost) tplan[dt] = std::move(alt);
+        }
+    }
 
     // --- encode for both dtypes
     for (int dt = 0; dt < 2; ++dt) {
@@ -438,37 +594,9 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                 ts.reg[r] = (uint8_t)sh.reg[r];
                 is_reg[sh.reg[r]] = true;
             }
-            // thread bits: one representative of each bank class first
-            std::vector<int> free_bits;
-            for (int b = 0; b < TILE_K; ++b)
-                if (!is_reg[b]) free_bits.push_back(b);
-            std::vector<int> lanes;
-            const int classes64[4][2] = {{0, -1}, {1, 4}, {2, 5}, {3, 6}};
-            const int classes128[3][2] = {{0, 3}, {1, 4}, {2, 5}};
-            const int ncls = dt == 0 ? 4 : 3;
-            for (int k = 0; k < ncls; ++k) {
-                for (int t = 0; t < 2; ++t) {
-                    const int b = dt == 0 ? classes64[k][t] : classes128[k][t];
-                    if (b >= 0 && !is_reg[b] &&
-                        std::find(lanes.begin(), lanes.end(), b) == lanes.end()) {
-                        lanes.push_back(b);
-                        break;
-                    }
-                }
-            }
-            for (int b : free_bits)
-                if (std::find(lanes.begin(), lanes.end(), b) == lanes.end()) lanes.push_back(b);
-            for (int u = 0; u < TILE_T; ++u) ts.thr[u] = (uint8_t)lanes[u];
-            // permutation gates at the start / end of the stage become the
-            // load map F = f1 o f2 o ... and the store map G = ... o g2 o g1
-            int lead_end = sh.begin;
-            while (lead_end < sh.end && is_perm_gate(c->gates[P.gates[order[lead_end]]].kind)) ++lead_end;
-            int trail_begin = sh.end;
-            while (trail_begin > lead_end && is_perm_gate(c->gates[P.gates[order[trail_begin - 1]]].kind))
-                --trail_begin;
-            Aff F, G;
-            for (int q = sh.begin; q < lead_end; ++q) F = compose(F, perm_map(c->gates[P.gates[order[q]]], loc.data()));
-            for (int q = trail_begin; q < sh.end; ++q) G = compose(perm_map(c->gates[P.gates[order[q]]], loc.data()), G);
+            for (int u = 0; u < TILE_T; ++u) ts.thr[u] = (uint8_t)tplan[dt].thr[s][u];
+            const int lead_end = lead_ends[s], trail_begin = trail_begins[s];
+            const Aff &F = Fm[s], &G = Gm[s];
             for (int j = 0; j < (1 << TILE_R); ++j) {
                 uint32_t o = 0;
                 for (int r = 0; r < TILE_R; ++r)
@@ -490,23 +618,10 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                 ts.ld_hi[w] = (uint16_t)swz_host(F.lin(o), amp_bytes);
                 ts.st_hi[w] = (uint16_t)swz_host(G.lin(o), amp_bytes);
             }
-            // Does every thread store only to addresses it loaded itself?  If
-            // not, a store could overwrite an amplitude another thread has
-            // yet to load, so the stage needs a barrier between the two.
-            ts.sync_mid = 0;
-            ts.pad0 = 0;
-            for (int t = 0; t < TILE_THREADS && !ts.sync_mid; ++t) {
-                uint32_t ld[1 << TILE_R], st[1 << TILE_R];
-                const uint32_t bl = ts.ld_lo[t & 31] ^ ts.ld_hi[t >> 5], bs = ts.st_lo[t & 31] ^ ts.st_hi[t >> 5];
-                for (int j = 0; j < (1 << TILE_R); ++j) {
-                    ld[j] = bl ^ ts.ld_roff[j];
-                    st[j] = bs ^ ts.st_roff[j];
-                }
-                std::sort(ld, ld + (1 << TILE_R));
-                std::sort(st, st + (1 << TILE_R));
-                for (int j = 0; j < (1 << TILE_R); ++j)
-                    if (ld[j] != st[j]) ts.sync_mid = 1;
-            }
+            // barriers from the thread plan: between this stage's loads and
+            // stores, and between its stores and the next stage's loads
+            ts.sync_mid = tplan[dt].mid[s];
+            ts.sync_end = tplan[dt].end[s];
             auto pos = [&](int lb) -> uint8_t {
                 for (int r = 0; r < TILE_R; ++r)
                     if (ts.reg[r] == lb) return (uint8_t)r;

@@ -93,17 +93,20 @@ struct TileStage {
     uint8_t reg[TILE_R];      // local bit of register-index bit r
     uint8_t thr[TILE_T];      // local bit of thread-index bit u
     uint16_t op_begin, op_end;
-    // 1 when some thread stores to an address another thread loads (F and G
-    // move amplitudes between threads): the group meets between the stage's
-    // loads and stores
+    // Barriers (SYNC_*): sync_mid between the stage's loads and its stores;
+    // sync_end between its stores and the next stage's loads (in either
+    // direction of the sweep; unused after the last stage).  SYNC_NONE: every
+    // thread only meets amplitudes it holds itself; SYNC_WARP: every warp
+    // only meets its own (__syncwarp); SYNC_GROUP: the group of 256 meets.
     uint16_t sync_mid;
-    uint16_t pad0;
+    uint16_t sync_end;
     uint16_t ld_roff[1 << TILE_R];
     uint16_t st_roff[1 << TILE_R];
     uint16_t ld_lo[32], ld_hi[TILE_THREADS / 32];
     uint16_t st_lo[32], st_hi[TILE_THREADS / 32];
 };
 static_assert(sizeof(TileStage) % 4 == 0, "stages are copied to shared memory in 4-byte words");
+enum : uint16_t { SYNC_NONE = 0, SYNC_GROUP = 1, SYNC_WARP = 2 };
 constexpr int TILE_TB = 2 * (32 + TILE_THREADS / 32);  // per-stage lane/warp table entries
 constexpr int TILE_MAX_GRAD = 32;                        // gradient ops per pass
 

@@ -615,6 +615,12 @@ template <typename V> __device__ __forceinline__ void tile_sync(const TileCtx<V>
     asm volatile("bar.sync %0, %1;" ::"r"(c.bar_id), "n"(TILE_THREADS) : "memory");
 }
 
+// A stage barrier of level lvl (SYNC_*): the group's, the warp's or none.
+template <typename V> __device__ __forceinline__ void stage_sync(const TileCtx<V> &c, uint32_t lvl) {
+    if (lvl == SYNC_GROUP) tile_sync(c);
+    else if (lvl == SYNC_WARP) __syncwarp();
+}
+
 // Gradient partials: [gradient op][column].  One block per tile (ATOM false):
 // a column per thread, plain read-modify-write.  Ring kernels (ATOM true):
 // the groups share 128 columns (threads t and t + 128 of every group), added
@@ -759,7 +765,7 @@ template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
                     apply_op<V, true, true>(op, a, b, c.pool, c.tid, c.subs, c.dgt);
                 }
             }
-            if (st.sync_mid) tile_sync(c);
+            stage_sync(c, st.sync_mid);
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
                 const uint32_t ad = base_st ^ roff_st[j];
@@ -768,9 +774,11 @@ template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
                     if (ADJ) c.tile_b[ad] = b[j];
                 }
             }
-            // the last stage's writes are read next by the TMA store
+            // the last stage's writes are read next by the TMA store; between
+            // stages s and s + 1 (either direction) the barrier of sync_end[s]
             if (si == c.n_stages - 1) fence_async_smem();
-            if (si < c.n_stages - 1 || c.end_sync) tile_sync(c);
+            if (si < c.n_stages - 1) stage_sync(c, c.stages[ADJ ? s - 1 : s].sync_end);
+            else if (c.end_sync) tile_sync(c);
         }
     }
 };
