@@ -240,6 +240,7 @@ tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gate
 
 tqd_status tqd_circuit_free(tqd_circuit *c) {
     if (!c) return TQD_OK;
+    GUARD(c->device);  // its buffers (forward checkpoints included) belong to that device
     release_circuit(c);
     delete c;
     return TQD_OK;

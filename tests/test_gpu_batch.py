@@ -90,3 +90,28 @@ def test_batched_workload_sample():
     circs = [S.Circuit(c) for c, _, _ in items]
     b = S.Batch(circs, [t for _, _, t in items], streams=4)
     check_batch(items, b)
+
+
+def test_batch_sharded_across_ranks():
+    """The batched workload's split across ranks (bench.py --gpus N): each of
+    3 ranks' shares, run here one after the other as its own batch, gives
+    every circuit the energy and gradient of the whole batch and of the
+    oracle; the shares cover the batch once."""
+    from paper_2511_19291_gb300 import shard as SH
+    S = sim()
+    items = ragged(97, 15, 4, 14, 1, 3)
+    costs = [SH.circuit_cost(c.n_qubits, len(c.gates)) for c, _, _ in items]
+    parts = SH.partition(costs, 3)
+    assert sorted(i for p in parts for i in p) == list(range(len(items)))
+    whole = S.Batch([S.Circuit(c) for c, _, _ in items], [t for _, _, t in items], streams=4)
+    check_batch(items, whole)
+    e_whole = whole.energies.cpu().numpy()
+    for part in parts:
+        sub = [items[i] for i in part]
+        b = S.Batch([S.Circuit(c) for c, _, _ in sub], [t for _, _, t in sub], streams=4)
+        check_batch(sub, b)
+        e = b.energies.cpu().numpy()
+        for k, i in enumerate(part):
+            assert abs(e[k] - e_whole[i]) < 1e-6, (i, e[k], e_whole[i])
+            np.testing.assert_allclose(b.grads_of(k).cpu().numpy(), whole.grads_of(i).cpu().numpy(),
+                                       atol=1e-6 * W.observable_l1(items[i][2]), rtol=0)
