@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=512, help="circuits of the batched measurement (0 = skip)")
     ap.add_argument("--tc-gates", type=int, default=200, help="gates of the tensor-core block measurement (0 = skip)")
     ap.add_argument("--qft-n", type=int, default=32, help="qubits of the QFT + ansatz measurement (0 = skip)")
+    ap.add_argument("--grad-fn", type=int, default=1, choices=[0, 1],
+                    help="time the 24-qubit workload's gradient through the autograd.Function (0 = skip)")
     return ap.parse_args()
 
 
@@ -329,6 +331,40 @@ def batch_bench(S, torch, dev, count, barrier, reps=3, rank=0, world=1):
     return out
 
 
+# ------------------------------------------- gradient through autograd.Function
+def grad_fn_bench(S, torch, dev, barrier, reps=10):
+    """The 24-qubit, 10-layer ansatz with the Ising observable (480 angles),
+    differentiated through the autograd.Function the way a training loop
+    does: e = expval_fn(theta); e.backward().  grad-evals/s over `reps`
+    evaluations after two warm-up ones."""
+    from paper_2511_19291_gb300 import workloads as W
+    w = W.workload_grad()
+    c = S.Circuit(w.circuit, device=dev)
+    obs = S.Observable(w.terms)
+    p = torch.tensor(w.params, dtype=torch.float64, device=dev, requires_grad=True)
+
+    def step():
+        p.grad = None
+        e = S.expval_fn(p, c, obs)
+        e.backward()
+        return e
+
+    for _ in range(2):
+        step()
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        e = step()
+    b.record()
+    barrier()
+    ms = a.elapsed_time(b) / reps
+    return {"workload": w.name, "n_qubits": w.circuit.n_qubits, "n_params": w.circuit.n_params,
+            "path": "expval_fn + backward (autograd.Function)", "grad_evals_per_s": 1000.0 / ms,
+            "ms_per_grad_eval": ms, "energy": e.item()}
+
+
 # ------------------------------------------------ tensor-core block measurement
 def tc_bench(S, torch, dev, n, n_gates, barrier, reps=5):
     """One run of `n_gates` gates on qubits 0..5 of an n-qubit complex64 state:
@@ -526,6 +562,8 @@ def main():
     if args.batch_count > 0:
         batched = batch_bench(S, torch, dev, args.batch_count, barrier, rank=rank, world=world)
 
+    grad_fn = grad_fn_bench(S, torch, dev, barrier) if args.grad_fn else None
+
     qft = None
     if args.qft_n > 0:
         del psi, lam
@@ -582,6 +620,7 @@ def main():
         "sweep": sweep,
         "batched": batched,
         "tc_block": tcb,
+        "grad24": grad_fn,
         "qft32": qft,
         "clocks": clk.summary(),
         "kernels": kernels,

@@ -142,7 +142,10 @@ tqd_status tqd_state_alloc(int n_qubits, tqd_dtype dtype, void *dev_amps, size_t
  * basis_index = 0).  basis_index < 2^n. */
 tqd_status tqd_state_reset(tqd_state *state, uint64_t basis_index, void *stream);
 
-/* Frees the handle, never the amplitudes. NULL is accepted. */
+/* Frees the handle, never the amplitudes. The handle's reduction workspace
+ * (allocated stream-ordered on first use) is released in the order of the
+ * stream that used it last, so work still queued there may keep running; that
+ * stream must still exist. NULL is accepted. */
 tqd_status tqd_state_free(tqd_state *state);
 
 /* -------------------------------------------------------------- circuits */
@@ -158,6 +161,9 @@ tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gate
                               const double *matrices, size_t n_matrix_entries,
                               const tqd_plan_opts *opts, tqd_circuit **out);
 
+/* Waits for the circuit's device to finish its queued work (which may read the
+ * circuit's buffers), then frees the circuit and its device buffers (forward
+ * checkpoints included). NULL is accepted. */
 tqd_status tqd_circuit_free(tqd_circuit *circuit);
 
 /* Diagnostics that need no GPU: validates the gate list as tqd_circuit_create

@@ -122,6 +122,7 @@ tqd_status tqd_state_alloc(int n_qubits, tqd_dtype dtype, void *dev_amps, size_t
     s->device = attr.device;
     s->work = nullptr;
     s->work_len = 0;
+    s->work_stream = nullptr;
     *out = s;
     return TQD_OK;
 }
@@ -137,8 +138,11 @@ tqd_status tqd_state_reset(tqd_state *state, uint64_t basis_index, void *stream)
 tqd_status tqd_state_free(tqd_state *state) {
     if (!state) return TQD_OK;
     if (state->work) {
+        // kernels queued on the workspace's stream may still use it: release
+        // it in that stream's order (a plain cudaFree of a stream-ordered
+        // allocation does not wait for them)
         DeviceGuard g(state->device);
-        cudaFree(state->work);
+        cudaFreeAsync(state->work, state->work_stream);
     }
     delete state;
     return TQD_OK;
@@ -241,6 +245,8 @@ tqd_status tqd_circuit_create(int n_qubits, const tqd_gate *gates, size_t n_gate
 tqd_status tqd_circuit_free(tqd_circuit *c) {
     if (!c) return TQD_OK;
     GUARD(c->device);  // its buffers (forward checkpoints included) belong to that device
+    // work queued with the circuit may still read its buffers
+    cudaDeviceSynchronize();
     release_circuit(c);
     delete c;
     return TQD_OK;

@@ -82,8 +82,9 @@ struct tqd_state {
     void *amps;
     size_t bytes;
     int device;
-    double *work;       // reduction workspace (device), grown on demand
+    double *work;       // reduction workspace (device, stream-ordered allocation), grown on demand
     size_t work_len;    // doubles
+    cudaStream_t work_stream;  // stream of the workspace's last use: it is released in that stream's order
 };
 
 struct tqd_circuit {

@@ -239,6 +239,7 @@ static void fill_pack(TermPack &tp, uint64_t x, const std::vector<TermDev> &term
 }
 
 cudaError_t ensure_work(tqd_state *st, size_t len, cudaStream_t s) {
+    st->work_stream = s;  // every user of the workspace passes here with its stream
     if (st->work_len >= len) return cudaSuccess;
     if (st->work) {
         cudaError_t e = cudaFreeAsync(st->work, s);

@@ -408,30 +408,30 @@ def shots_gaussian_fn(params: torch.Tensor, circuit: Circuit, n_shots: float, z:
 
 
 class _ExpvalFn(torch.autograd.Function):
-    """E(theta) = <psi_L|H|psi_L>.  Forward keeps only theta and psi_L; backward
-    recomputes earlier states by un-applying the circuit (Sec. 4.4)."""
+    """E(theta) = <psi_L|H|psi_L>, a scalar, so dL/dtheta = (dL/dE) dE/dtheta.
+    When theta needs a gradient, forward runs the whole gradient evaluation
+    at once (tqd_value_and_grad: the forward passes, E read off lambda = H
+    psi_L, the adjoint reverse sweep of Sec. 4.4) and keeps only dE/dtheta;
+    backward scales it.  Otherwise forward applies the circuit and measures E.
+    No intermediate state is kept between the two."""
 
     @staticmethod
     def forward(ctx, params, circuit, obs, dtype, basis_index):
         psi = State(circuit.n, dtype, params.device).reset(basis_index)
-        apply(psi, circuit, params)
-        e = expval(psi, obs)
-        ctx.save_for_backward(params)
-        ctx.psi, ctx.circuit, ctx.obs = psi, circuit, obs
+        if not ctx.needs_input_grad[0]:
+            apply(psi, circuit, params)
+            return expval(psi, obs)
+        lam = State(circuit.n, dtype, params.device)
+        p64 = params.detach().to(torch.float64).contiguous()
+        e, g = value_and_grad(psi, lam, circuit, p64, obs)
+        ctx.save_for_backward(g)
+        ctx.param_dtype = params.dtype
         return e
 
     @staticmethod
     def backward(ctx, grad_e):
-        (params,) = ctx.saved_tensors
-        psi = ctx.psi
-        if psi is None:
-            raise RuntimeError("this expectation's backward already ran (the saved state is consumed)")
-        lam = State(psi.n, psi.tensor.dtype, psi.device)
-        w = grad_e.reshape(1).to(torch.float64).expand(len(ctx.obs)).contiguous()
-        grads = torch.zeros_like(params)
-        backward(psi, lam, ctx.circuit, params, ctx.obs, grads, weights=w)
-        ctx.psi = None
-        return grads, None, None, None, None
+        (g,) = ctx.saved_tensors
+        return (grad_e.to(torch.float64) * g).to(ctx.param_dtype), None, None, None, None
 
 
 class _MeasureFn(torch.autograd.Function):

@@ -236,6 +236,41 @@ def test_autograd_function(mode):
     assert ok, worst
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_autograd_function_paths(dtype):
+    """expval_fn with angles that need no gradient (apply and measure only),
+    with float32 angles (the gradient comes back in float32) and on a
+    complex128 state, against the oracle; a second backward through the same
+    graph is refused by torch as usual."""
+    S = sim()
+    n = 13
+    circ = W.hea_ansatz(n, 2)
+    params = W.config_rng(8).angles(circ.n_params)
+    terms = W.ising(n)
+    c = S.Circuit(circ)
+    ref_e = oracle.energy(circ, params, terms)
+    ref_g = oracle.grad_param_shift(circ, params, terms)
+    e0 = S.expval_fn(params_tensor(params), c, terms, dtype=DTYPES[dtype])
+    assert not e0.requires_grad and abs(e0.item() - ref_e) < E_TOL[dtype] * 10
+    p32 = torch.tensor(params, dtype=torch.float32, device="cuda", requires_grad=True)
+    e = S.expval_fn(p32, c, terms, dtype=DTYPES[dtype])
+    (-0.5 * e).backward()
+    assert p32.grad.dtype == torch.float32
+    # float32 angles: compare with the oracle at the rounded angles
+    p_r = p32.detach().double().cpu().numpy()
+    ok, worst = grad_close(p32.grad.double().cpu().numpy(), -0.5 * oracle.grad_param_shift(circ, p_r, terms),
+                           1e-4, hnorm=W.observable_l1(terms))
+    assert ok, worst
+    p64 = params_tensor(params).requires_grad_(True)
+    e = S.expval_fn(p64, c, terms, dtype=DTYPES[dtype])
+    e.backward(retain_graph=False)
+    ok, worst = grad_close(p64.grad.cpu().numpy(), ref_g, G_REL[dtype],
+                           hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+    assert ok, worst
+    with pytest.raises(RuntimeError):
+        e.backward()
+
+
 def test_measure_allz_autograd():
     S = sim()
     n = 6
