@@ -664,20 +664,33 @@ std::vector<PauliTileDesc> plan_pauli_tiles(const std::vector<PauliGroup> &group
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return high_count(groups[a].xmask) > high_count(groups[b].xmask);
     });
+    // Groups with x bits above qubit 3 go to the first set they fit in; those
+    // without (the diagonal group, X/Y on qubits 0..3), which fit in any set
+    // and come last in this order, go to the set with the least work so far
+    // (16 per group, the Walsh-Hadamard transform, plus 1 per term), so that
+    // the launches carry similar work.
     std::vector<uint64_t> sets;
     std::vector<std::vector<int>> members;
+    std::vector<size_t> work;
     for (int g : order) {
         const uint64_t h = groups[g].xmask & ~(uint64_t)15;
         int placed = -1;
-        for (size_t s = 0; s < sets.size() && placed < 0; ++s)
-            if (__builtin_popcountll(sets[s] | h) <= 8) placed = (int)s;
+        if (h == 0) {
+            for (size_t s = 0; s < sets.size(); ++s)
+                if (placed < 0 || work[s] < work[placed]) placed = (int)s;
+        } else {
+            for (size_t s = 0; s < sets.size() && placed < 0; ++s)
+                if (__builtin_popcountll(sets[s] | h) <= 8) placed = (int)s;
+        }
         if (placed < 0) {
             sets.push_back(0);
             members.emplace_back();
+            work.push_back(0);
             placed = (int)sets.size() - 1;
         }
         sets[placed] |= h;
         members[placed].push_back(g);
+        work[placed] += 16 + groups[g].terms.size();
     }
     for (size_t s = 0; s < sets.size(); ++s) {
         // pad Q with unused qubits up to 8 high qubits
