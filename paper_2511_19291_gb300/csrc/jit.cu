@@ -8,6 +8,8 @@
 // the matrix buffer.
 #include <dlfcn.h>
 #include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
@@ -15,6 +17,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <thread>
 #include <unordered_map>
@@ -41,6 +45,7 @@ struct Nvrtc {
     decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
     decltype(&nvrtcGetCUBIN) cubin = nullptr;
     decltype(&nvrtcDestroyProgram) destroy = nullptr;
+    decltype(&nvrtcVersion) version = nullptr;
     bool ok = false;
 };
 
@@ -61,6 +66,7 @@ const Nvrtc &nvrtc() {
         n.cubin_size = (decltype(n.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
         n.cubin = (decltype(n.cubin))dlsym(h, "nvrtcGetCUBIN");
         n.destroy = (decltype(n.destroy))dlsym(h, "nvrtcDestroyProgram");
+        n.version = (decltype(n.version))dlsym(h, "nvrtcVersion");
         n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
     });
     return n;
@@ -419,6 +425,113 @@ std::string jit_source(const tqd_circuit *c, int pass, int dt, bool adj, bool ri
     return generate(c->tile_passes[pass].dev[dt], dt, adj, ring, tmaw, adj && psi_ro);
 }
 
+// ----------------------------------------------------------- disk cache
+// Compiled kernels persist across processes in a cache directory
+// (TQD_JIT_CACHE_DIR, else $XDG_CACHE_HOME/tqd-jit, else $HOME/.cache/tqd-jit;
+// TQD_JIT_CACHE=0 turns it off).  An entry stores its whole key: the target,
+// the compiler version, the build's options, the device headers the source
+// includes and the generated source itself; it is used only when all of it
+// matches byte for byte, so another library build or compiler never reuses
+// a kernel.  Entries are written to a temporary file and renamed into place;
+// anything unreadable, mismatched or unwritable is simply compiled again.
+namespace {
+
+uint64_t fnv1a(const char *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) h = (h ^ (unsigned char)p[i]) * 1099511628211ull;
+    return h;
+}
+
+const std::string &cache_dir() {
+    static std::string dir;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *off = getenv("TQD_JIT_CACHE");
+        if (off && off[0] == '0') return;
+        if (const char *d = getenv("TQD_JIT_CACHE_DIR")) dir = d;
+        else if (const char *x = getenv("XDG_CACHE_HOME")) dir = std::string(x) + "/tqd-jit";
+        else if (const char *h = getenv("HOME")) dir = std::string(h) + "/.cache/tqd-jit";
+        if (dir.empty()) return;
+        // create every missing component
+        for (size_t i = 1; i <= dir.size(); ++i)
+            if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+        struct stat st;
+        if (stat(dir.c_str(), &st) != 0 || !S_ISDIR(st.st_mode)) dir.clear();
+    });
+    return dir;
+}
+
+// Everything besides the source that decides what the compiler produces.
+const std::string &cache_key_prefix() {
+    static std::string prefix;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int mj = 0, mn = 0;
+        if (nvrtc().version) nvrtc().version(&mj, &mn);
+        std::ostringstream o;
+        o << "tqd-jit 1\nnvrtc " << mj << "." << mn << "\n";
+#ifdef TQD_CHECKED
+        o << "checked\n";
+#endif
+        for (int i = 0; i < k_jit_n_headers; ++i)
+            o << k_jit_header_names[i] << " " << std::hex
+              << fnv1a(k_jit_header_srcs[i], strlen(k_jit_header_srcs[i])) << std::dec << "\n";
+        prefix = o.str();
+    });
+    return prefix;
+}
+
+bool read_u64(std::istream &in, uint64_t &v) { return (bool)in.read(reinterpret_cast<char *>(&v), sizeof(v)); }
+
+bool cache_load(const std::string &path, const std::string &key, std::string *cubin) {
+    std::ifstream in(path, std::ios::binary);
+    uint64_t klen = 0, clen = 0;
+    if (!in || !read_u64(in, klen) || klen != key.size()) return false;
+    std::string k(klen, '\0');
+    if (!in.read(&k[0], (std::streamsize)klen) || k != key) return false;
+    if (!read_u64(in, clen) || clen == 0 || clen > (1u << 26)) return false;
+    cubin->assign(clen, '\0');
+    return (bool)in.read(&(*cubin)[0], (std::streamsize)clen);
+}
+
+void cache_store(const std::string &path, const std::string &key, const std::string &cubin) {
+    std::ostringstream tmpname;
+    tmpname << path << ".tmp." << getpid() << "." << std::hash<std::thread::id>()(std::this_thread::get_id());
+    const std::string tmp = tmpname.str();
+    {
+        std::ofstream out(tmp, std::ios::binary | std::ios::trunc);
+        const uint64_t klen = key.size(), clen = cubin.size();
+        out.write(reinterpret_cast<const char *>(&klen), sizeof(klen));
+        out.write(key.data(), (std::streamsize)klen);
+        out.write(reinterpret_cast<const char *>(&clen), sizeof(clen));
+        out.write(cubin.data(), (std::streamsize)clen);
+        if (!out) {
+            out.close();
+            unlink(tmp.c_str());
+            return;
+        }
+    }
+    if (rename(tmp.c_str(), path.c_str()) != 0) unlink(tmp.c_str());
+}
+
+// compile_cubin through the disk cache.
+std::string compile_cached(const std::string &src, int arch, std::string *log) {
+    const std::string &dir = cache_dir();
+    if (dir.empty()) return compile_cubin(src, arch, log);
+    std::string key = cache_key_prefix();
+    key += "sm_" + std::to_string(arch) + "a\n";
+    key += src;
+    char name[40];
+    snprintf(name, sizeof(name), "/%016llx.cubin", (unsigned long long)fnv1a(key.data(), key.size()));
+    const std::string path = dir + name;
+    std::string cubin;
+    if (cache_load(path, key, &cubin)) return cubin;
+    cubin = compile_cubin(src, arch, log);
+    if (!cubin.empty()) cache_store(path, key, cubin);
+    return cubin;
+}
+
+}  // namespace
+
 static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bool tmaw, bool psi_ro) {
     if (!nvrtc().ok || !driver().ok) {
         set_error("specialised pass kernels: NVRTC or the CUDA driver entry points are unavailable");
@@ -451,7 +564,7 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bo
         for (int t = 0; t < nt; ++t)
             th.emplace_back([&] {
                 for (int i; (i = next.fetch_add(1)) < (int)need.size();)
-                    cubins[i] = compile_cubin(srcs[need[i]], arch, &logs[i]);
+                    cubins[i] = compile_cached(srcs[need[i]], arch, &logs[i]);
             });
         for (auto &t : th) t.join();
     }

@@ -599,3 +599,53 @@ def test_main_example_ladder_encoder_batch(nq, dtype):
         opt.step()
         losses.append(l2.item())
     assert losses[-1] < losses[0]
+
+
+_CACHE_SCRIPT = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+from paper_2511_19291_gb300 import sim as S, workloads as W
+n = 22
+circ = W.hea_ansatz(n, 2)
+params = torch.tensor(W.config_rng(9).angles(circ.n_params), dtype=torch.float64, device="cuda")
+c = S.Circuit(circ)
+psi, lam = S.State(n).reset(0), S.State(n)
+e, g = S.value_and_grad(psi, lam, c, params, W.ising(n))
+torch.cuda.synchronize()
+print(repr(e.item()), repr(float(g.abs().sum().item())))
+"""
+
+
+def test_jit_disk_cache(tmp_path):
+    """Pass-specialised kernels persist across processes: a first process
+    fills an empty cache directory, a second one loads them (nothing is
+    rewritten; the same energy bit for bit), and a third, after every entry
+    was truncated, compiles them again and still agrees."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, TQD_JIT_CACHE_DIR=str(tmp_path / "jit"))
+    script = _CACHE_SCRIPT.format(root=root)
+
+    def run():
+        r = subprocess.run([sys.executable, "-c", script], env=env, capture_output=True, text=True, timeout=900)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return r.stdout.strip().splitlines()[-1]
+
+    def same(a, b):
+        # the energy's reduction is deterministic; the gradient partials are
+        # summed with shared-memory atomics, whose order varies run to run
+        (ea, ga), (eb, gb) = (map(float, x.split()) for x in (a, b))
+        return ea == eb and abs(ga - gb) <= 1e-9 * abs(ga)
+
+    first = run()
+    entries = sorted((tmp_path / "jit").glob("*.cubin"))
+    assert entries, "no cache entries written"
+    stamps = {p: p.stat().st_mtime_ns for p in entries}
+    assert same(run(), first)
+    assert all(p.stat().st_mtime_ns == stamps[p] for p in entries)  # read, not rewritten
+    for p in entries:
+        p.write_bytes(p.read_bytes()[:20])
+    assert same(run(), first)
+    assert all(p.stat().st_size > 20 for p in entries)  # rewritten whole
