@@ -1,9 +1,10 @@
 """The fused planner on the host: every circuit's encoded passes, executed
 from their descriptors (tile gathering, stage address tables, op positions,
 forward and reverse), against the gates applied one by one, for both
-precisions' descriptors.  No GPU: tqd_plan_check runs on the CPU.  Also
-checks that every stage that moves amplitudes between threads carries the
-barrier between its loads and stores."""
+precisions' descriptors.  No GPU: tqd_plan_check runs on the CPU.  It also
+checks every barrier flag against the address tables: a point marked
+"none" must keep every thread on its own amplitudes, one marked "warp" every
+warp on its own (a weaker flag than the tables allow fails the check)."""
 import numpy as np
 import pytest
 
@@ -62,3 +63,41 @@ def test_plan_check_rejects_small_and_large():
         S.plan_check(W.hea_ansatz(8, 1), np.zeros(16))
     with pytest.raises(Exception):
         S.plan_check(W.hea_ansatz(21, 1), np.zeros(42))
+
+
+def permutation_heavy(seed, n, ng):
+    """Dense CNOT, SWAP and X among RY and RZ: many permutations folded into
+    the stages' load and store maps, so every kind of barrier point occurs."""
+    rng = W.SplitMix64(seed)
+    gates, n_params = [], 0
+    for _ in range(ng):
+        r = rng.randint(0, 9)
+        a = rng.randint(0, n - 1)
+        b = (a + 1 + rng.randint(0, n - 2)) % n
+        if r <= 3:
+            gates.append(W.Gate("CNOT", (a, b)))
+        elif r <= 5:
+            gates.append(W.Gate("SWAP", (a, b)))
+        elif r == 6:
+            gates.append(W.Gate("X", (a,)))
+        elif r == 7:
+            gates.append(W.Gate("RY", (a,), param=n_params))
+            n_params += 1
+        else:
+            gates.append(W.Gate("RZ", (a,), param=n_params))
+            n_params += 1
+    return W.Circuit(n, gates, n_params), rng.angles(max(1, n_params))
+
+
+@pytest.mark.parametrize("n,ng,seed", [(12, 200, 1), (14, 300, 2), (16, 250, 3), (19, 150, 4)])
+def test_permutation_heavy_plans(n, ng, seed):
+    circ, params = permutation_heavy(9300 + seed, n, ng)
+    check(circ, params, seed)
+
+
+@pytest.mark.parametrize("n,layers", [(20, 2), (20, 6)])
+def test_ansatz_plans_20_qubits(n, layers):
+    """The ansatz at the largest host-checkable width, where windows of the
+    26-qubit workload's kind (overlapping 8-qubit sets) appear."""
+    circ = W.hea_ansatz(n, layers)
+    check(circ, W.config_rng(5).angles(circ.n_params))
