@@ -215,33 +215,44 @@ def oracle_sample(w, gate_sample=6, term_sample=2):
     return 1.0 / t_grad, sample, t_gates + t_terms
 
 
-def _oracle_sample_worker(args):
-    w, gate_sample, term_sample = args
-    v, _, spent = oracle_sample(w, gate_sample, term_sample)
-    return v, spent
-
-
-def oracle_all_cores(w, gate_sample=6, term_sample=2, procs=None):
+def oracle_all_cores(n, layers, gate_sample=6, term_sample=2, procs=None, deadline_s=300.0):
     """The same oracle, unchanged, as one process per host core, each timing
-    the bounded sample at once (a parameter-shift gradient's 2P + 1
-    evaluations are independent, so a CPU run would spread them this way):
-    the rate is the sum of the processes' extrapolated rates.  A spawn pool,
-    which is safe after CUDA has been initialised in this process."""
-    import multiprocessing as mp
+    the bounded sample of the n-qubit, `layers`-layer workload at once (a
+    parameter-shift gradient's 2P + 1 evaluations are independent, so a CPU
+    run would spread them this way): the rate is the sum of the processes'
+    extrapolated rates.  Plain subprocesses with a deadline: one that dies
+    or overruns turns the measurement into an 'unavailable' note."""
     procs = procs or os.cpu_count() or 1
     try:  # about 3 states per process (the state and numpy temporaries), in half the free memory
         avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
-        procs = max(1, min(procs, int(avail / 2 // (3 * 16 << w.circuit.n_qubits))))
+        procs = max(1, min(procs, int(avail / 2 // (3 * 16 << n))))
     except (ValueError, OSError, AttributeError):
         pass
-    with mp.get_context("spawn").Pool(procs) as pool:
-        res = pool.map(_oracle_sample_worker, [(w, gate_sample, term_sample)] * procs)
-    value = sum(v for v, _ in res)
-    n = w.circuit.n_qubits
+    code = ("import json, sys; sys.path.insert(0, {root!r}); import bench; "
+            "from paper_2511_19291_gb300 import workloads as W; "
+            "v, _, t = bench.oracle_sample(W.workload_hea(2, {n}, {layers}, 'ising'), {g}, {t}); "
+            "print(json.dumps([v, t]))").format(root=ROOT, n=n, layers=layers, g=gate_sample, t=term_sample)
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                           text=True) for _ in range(procs)]
+    end = time.monotonic() + deadline_s
+    values = []
+    try:
+        for p in ps:
+            out, _ = p.communicate(timeout=max(1.0, end - time.monotonic()))
+            if p.returncode != 0:
+                return {"unavailable": f"an oracle process exited with {p.returncode}"}
+            values.append(json.loads(out.strip().splitlines()[-1])[0])
+    except subprocess.TimeoutExpired:
+        return {"unavailable": f"oracle processes ran past {deadline_s:.0f} s"}
+    finally:
+        for p in ps:
+            if p.poll() is None:
+                p.kill()
+                p.wait()
     sample = (f"{gate_sample} gates and {term_sample} terms of the {n}-qubit workload in each of {procs} "
               f"concurrent single-threaded processes (one per host core), each extrapolated to one "
               f"parameter-shift gradient; rate = sum over processes")
-    return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample}
+    return {"value": sum(values), "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample}
 
 
 def run_reference(args):
@@ -649,7 +660,7 @@ def main():
         v, sample, _ = oracle_sample(w)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
         try:
-            cpu_all = oracle_all_cores(w)
+            cpu_all = oracle_all_cores(args.n, args.layers)
         except Exception as exc:  # context only: never fails the line
             cpu_all = {"unavailable": repr(exc)[:200]}
 
