@@ -40,3 +40,17 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_oracle_on_all_cores_small():
+    """The all-core oracle baseline: one process per core, rates summed; a
+    deadline it cannot meet turns it into an 'unavailable' note and leaves no
+    process behind."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_all_cores(14, 2, gate_sample=4, term_sample=2, procs=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "grad-evals/s" and r["value"] > 0
+    slow = bench.oracle_all_cores(24, 10, gate_sample=6, term_sample=2, procs=2, deadline_s=0.01)
+    assert "unavailable" in slow
+    left = subprocess.run(["ps", "-eo", "args"], capture_output=True, text=True).stdout
+    assert "workload_hea(2, 24, 10" not in left
