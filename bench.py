@@ -238,12 +238,12 @@ def oracle_all_cores(n, layers, gate_sample=6, term_sample=2, procs=None, deadli
     values = []
     try:
         for p in ps:
-            out, _ = p.communicate(timeout=max(1.0, end - time.monotonic()))
+            out, _ = p.communicate(timeout=max(0.01, end - time.monotonic()))
             if p.returncode != 0:
                 return {"unavailable": f"an oracle process exited with {p.returncode}"}
             values.append(json.loads(out.strip().splitlines()[-1])[0])
     except subprocess.TimeoutExpired:
-        return {"unavailable": f"oracle processes ran past {deadline_s:.0f} s"}
+        return {"unavailable": f"oracle processes ran past {deadline_s:g} s"}
     finally:
         for p in ps:
             if p.poll() is None:
