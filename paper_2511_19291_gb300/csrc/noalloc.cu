@@ -14,6 +14,7 @@
 // loads the library keeps that much reserved until the process exits.  Every
 // call on a device shares the same array: two calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on it.
+#include <cuda.h>
 #include <math.h>
 #include <mutex>
 
@@ -107,18 +108,55 @@ __global__ void k_na_total(const double *__restrict__ sums, int count, double *_
     }
 }
 
-// Device address of g_scratch, looked up once per device with that device current.
+// Device address of g_scratch, looked up with the device current the first
+// time a context of that device calls.  The cache is keyed on the driver's
+// context ID, which is unique for the life of the process: after
+// cudaDeviceReset (or any other end of the device's context) the next call
+// finds a new ID and looks the address up again instead of reusing one that
+// belonged to the destroyed context.
+typedef CUresult (*FnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*FnCtxGetId)(CUcontext, unsigned long long *);
+
 static std::mutex g_mu;
 static double *g_addr[64] = {nullptr};
+static unsigned long long g_ctx[64] = {0};
+
+// ID of the calling thread's current context; 0 when there is none yet or
+// the driver entry points are unavailable (the address is then looked up on
+// every call).
+static unsigned long long current_ctx_id() {
+    static FnCtxGetCurrent get_current = nullptr;
+    static FnCtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (FnCtxGetCurrent)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (FnCtxGetId)p;
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 static cudaError_t scratch_address(int dev, double **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_addr[dev] || id == 0 || id != g_ctx[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = (double *)p;
+        // the lookup makes the device's context current if it was not yet
+        g_ctx[dev] = id != 0 ? id : current_ctx_id();
     }
     *out = g_addr[dev];
     return cudaSuccess;

@@ -46,6 +46,24 @@ def test_noalloc_matches_expval_two_calls_in_a_row(dtype):
             assert abs(got - ref) <= E_TOL[dtype], (got, ref)
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_noalloc_against_oracle(dtype):
+    """Directly against the oracle's expectation value (Sec. 2.2.1), twice in
+    a row on the same state."""
+    import oracle
+    S = sim()
+    n = 13
+    rng = W.SplitMix64(7100)
+    circ, params = W.random_circuit(rng, n, 70)
+    terms = W.random_pauli_terms(rng, n, 20) + W.ising(n)
+    st, _, _ = gpu_state(circ, params, "fused", dtype)
+    ref = oracle.expval(n, oracle.run(circ, params), terms)[0]
+    obs = S.Observable(terms)
+    for _ in range(2):
+        got = noalloc_expval(st, obs).item()
+        assert abs(got - ref) <= E_TOL[dtype], (got, ref)
+
+
 def test_noalloc_empty_and_too_large():
     S = sim()
     st, _, _ = gpu_state(W.hea_ansatz(12, 1), np.zeros(24), "fused", "c64")
