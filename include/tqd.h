@@ -200,12 +200,24 @@ tqd_status tqd_plan_check(int n_qubits, const tqd_gate *gates, size_t n_gates, i
 tqd_status tqd_circuit_info(const tqd_circuit *circuit, int *n_passes, int *n_launches_apply,
                             int *n_launches_backward);
 
-/* Synchronizes the device and reads the circuit's device error word:
- * *device_error = 0 when every launch of this circuit completed normally,
- * 1 when a bounded wait for a tile copy gave up (that launch's results are
- * invalid), 2 when a kernel built with TQD_CHECKED found an index out of
- * range.  Returns TQD_ERR_TIMEOUT for 1, TQD_ERR_NUMERIC for 2. */
+/* Synchronizes the device, reads the circuit's device error word and clears
+ * it: *device_error = 0 when every launch of this circuit since the last
+ * check completed normally, 1 when a bounded wait for a tile copy gave up
+ * (every device wait gives up after about one second of elapsed time; that
+ * launch's results are invalid, the context stays usable), 2 when a kernel
+ * built with TQD_CHECKED found an index out of range.  Returns
+ * TQD_ERR_TIMEOUT for 1, TQD_ERR_NUMERIC for 2. */
 tqd_status tqd_circuit_check(const tqd_circuit *circuit, int *device_error);
+
+/* Test hook of the give-up path (the paper has no counterpart): while
+ * enabled, every fused tile pass of this circuit arms the barrier of block
+ * 0's first tile without issuing its copy, so that block's wait runs out its
+ * time limit (about one second per launch, and as long again for the waits
+ * that depend on that tile), the block returns, and tqd_circuit_check then
+ * reports TQD_ERR_TIMEOUT.  The launch's results are invalid.  Other
+ * launches (gate-by-gate kernels, tensor-core blocks, observables) are not
+ * affected. */
+tqd_status tqd_circuit_test_stall(tqd_circuit *circuit, int enable);
 
 /* psi <- G_L ... G_1 psi (Sec. 4.1; gate semantics of Algorithm 1).
  * dev_params: device array of n_params doubles (may be NULL when n_params
@@ -266,8 +278,11 @@ tqd_status tqd_backward(tqd_state *psi, tqd_state *lambda, const tqd_circuit *ci
  *
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls on a device share the one array:
- * calls whose GPU work overlaps (different streams or host threads) race. */
+ * before any stream capture.  The address is kept per device context: after
+ * cudaDeviceReset (or whatever else ends the device's context) the next call
+ * looks it up again, so that call too must come before any capture.  All
+ * calls on a device share the one array: calls whose GPU work overlaps
+ * (different streams or host threads) race. */
 #define TQD_NOALLOC_SCRATCH_DOUBLES 131072
 tqd_status tqd_expval_noalloc(const tqd_state *state, const tqd_pauli_term *terms, size_t n_terms,
                               double *dev_out, void *stream);

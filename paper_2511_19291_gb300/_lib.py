@@ -28,7 +28,8 @@ CHECKPOINTS_NONE = 0xFFFFFFFF
 # Every symbol include/tqd.h declares (checked by the ABI test).
 EXPORTS = (
     "tqd_state_alloc", "tqd_state_reset", "tqd_state_free",
-    "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_jit_check",
+    "tqd_circuit_create", "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_circuit_test_stall",
+    "tqd_jit_check",
     "tqd_plan_check",
     "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
@@ -108,6 +109,7 @@ def load(path: str | None = None):
         L.tqd_circuit_free.argtypes = [vp]
         L.tqd_circuit_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.tqd_circuit_check.argtypes = [vp, C.POINTER(i32)]
+        L.tqd_circuit_test_stall.argtypes = [vp, i32]
         L.tqd_jit_check.argtypes = [i32, vp, sz, i32, vp, sz, i32, C.POINTER(i32)]
         L.tqd_plan_check.argtypes = [i32, vp, sz, i32, vp, sz, vp, u64, C.POINTER(dbl), C.POINTER(dbl),
                                      C.POINTER(i32), C.POINTER(i32)]
@@ -131,7 +133,8 @@ def load(path: str | None = None):
         L.tqd_profile_enable.argtypes = [i32]
         L.tqd_profile_read.argtypes = [vp, i32, C.POINTER(i32)]
         for name in ("tqd_state_alloc", "tqd_state_reset", "tqd_state_free", "tqd_circuit_create",
-                     "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_apply_circuit", "tqd_expval",
+                     "tqd_circuit_free", "tqd_circuit_info", "tqd_circuit_check", "tqd_circuit_test_stall",
+                     "tqd_apply_circuit", "tqd_expval",
                      "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable", "tqd_backward", "tqd_value_and_grad",
                      "tqd_backward_seeded", "tqd_probabilities", "tqd_sample", "tqd_shots_gaussian",
                      "tqd_shots_gaussian_backward",

@@ -307,6 +307,7 @@ tqd_status tqd_circuit_check(const tqd_circuit *c, int *device_error) {
     int v = 0;
     CHECK_CUDA(cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     *device_error = v;
+    if (v != 0) CHECK_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
     if (v == 1) {
         tqd::set_error("tqd_circuit_check: a bounded wait for a tile copy gave up");
         return TQD_ERR_TIMEOUT;
@@ -315,6 +316,12 @@ tqd_status tqd_circuit_check(const tqd_circuit *c, int *device_error) {
         tqd::set_error("tqd_circuit_check: a checked kernel found an index out of range (code %d)", v);
         return TQD_ERR_NUMERIC;
     }
+    return TQD_OK;
+}
+
+tqd_status tqd_circuit_test_stall(tqd_circuit *c, int enable) {
+    CHECK_ARG(c != nullptr, "tqd_circuit_test_stall: circuit is NULL");
+    c->test_stall = enable != 0;
     return TQD_OK;
 }
 

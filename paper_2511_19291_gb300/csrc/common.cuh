@@ -89,6 +89,18 @@ __device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
     return f2_unpack(d);
 }
 
+// ---------------------------------------------------------- bounded waits
+// Every spin wait of the library gives up after this much elapsed time on the
+// device's global nanosecond timer (a poll count has no bound in time: one
+// mbarrier.try_wait may suspend the thread for a hardware-chosen interval).
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+
+__device__ __forceinline__ uint64_t gtimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ------------------------------------------------------------- reductions
 // Kahan-compensated FP32 (or plain FP64) running sum.
 template <typename T> struct KSum {

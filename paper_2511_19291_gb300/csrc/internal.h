@@ -117,6 +117,7 @@ struct tqd_circuit {
     std::vector<void *> tc_blocks;   // tqd::TcBlock*, forward of passes whose gates all act on qubits 0..5
     tqd::TilePassDev *d_tile_desc;  // [pass][c64, c128] descriptors in device memory
     int *d_err;                  // device error word (bounded waits that gave up, failed checks)
+    mutable int test_stall = 0;  // tqd_circuit_test_stall: tile passes launch with TILE_STALL_TEST
     // pass-specialised kernels (CUfunction) per [precision][direction][kind][pass]
     // (kind: tqd::jit_kind of the buffer layout and whether psi is read-only),
     // compiled on first use; nullptr entries run the generic kernel

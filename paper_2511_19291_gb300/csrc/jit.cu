@@ -207,8 +207,26 @@ void emit_apply(std::string &o, const TilePassDev &D, const TileOp &op, bool adj
     }
 }
 
+// Gradient values of a tile in the order the reverse sweep meets them: value
+// i goes to the warp reduction as number i % 32 of its chunk (gpush), whose
+// warp totals are written to slots top - lane (top = n_grad - 1 - the values
+// of earlier chunks).  The encoder numbers a pass's gradient ops in forward
+// order, so the reverse order is slot n_grad - 1 - i; a pass that breaks
+// that order gets a source that does not compile.
+struct GradEmit {
+    int n_grad = 0;
+    int idx = 0;
+};
+
+void emit_push(std::string &o, GradEmit &ge, int slot, const char *expr) {
+    const int top = ge.n_grad - 1 - (ge.idx & ~31);
+    if (slot != ge.n_grad - 1 - ge.idx) put(o, "#error \"gradient slot %d out of order\"\n", slot);
+    put(o, "gpush<%d, TV>(ga, %s, c, %d);\n", ge.idx & 31, expr, top);
+    ++ge.idx;
+}
+
 // Reverse sweep: the op's angle derivatives from (psi, lambda) after it.
-void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
+void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op, GradEmit &ge) {
     if (op.type == TOP_DG) {
         bool need = false;
         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) need |= D.subs[q].gslot >= 0;
@@ -221,7 +239,8 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
             if (p & 0x80) snprintf(buf, len, "((tid >> %d) & 1u)", p & 0x7f);
             else buf[0] = 0;
         };
-        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+        // descending: the pass's values arrive in descending slot order
+        for (int q = op.sub0 + op.nsub - 1; q >= op.sub0; --q) {
             const TileSub &sb = D.subs[q];
             if (sb.gslot < 0) continue;
             char ta[32], tb[32], e[160];
@@ -239,17 +258,18 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op) {
             } else {
                 snprintf(e, sizeof e, "grad_diag<TV>(%d, %d, %d, %d, w, tid)", sb.type, sb.a, sb.b, sb.gen);
             }
-            put(o, "gacc_add<KRING>(c.gacc, %d, tid, %s);\n", sb.gslot, e);
+            emit_push(o, ge, sb.gslot, e);
         }
         o += "}\n";
         return;
     }
     if (op.gslot < 0) return;
+    char e[160];
     if (op.type == TOP_G1 || op.type == TOP_G1R)
-        put(o, "gacc_add<KRING>(c.gacc, %d, tid, grad_g1<%d, TV>(%d, a, b));\n", op.gslot, op.a, op.gen);
+        snprintf(e, sizeof e, "grad_g1<%d, TV>(%d, a, b)", op.a, op.gen);
     else
-        put(o, "gacc_add<KRING>(c.gacc, %d, tid, grad_diag_op<TV>(%d, %d, %d, %d, a, b, tid));\n", op.gslot,
-            op.type, op.a, op.b, op.gen);
+        snprintf(e, sizeof e, "grad_diag_op<TV>(%d, %d, %d, %d, a, b, tid)", op.type, op.a, op.b, op.gen);
+    emit_push(o, ge, op.gslot, e);
 }
 
 // The 16 shared-memory accesses of a stage: register j of the thread sits at
@@ -297,11 +317,13 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
     std::string o;
     o.reserve(1 << 16);
     o += "#include \"tile_dev.cuh\"\nnamespace tqd {\n";
-    put(o, "typedef %s TV;\ntypedef %s TT;\nconstexpr bool KADJ = %s;\nconstexpr bool KRING = %s;\n",
-        dt == 0 ? "float2" : "double2", dt == 0 ? "float" : "double", tf(adj), tf(ring));
-    o += "struct PassRunner {\n";
+    put(o, "typedef %s TV;\ntypedef %s TT;\nconstexpr bool KADJ = %s;\n", dt == 0 ? "float2" : "double2",
+        dt == 0 ? "float" : "double", tf(adj));
+    o += "struct PassRunner {\nGradAcc<TT> ga;\n";
     emit_init(o, D);
-    o += "__device__ __forceinline__ void run(const TileCtx<TV> &c) const {\n"
+    GradEmit ge;
+    ge.n_grad = h.n_grad;
+    o += "__device__ __forceinline__ void run(const TileCtx<TV> &c) {\n"
          "int *err = c.err;\n(void)err;\nconst uint32_t tid = c.tid;\n(void)tid;\nTV a[NR];\nTV b[NR];\n";
     for (int si = 0; si < h.n_stages; ++si) {
         const int s = adj ? h.n_stages - 1 - si : si;
@@ -316,7 +338,7 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
             for (int k = st.op_begin; k < st.op_end; ++k) emit_apply(o, D, D.ops[k], false);
         } else {
             for (int k = (int)st.op_end - 1; k >= (int)st.op_begin; --k) {
-                emit_grad(o, D, D.ops[k]);
+                emit_grad(o, D, D.ops[k], ge);
                 emit_apply(o, D, D.ops[k], true);
             }
         }
@@ -340,7 +362,16 @@ std::string generate(const TilePassDev &D, int dt, bool adj, bool ring, bool tma
         }
         o += "}\n";
     }
-    o += "}\n};\n}  // namespace tqd\n";
+    o += "}\n";
+    // end of a tile: the last chunk of gradient values (after the tile has
+    // been handed on)
+    if (adj && ge.n_grad > 0 && (ge.idx & 31) != 0)
+        put(o, "__device__ __forceinline__ void finish(const TileCtx<TV> &c) { gflush<%d, TV>(ga, c, %d); }\n",
+            ge.idx & 31, ge.n_grad - 1 - (ge.idx & ~31));
+    else
+        o += "__device__ __forceinline__ void finish(const TileCtx<TV> &) {}\n";
+    if (adj && ge.idx != ge.n_grad) put(o, "#error \"%d gradient values for %d slots\"\n", ge.idx, ge.n_grad);
+    o += "};\n}  // namespace tqd\n";
     // the generic kernels' launch bounds (tile_min_blocks<V, ADJ, 1>; ring: one block of G groups)
     const int minb = dt == 0 ? (adj ? 2 : 3) : 1;
     put(o,

@@ -112,16 +112,21 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
     return d;
 }
 
+// Bounded wait for phase `parity` of `bar`: false once WAIT_LIMIT_NS of
+// elapsed time passed without it.
 __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok = 0;
-    for (uint32_t it = 0; it < (1u << 26) && !ok; ++it) {
+    uint64_t t0 = 0;
+    for (bool first = true;; first = false) {
+        uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
             : "=r"(ok)
             : "r"(tc_sptr(bar)), "r"(parity)
             : "memory");
+        if (ok) return true;
+        if (first) t0 = gtimer_ns();
+        else if (gtimer_ns() - t0 > WAIT_LIMIT_NS) return false;
     }
-    return ok != 0;
 }
 
 // Pipelined over the block's tiles (one block per SM): two TMA buffers for

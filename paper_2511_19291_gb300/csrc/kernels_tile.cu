@@ -33,7 +33,7 @@ __global__ void __launch_bounds__((TMAW ? RingCfg<ADJ>::THREADS_TMAW : RingCfg<A
     k_tile_ring(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam,
                 const TilePassDev *__restrict__ Pg, const RT<V> *__restrict__ mats, double *__restrict__ partials,
                 int pblk, int *__restrict__ err, int flags) {
-    tile_pass_ring<V, ADJ, RingCfg<ADJ>::G, RingCfg<ADJ>::B, TMAW, InterpRunner<V, ADJ, true>>(
+    tile_pass_ring<V, ADJ, RingCfg<ADJ>::G, RingCfg<ADJ>::B, TMAW, InterpRunner<V, ADJ>>(
         &map_psi, &map_lam, Pg, mats, partials, pblk, err, flags);
 }
 
@@ -131,7 +131,7 @@ static uint32_t max_smem_ring(const tqd_circuit *c, int dt) {
 
 // Static shared memory of the ring body (descriptor head, barriers, counters).
 template <bool ADJ> static constexpr uint32_t ring_static_smem() {
-    return (uint32_t)(sizeof(TileHead) + RingCfg<ADJ>::B * (8 + 8 + 4) + RingCfg<ADJ>::G * 4 + 256);
+    return (uint32_t)(sizeof(TileHead) + RingCfg<ADJ>::B * (8 + 8 + 4) + RingCfg<ADJ>::G * 2 * 4 + 256);
 }
 
 template <typename V, bool ADJ>
@@ -291,7 +291,7 @@ cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *
     const void *src = psi_src ? psi_src : psi->amps;
     void *dst = psi_dst ? psi_dst : psi->amps;
     // a reverse pass whose psi comes from elsewhere leaves it as it is
-    const int flags = (lam && psi_src) ? TILE_PSI_RO : 0;
+    const int flags = ((lam && psi_src) ? TILE_PSI_RO : 0) | (c->test_stall ? TILE_STALL_TEST : 0);
     if (psi->dtype == TQD_C64)
         return lam ? launch_t<float2, true>(src, dst, lam, c, pass, flags, s)
                    : launch_t<float2, false>(src, dst, lam, c, pass, flags, s);

@@ -44,8 +44,11 @@ constexpr int TILE_MAX_OPS = 240;
 constexpr int TILE_MAX_DIMS = 5;  // TMA tensor rank limit
 
 // Launch flags of a tile pass.  TILE_PSI_RO (reverse sweep): psi is read from
-// a forward checkpoint and only lambda is written back.
+// a forward checkpoint and only lambda is written back.  TILE_STALL_TEST:
+// block 0 arms the barrier of its first tile without issuing the copy, so the
+// wait for that tile runs out its time limit (the test of the give-up path).
 constexpr int TILE_PSI_RO = 1;
+constexpr int TILE_STALL_TEST = 2;
 
 // Op types.  Positions are resolved per stage: `pos` < 0x80 is a register
 // position (bit of the register index), `pos` >= 0x80 is thread-index bit
@@ -136,9 +139,9 @@ static_assert(RingCfg<true>::G * TILE_THREADS * RingCfg<true>::REGS_GROUP + 128 
 static_assert(RingCfg<false>::G * TILE_THREADS * RingCfg<false>::REGS_GROUP + 128 * RingCfg<false>::REGS_TMA ==
                   RingCfg<false>::THREADS_TMAW * RingCfg<false>::REGS_LAUNCH,
               "register shares of the forward ring");
-// Gradient-partial columns of a ring kernel (threads t and t + 128 of every
-// group share one).
-constexpr int GACC_RING_COLS = TILE_THREADS / 2;
+// Gradient partials of the reverse sweep: one FP64 column per compute warp of
+// a block and gradient op.
+constexpr int TILE_WARPS = TILE_THREADS / 32;
 
 // Scalar part of a pass descriptor.
 struct TileHead {

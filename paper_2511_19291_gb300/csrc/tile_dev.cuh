@@ -15,8 +15,13 @@
 // (Im<lambda|P|psi> for R_P(t) = exp(-i t P/2), -2 Im<lambda|Pi|psi> for the
 // phase gates) over the tile.
 //
-// Every wait is bounded: a TMA load that does not complete sets the error
-// word and the block returns.
+// Gradient partials: inside one tile a thread sums its amplitudes' products
+// and the warp adds its 32 shares in state precision; across tiles every
+// partial is added in FP64 (one shared-memory column per warp and gradient op).
+//
+// Every wait is bounded in time (WAIT_LIMIT_NS on the global timer): a TMA
+// load that does not complete sets the error word and the block returns once
+// the copies it issued have landed (or their waits have run out too).
 #pragma once
 
 #include "tile_desc.h"  // first: it supplies the fixed-width integer types under NVRTC
@@ -542,14 +547,14 @@ struct TileSmem {
 
 // Shared-memory layout of a block: `nbuf` tile buffers, each holding psi's
 // tile (and lambda's in the reverse sweep), then the pass descriptor's parts;
-// `gcols` gradient-partial columns per gradient op.
+// `gcols` FP64 gradient-partial columns (one per compute warp) per gradient op.
 template <typename V, bool ADJ>
 __host__ __device__ inline TileSmem tile_smem_n(const TileHead &h, int nbuf, int gcols) {
     const int pool_len = h.pool_len, n_grad = h.n_grad, n_dg = h.n_dg, n_stages = h.n_stages;
     TileSmem s;
     s.tiles = (uint32_t)nbuf * (ADJ ? 2u : 1u) * (1u << TILE_K) * (uint32_t)sizeof(V);
     s.pool = (uint32_t)((pool_len * sizeof(RT<V>) + 15) & ~15u);
-    s.gacc = ADJ ? (uint32_t)(n_grad * gcols * sizeof(RT<V>)) : 0u;
+    s.gacc = ADJ ? (uint32_t)(n_grad * gcols * sizeof(double)) : 0u;
     s.gacc = (s.gacc + 15) & ~15u;
     s.dgt = (uint32_t)(n_dg * NR * sizeof(V));
     s.tbt = (uint32_t)((n_stages * TILE_TB * sizeof(uint16_t) + 15) & ~15u);
@@ -561,12 +566,12 @@ __host__ __device__ inline TileSmem tile_smem_n(const TileHead &h, int nbuf, int
 }
 template <typename V, bool ADJ, int NB>
 __host__ __device__ inline TileSmem tile_smem(const TileHead &h) {
-    return tile_smem_n<V, ADJ>(h, NB, TILE_THREADS);
+    return tile_smem_n<V, ADJ>(h, NB, TILE_WARPS);
 }
-// Ring kernels: B buffers shared by the block's groups; 128 gradient columns.
+// Ring kernels: B buffers shared by the block's G groups (G * 8 warp columns).
 template <typename V, bool ADJ, int B>
 __host__ __device__ inline TileSmem tile_smem_ring(const TileHead &h) {
-    return tile_smem_n<V, ADJ>(h, B, GACC_RING_COLS);
+    return tile_smem_n<V, ADJ>(h, B, RingCfg<ADJ>::G * TILE_WARPS);
 }
 
 // Blocks per SM the register budget is sized for: what the shared memory of
@@ -595,7 +600,7 @@ template <typename V> struct TileCtx {
     V *tile_a;               // psi's tile (2^K amplitudes, swizzled)
     V *tile_b;               // lambda's tile (reverse sweep)
     const RT<V> *pool;       // matrix scalars of the pass's ops
-    RT<V> *gacc;             // [gradient op][thread] partial derivatives
+    double *gacc;            // [warp column][gradient op] FP64 partial derivatives
     const V *dgt;            // [diagonal run][16] phase tables
     const uint16_t *tbt;     // [stage][TILE_TB] lane / warp address tables
     const TileStage *stages;
@@ -604,6 +609,8 @@ template <typename V> struct TileCtx {
     int n_stages;
     uint32_t tid;            // thread index within the group of 256 that works on the tile
     int lane, warp;
+    int gcols, gcol;         // gradient columns of the block; this warp's column
+    int n_grad;              // gradient ops of the pass
     uint32_t bar_id;         // named barrier of that group (0 = the whole block of 256)
     bool end_sync;           // the last stage ends with the group's barrier too (else each
                              // thread signals the tile's end itself, after its fence)
@@ -621,14 +628,115 @@ template <typename V> __device__ __forceinline__ void stage_sync(const TileCtx<V
     else if (lvl == SYNC_WARP) __syncwarp();
 }
 
-// Gradient partials: [gradient op][column].  One block per tile (ATOM false):
-// a column per thread, plain read-modify-write.  Ring kernels (ATOM true):
-// the groups share 128 columns (threads t and t + 128 of every group), added
-// with shared-memory atomics (GACC_RING_COLS columns).
-template <bool ATOM, typename T>
-__device__ __forceinline__ void gacc_add(T *gacc, int slot, uint32_t tid, T v) {
-    if constexpr (ATOM) atomicAdd(gacc + slot * GACC_RING_COLS + (tid & (GACC_RING_COLS - 1)), v);
-    else gacc[slot * TILE_THREADS + tid] += v;
+// ------------------------------------------------------ gradient partials
+// A gradient value of a tile is one thread's share (its 16 amplitudes, state
+// precision) of one angle derivative.  The warp's total of each value is
+// added in FP64 to the warp's own column gacc[gcol][slot]: no atomics, and
+// every sum across tiles is FP64.
+//
+// The warp totals come from a transposed butterfly.  Values are merged two at
+// a time like the digits of a binary counter: merging two partial sums of
+// level L (each already reduced over lane bits 0 .. L-1) exchanges over lane
+// bit L; lanes with that bit clear keep the first value's half, the others
+// the second's.  After 32 values -- or at the end of the tile, padded with
+// zeros -- lane i holds the warp total of the chunk's value i: one shuffle
+// per value instead of five.  The reverse sweep meets the pass's gradient ops
+// in descending slot order, so value i of a tile belongs to slot
+// n_grad - 1 - i.
+template <typename T> struct GradAcc {
+    T s[5];   // pending partial sums, s[L] of level L
+    int cnt;  // values in the current chunk (runtime form)
+    int done; // values of the tile already written (runtime form)
+};
+
+template <typename T> __device__ __forceinline__ T gmerge(T x, T y, int lane, int L) {
+    const bool hi = (lane >> L) & 1;
+    return (hi ? y : x) + __shfl_xor_sync(0xffffffffu, hi ? x : y, 1 << L);
+}
+template <typename T> __device__ __forceinline__ T gpad(T x, int lane, int L) {
+    const T t = x + __shfl_xor_sync(0xffffffffu, x, 1 << L);
+    return ((lane >> L) & 1) ? T(0) : t;
+}
+// Lanes i < m add their warp total v (value i of the chunk) to slot top - i.
+template <typename V>
+__device__ __forceinline__ void gwrite(const TileCtx<V> &c, int top, int m, RT<V> v) {
+    if (c.lane < m) c.gacc[c.gcol * c.n_grad + (top - c.lane)] += (double)v;
+}
+
+// Value number C (0..31, compile time) of the chunk that ends at slot top.
+template <int C, typename V>
+__device__ __forceinline__ void gpush(GradAcc<RT<V>> &ga, RT<V> v, const TileCtx<V> &c, int top) {
+    using T = RT<V>;
+    T g = v;
+    if constexpr (!(C & 1)) { ga.s[0] = g; return; }
+    g = gmerge<T>(ga.s[0], g, c.lane, 0);
+    if constexpr (!(C & 2)) { ga.s[1] = g; return; }
+    g = gmerge<T>(ga.s[1], g, c.lane, 1);
+    if constexpr (!(C & 4)) { ga.s[2] = g; return; }
+    g = gmerge<T>(ga.s[2], g, c.lane, 2);
+    if constexpr (!(C & 8)) { ga.s[3] = g; return; }
+    g = gmerge<T>(ga.s[3], g, c.lane, 3);
+    if constexpr (!(C & 16)) { ga.s[4] = g; return; }
+    g = gmerge<T>(ga.s[4], g, c.lane, 4);
+    gwrite<V>(c, top, 32, g);  // C == 31: the chunk is complete
+}
+// End of a chunk of M < 32 values (compile time): pad to 32 and write.
+template <int M, typename V>
+__device__ __forceinline__ void gflush(GradAcc<RT<V>> &ga, const TileCtx<V> &c, int top) {
+    using T = RT<V>;
+    if constexpr (M > 0) {
+        T acc = T(0);
+        bool have = false;
+#pragma unroll
+        for (int L = 0; L < 5; ++L) {
+            if (M & (1 << L)) {
+                acc = have ? gmerge<T>(ga.s[L], acc, c.lane, L) : gpad<T>(ga.s[L], c.lane, L);
+                have = true;
+            } else if (have) {
+                acc = gpad<T>(acc, c.lane, L);
+            }
+        }
+        gwrite<V>(c, top, M, acc);
+    }
+}
+// Runtime forms (the generic runner): the counter is uniform over the warp,
+// so every branch is too.
+template <typename V>
+__device__ __forceinline__ void gpush_rt(GradAcc<RT<V>> &ga, RT<V> v, const TileCtx<V> &c) {
+    using T = RT<V>;
+    T g = v;
+#pragma unroll
+    for (int L = 0; L < 5; ++L) {
+        if (!(ga.cnt & (1 << L))) {
+            ga.s[L] = g;
+            ++ga.cnt;
+            return;
+        }
+        g = gmerge<T>(ga.s[L], g, c.lane, L);
+    }
+    gwrite<V>(c, c.n_grad - 1 - ga.done, 32, g);
+    ga.cnt = 0;
+    ga.done += 32;
+}
+template <typename V>
+__device__ __forceinline__ void gflush_rt(GradAcc<RT<V>> &ga, const TileCtx<V> &c) {
+    using T = RT<V>;
+    if (ga.cnt > 0) {
+        T acc = T(0);
+        bool have = false;
+#pragma unroll
+        for (int L = 0; L < 5; ++L) {
+            if (ga.cnt & (1 << L)) {
+                acc = have ? gmerge<T>(ga.s[L], acc, c.lane, L) : gpad<T>(ga.s[L], c.lane, L);
+                have = true;
+            } else if (have) {
+                acc = gpad<T>(acc, c.lane, L);
+            }
+        }
+        gwrite<V>(c, c.n_grad - 1 - ga.done, ga.cnt, acc);
+    }
+    ga.cnt = 0;
+    ga.done = 0;
 }
 
 // Register j's tile index in a stage: lane and warp table entries XOR the
@@ -721,9 +829,17 @@ __device__ __forceinline__ void tile_stl2(const TileCtx<V> &c, const V (&a)[NR],
 }
 
 // The generic stage runner: interprets the pass's stage and op lists.
-template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
-    __device__ __forceinline__ void init(const TileCtx<V> &) {}
-    __device__ __forceinline__ void run(const TileCtx<V> &c) const {
+// finish(c) ends a tile: the reverse sweep writes the last gradient chunk.
+template <typename V, bool ADJ> struct InterpRunner {
+    GradAcc<RT<V>> ga;
+    __device__ __forceinline__ void init(const TileCtx<V> &) {
+        ga.cnt = 0;
+        ga.done = 0;
+    }
+    __device__ __forceinline__ void finish(const TileCtx<V> &c) {
+        if (ADJ) gflush_rt<V>(ga, c);
+    }
+    __device__ __forceinline__ void run(const TileCtx<V> &c) {
         using T = RT<V>;
         int *err = c.err;
         for (int si = 0; si < c.n_stages; ++si) {
@@ -754,13 +870,15 @@ template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
                         T w[NR];
 #pragma unroll
                         for (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);
-                        for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+                        // descending, so that the pass's gradient values arrive in
+                        // descending slot order
+                        for (int q = op.sub0 + op.nsub - 1; q >= op.sub0; --q) {
                             const TileSub sb = c.subs[q];
                             if (sb.gslot < 0) continue;
-                            gacc_add<ATOM>(c.gacc, sb.gslot, c.tid, grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, c.tid));
+                            gpush_rt<V>(ga, grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, c.tid), c);
                         }
                     } else if (op.gslot >= 0) {
-                        gacc_add<ATOM>(c.gacc, op.gslot, c.tid, grad_op<V>(op, a, b, c.tid));
+                        gpush_rt<V>(ga, grad_op<V>(op, a, b, c.tid), c);
                     }
                     apply_op<V, true, true>(op, a, b, c.pool, c.tid, c.subs, c.dgt);
                 }
@@ -787,7 +905,7 @@ template <typename V, bool ADJ, bool ATOM = false> struct InterpRunner {
 template <typename V> struct TileShared {
     V *tiles;
     RT<V> *pool;
-    RT<V> *gacc;
+    double *gacc;
     V *dgt;
     uint16_t *tbt;
     TileStage *stages;
@@ -812,7 +930,7 @@ __device__ __forceinline__ TileShared<V> tile_setup(const TileHead &P, const Til
     TileShared<V> S;
     S.tiles = reinterpret_cast<V *>(sm);
     S.pool = reinterpret_cast<T *>(sm + L.tiles);
-    S.gacc = reinterpret_cast<T *>(sm + L.tiles + L.pool);
+    S.gacc = reinterpret_cast<double *>(sm + L.tiles + L.pool);
     S.dgt = reinterpret_cast<V *>(sm + L.tiles + L.pool + L.gacc);
     S.tbt = reinterpret_cast<uint16_t *>(sm + L.tiles + L.pool + L.gacc + L.dgt);
     S.stages = reinterpret_cast<TileStage *>(sm + L.tiles + L.pool + L.gacc + L.dgt + L.tbt);
@@ -852,7 +970,7 @@ __device__ __forceinline__ TileShared<V> tile_setup(const TileHead &P, const Til
                                                                                      : St.st_hi[e - 64 - NW];
     }
     if (ADJ) {
-        for (int i = tid; i < P.n_grad * gcols; i += blockDim.x) S.gacc[i] = T(0);
+        for (int i = tid; i < P.n_grad * gcols; i += blockDim.x) S.gacc[i] = 0.0;
     }
     __syncthreads();
     // phase tables of the diagonal runs: entry j = product of the run's gates
@@ -885,15 +1003,18 @@ __device__ __forceinline__ void tile_coords(const TileHead &P, uint64_t tile, in
 }
 
 // One thread: TMA loads of a tile (psi, and lambda when ADJ) into `dst`,
-// completing on barrier `bar`.
+// completing on barrier `bar`.  stall (TILE_STALL_TEST): the barrier is armed
+// for the tile's bytes but no copy is issued, so its phase never completes
+// and the wait for it runs out (nothing is in flight for it either).
 template <typename V, bool ADJ>
 __device__ __forceinline__ void tile_issue_load(const TileHead &P, const void *map_psi, const void *map_lam, V *dst,
-                                                uint64_t *bar, uint64_t tile) {
+                                                uint64_t *bar, uint64_t tile, bool stall = false) {
     constexpr int TS = 1 << TILE_K;
     constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
     const uint32_t tile_bytes = TS * (uint32_t)sizeof(V);
     const uint32_t box_bytes = tile_bytes >> P.n_extra;
     mbar_expect_tx(bar, tile_bytes * NSTATE);
+    if (stall) return;
     for (int e = 0; e < (1 << P.n_extra); ++e) {
         int c[TILE_MAX_DIMS];
         tile_coords(P, tile, e, c);
@@ -926,23 +1047,24 @@ __device__ __forceinline__ void tile_issue_store(const TileHead &P, const void *
 }
 
 // Bounded wait of one thread for phase `parity` of barrier `bar`: 1 when the
-// phase completed, 0 when the wait gave up.
+// phase completed, 0 when WAIT_LIMIT_NS passed first.
 __device__ __forceinline__ int mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; !mbar_try_wait(bar, parity);)
-        if (++it > (1u << 26)) return 0;
+    if (mbar_try_wait(bar, parity)) return 1;
+    const uint64_t t0 = gtimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (gtimer_ns() - t0 > WAIT_LIMIT_NS) return 0;
     return 1;
 }
 
-// Gradient partials of the block (gcols columns per gradient op, state
-// precision) added in FP64, one warp per gradient op.  Ends the pass.
-// nw: the warps taking part (the block's first nw).
-template <typename T>
-__device__ __forceinline__ void tile_write_partials(const TileHead &P, const TilePassDev *Pg, const T *gacc, int gcols,
-                                                    double *partials, int pblk, int nw) {
+// Gradient partials of the block (gcols FP64 columns of n_grad entries)
+// summed in FP64, one warp per gradient op.  Ends the pass.  nw: the warps taking
+// part (the block's first nw).
+__device__ __forceinline__ void tile_write_partials(const TileHead &P, const TilePassDev *Pg, const double *gacc,
+                                                    int gcols, double *partials, int pblk, int nw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = warp; k < P.n_grad; k += nw) {
         double t = 0;
-        for (int i = lane; i < gcols; i += 32) t += (double)gacc[k * gcols + i];
+        for (int i = lane; i < gcols; i += 32) t += gacc[i * P.n_grad + k];
         t = warp_sum(t);
         if (lane == 0) partials[(size_t)Pg->grad_gate_slot[k] * pblk + blockIdx.x] = t;
     }
@@ -964,6 +1086,7 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     __syncthreads();
     const TileSmem L = tile_smem<V, ADJ, NB>(P);
     const uint32_t tid = threadIdx.x;
+    const bool stall = (flags & TILE_STALL_TEST) && blockIdx.x == 0;
     if (tid == 0) {
         // the barriers sit after the descriptor parts; initialised before the
         // setup's first __syncthreads
@@ -973,7 +1096,7 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
         for (int i = 0; i < NB; ++i) mbar_init(bar + i, 1);
         mbar_fence_init();
     }
-    const TileShared<V> S = tile_setup<V, ADJ>(P, Pg, mats, L, TILE_THREADS, err);
+    const TileShared<V> S = tile_setup<V, ADJ>(P, Pg, mats, L, TILE_WARPS, err);
     uint64_t *bar = S.bar;
 
     constexpr int TS = 1 << TILE_K;          // amplitudes per tile
@@ -1006,6 +1129,9 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     ctx.tid = tid;
     ctx.lane = tid & 31;
     ctx.warp = tid >> 5;
+    ctx.gcols = TILE_WARPS;
+    ctx.gcol = ctx.warp;
+    ctx.n_grad = P.n_grad;
     ctx.bar_id = 0;
     ctx.end_sync = true;
     ctx.err = err;
@@ -1015,21 +1141,26 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     // NB = 2: the next tile's copy is in flight while this one is computed;
     // a buffer is refilled only after its previous store has read it.
     if (NB == 2 && tid == 0 && blockIdx.x < n_tiles)
-        tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles, bar, blockIdx.x);
+        tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles, bar, blockIdx.x, stall);
     int iter = 0;
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++iter) {
         const int cur = NB == 2 ? (iter & 1) : 0;
+        bool next_issued = false;
         if (tid == 0) {
             const uint64_t next = NB == 2 ? tile + gridDim.x : tile;
             if (next < n_tiles) {
                 bulk_wait_read0();
                 const int nb = NB == 2 ? cur ^ 1 : 0;
-                tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)nb * NSTATE * TS, bar + nb, next);
+                tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)nb * NSTATE * TS, bar + nb, next,
+                                        NB == 1 && stall && iter == 0);
+                next_issued = NB == 2;
             }
         }
         if (!wait_tile(cur)) {
             if (tid == 0) {
                 atomicExch(err, 1);
+                // the other buffer's copy (NB = 2) lands before the block leaves
+                if (next_issued) mbar_wait_bounded(bar + (cur ^ 1), (parity >> (cur ^ 1)) & 1u);
                 bulk_wait0();
             }
             return;
@@ -1038,13 +1169,13 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
         ctx.tile_b = ctx.tile_a + TS;
         runner.run(ctx);
         if (tid == 0) tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile, flags);
+        runner.finish(ctx);
     }
     if (tid == 0) bulk_wait0();
     if (ADJ) {
         __syncthreads();
-        // per-thread partial sums (state precision, about 16 amplitudes x
-        // the block's tiles each) are added in FP64, one warp per gradient op
-        tile_write_partials(P, Pg, S.gacc, TILE_THREADS, partials, pblk, TILE_THREADS / 32);
+        // the warps' FP64 columns, summed in FP64, one warp per gradient op
+        tile_write_partials(P, Pg, S.gacc, TILE_WARPS, partials, pblk, TILE_WARPS);
     }
 }
 
@@ -1088,7 +1219,10 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     __shared__ uint64_t fullb[B];
     __shared__ uint64_t doneb[B];
     __shared__ int gen[B];
-    __shared__ int s_timeout[G];
+    // per group and parity of its iteration: the first thread's wait outcome
+    // (two slots, so a slot is rewritten only after every thread of the group
+    // has passed the group barrier that follows its next read)
+    __shared__ int s_timeout[G][2];
     copy_words(&P, &Pg->h, sizeof(TileHead));
     const uint32_t tid = threadIdx.x;
     if (tid == 0) {
@@ -1101,18 +1235,28 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     }
     __syncthreads();
     const TileSmem L = tile_smem_ring<V, ADJ, B>(P);
-    const TileShared<V> S = tile_setup<V, ADJ>(P, Pg, mats, L, GACC_RING_COLS, err);
+    const TileShared<V> S = tile_setup<V, ADJ>(P, Pg, mats, L, G * TILE_WARPS, err);
 
     constexpr int TS = 1 << TILE_K;
     constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
     const uint64_t n_tiles = (uint64_t)1 << P.n_tiles_log2;
     const uint64_t n_local = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int grp = (int)(tid >> 8);  // G: the TMA warp
+    const bool stall = (flags & TILE_STALL_TEST) && blockIdx.x == 0;
+
+    // Before a thread that issued loads leaves early: wait (bounded) until
+    // the copies of tiles k0 .. k0 + B - 1 (its share: k = first mod step)
+    // have landed, so no copy is still writing into the block's shared
+    // memory when it exits.  A phase that already completed passes at once.
+    auto drain = [&](uint64_t k0, uint64_t first, uint64_t step) {
+        for (uint64_t k = k0; k < k0 + B && k < n_local; ++k)
+            if (k % step == first % step) mbar_wait_bounded(fullb + (int)(k % B), (uint32_t)(k / B) & 1u);
+    };
 
     if (!TMAW && tid == 0)
         for (int k = 0; k < B && (uint64_t)k < n_local; ++k)
             tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
-                                    blockIdx.x + (uint64_t)k * gridDim.x);
+                                    blockIdx.x + (uint64_t)k * gridDim.x, stall && k == 0);
     if (TMAW && grp == G) {
         // the TMA warpgroup gives registers to the groups and leaves when its
         // copies are done (the groups write the gradient partials)
@@ -1128,8 +1272,9 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
         if ((tid & 31) == 0 && pw < (uint32_t)NP) {
             for (int k = (int)pw; k < B && (uint64_t)k < n_local; k += NP)
                 tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
-                                        blockIdx.x + (uint64_t)k * gridDim.x);
-            for (uint64_t k = pw; k < n_local; k += NP) {
+                                        blockIdx.x + (uint64_t)k * gridDim.x, stall && k == 0);
+            uint64_t k = pw;
+            for (; k < n_local; k += NP) {
                 const int slot = (int)(k % B);
                 V *buf = S.tiles + (size_t)slot * NSTATE * TS;
                 if (!mbar_wait_bounded(doneb + slot, (uint32_t)(k / B) & 1u)) {
@@ -1143,6 +1288,9 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
                     tile_issue_load<V, ADJ>(P, map_psi, map_lam, buf, fullb + slot, tile + (uint64_t)B * gridDim.x);
                 }
             }
+            // the loads this thread issued and nobody took: tiles k .. k + B - 1
+            // of its share (none when the loop ran to the end)
+            if (k < n_local) drain(k, pw, NP);
             bulk_wait0();
         }
         return;
@@ -1161,12 +1309,16 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
         ctx.tid = gtid;
         ctx.lane = gtid & 31;
         ctx.warp = gtid >> 5;
+        ctx.gcols = G * TILE_WARPS;
+        ctx.gcol = grp * TILE_WARPS + ctx.warp;
+        ctx.n_grad = P.n_grad;
         ctx.bar_id = 1 + grp;
         ctx.end_sync = !TMAW;
         ctx.err = err;
         Runner runner;
         runner.init(ctx);
-        for (uint64_t k = grp; k < n_local; k += G) {
+        uint32_t it = 0;  // this group's iteration count
+        for (uint64_t k = grp; k < n_local; k += G, ++it) {
             const int slot = (int)(k % B);
             const uint32_t round = (uint32_t)(k / B);
             if (gtid == 0) {
@@ -1174,22 +1326,30 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
                 // tile k - B taken (only needed when buffers pass between groups)
                 if (B % G != 0) {
                     volatile int *gv = gen;
-                    for (uint32_t it = 0; gv[slot] < (int)round;)
-                        if (++it > (1u << 26)) {
-                            ok = 0;
-                            break;
-                        }
+                    if (gv[slot] < (int)round) {
+                        const uint64_t t0 = gtimer_ns();
+                        while (gv[slot] < (int)round)
+                            if (gtimer_ns() - t0 > WAIT_LIMIT_NS) {
+                                ok = 0;
+                                break;
+                            }
+                    }
                 }
                 if (ok) ok = mbar_wait_bounded(fullb + slot, round & 1u);
                 if (ok && B % G != 0) {
                     volatile int *gv = gen;
                     gv[slot] = (int)round + 1;
                 }
-                s_timeout[grp] = !ok;
+                s_timeout[grp][it & 1] = !ok;
             }
             asm volatile("bar.sync %0, %1;" ::"r"(ctx.bar_id), "n"(TILE_THREADS) : "memory");
-            if (s_timeout[grp]) {
-                if (gtid == 0) atomicExch(err, 1);
+            if (s_timeout[grp][it & 1]) {
+                if (gtid == 0) {
+                    atomicExch(err, 1);
+                    // without the TMA warpgroup this thread issued refills:
+                    // let every copy of the next B tiles land first
+                    if (!TMAW) drain(k, 0, 1);
+                }
                 break;
             }
             if (gtid != 0) mbar_try_wait(fullb + slot, round & 1u);
@@ -1213,13 +1373,16 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
                                             tile + (uint64_t)B * gridDim.x);
                 }
             }
+            // the tile's last gradient values go to the warps' FP64 columns
+            // after the tile has been handed on
+            runner.finish(ctx);
         }
         if (!TMAW && gtid == 0) bulk_wait0();
     }
     if (ADJ) {
         // the groups only (the TMA warpgroup has left): named barrier 15
         asm volatile("bar.sync 15, %0;" ::"n"(G * TILE_THREADS) : "memory");
-        tile_write_partials(P, Pg, S.gacc, GACC_RING_COLS, partials, pblk, G * TILE_THREADS / 32);
+        tile_write_partials(P, Pg, S.gacc, G * TILE_WARPS, partials, pblk, G * TILE_WARPS);
     }
 }
 

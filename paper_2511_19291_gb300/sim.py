@@ -205,11 +205,18 @@ class Circuit:
         return {"passes": a.value, "launches_apply": b.value, "launches_backward": c.value}
 
     def check(self) -> int:
-        """Synchronize and return the device error word (0 = all launches of
-        this circuit completed normally); raises on a non-zero word."""
+        """Synchronize, return the device error word (0 = all launches of
+        this circuit since the last check completed normally) and clear it;
+        raises on a non-zero word."""
         v = C.c_int()
         _lib.check(_L().tqd_circuit_check(self._h, C.byref(v)))
         return v.value
+
+    def test_stall(self, enable: bool) -> None:
+        """Test hook: while enabled, block 0 of every fused tile pass waits for
+        a tile copy that is never issued, runs out its time limit and
+        returns (the launch's results are invalid)."""
+        _lib.check(_L().tqd_circuit_test_stall(self._h, int(bool(enable))))
 
     def __del__(self):
         h = getattr(self, "_h", None)

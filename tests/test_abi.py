@@ -93,6 +93,8 @@ def test_null_handles_rejected(lib):
     assert lib.tqd_backward(None, None, None, None, None, 0, None, 1.0, None, None) == 1
     assert lib.tqd_state_free(None) == 0
     assert lib.tqd_circuit_free(None) == 0
+    assert lib.tqd_circuit_test_stall(None, 1) == 1
+    assert lib.tqd_circuit_check(None, None) == 1
 
 
 def test_specialised_pass_kernels_compile(lib):
