@@ -46,7 +46,7 @@ def check_batch(items, batch):
         e_ref, g_ref = reference(circ, params, terms)
         assert abs(energies[c] - e_ref) < 1e-5, (c, circ.n_qubits, energies[c], e_ref)
         g = batch.grads_of(c).cpu().numpy()
-        ok, worst = grad_close(g, g_ref, 1e-4, hnorm=W.observable_l1(terms))
+        ok, worst = grad_close(g, g_ref, 1e-4)
         assert ok, (c, circ.n_qubits, len(circ.gates), worst, float(np.max(np.abs(g - g_ref))),
                     float(np.max(np.abs(g_ref))))
 

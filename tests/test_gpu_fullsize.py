@@ -71,12 +71,12 @@ def test_main_workload_26q():
     del psi, lam, c
     torch.cuda.empty_cache()
     assert abs(e_v - e_d) < 1e-5
-    assert grad_close(g_v, g_d, 1e-4, hnorm=h1)[0]
+    assert grad_close(g_v, g_d, 1e-4)[0]
     print(f"\n26q: E c64 fused {e_f:.10f} plain {e_p:.10f} c128 {e_d:.14f}; "
           f"max|dg| fused {np.max(np.abs(g_f - g_d)):.2e} plain {np.max(np.abs(g_p - g_d)):.2e} (||H||_1 {h1})")
     assert abs(e_f - e_d) < 1e-5 and abs(e_p - e_d) < 1e-5
-    assert grad_close(g_f, g_d, 1e-4, hnorm=h1)[0]
-    assert grad_close(g_p, g_d, 1e-4, hnorm=h1)[0]
+    assert grad_close(g_f, g_d, 1e-4)[0]
+    assert grad_close(g_p, g_d, 1e-4)[0]
 
 
 def test_zero_angles_closed_form_26q():
@@ -116,7 +116,7 @@ def test_grad_workload_24q_finite_differences():
     del psi
     torch.cuda.empty_cache()
     assert abs(e_f - e_d) < 1e-5
-    ok, worst = grad_close(g_f, g_d, 1e-4, hnorm=h1)
+    ok, worst = grad_close(g_f, g_d, 1e-4)
     assert ok, worst
 
 
@@ -131,7 +131,7 @@ def test_grad_workload_form_14q_parameter_shift():
     for dtype, rel, hn in ((torch.complex64, 1e-4, W.observable_l1(terms)), (torch.complex128, 1e-10, None)):
         e, g, _ = energy_and_grad(circ, params, terms, dtype)
         assert abs(e - e_ref) < (1e-5 if dtype == torch.complex64 else 1e-12)
-        ok, worst = grad_close(g, ref, rel, hnorm=hn)
+        ok, worst = grad_close(g, ref, rel)
         assert ok, (dtype, worst)
 
 
@@ -176,4 +176,4 @@ def test_qft_31q_c64_error_against_c128():
     print(f"\n31q: |E64 - E128| = {abs(e64 - e128):.3e}, max|g64 - g128|/||H||_1 = "
           f"{np.max(np.abs(g64 - g128)) / h1:.3e}")
     assert abs(e64 - e128) < 1e-5
-    assert grad_close(g64, g128, 1e-4, hnorm=h1)[0]
+    assert grad_close(g64, g128, 1e-4)[0]

@@ -50,7 +50,7 @@ def test_expval_parity(dtype, n, seed):
     e_ref, per_ref = oracle.expval(n, psi, terms)
     e = S.expval(st, terms).item()
     per = S.expval_terms(st, terms).cpu().numpy()
-    assert abs(e - e_ref) <= E_TOL[dtype] * max(1.0, W.observable_l1(terms) / 10)
+    assert abs(e - e_ref) <= E_TOL[dtype], (e, e_ref)
     np.testing.assert_allclose(per, per_ref, atol=E_TOL[dtype], rtol=0)
 
 
@@ -126,7 +126,7 @@ def test_fused_tile_variants_random(variant, dtype, n, ng, seed):
     del st
     ref = oracle.grad_param_shift(circ, params, terms)
     g, st = gpu_grad(circ, params, terms, "fused", dtype, **kw)
-    ok, worst = grad_close(g, ref, G_REL[dtype], hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+    ok, worst = grad_close(g, ref, G_REL[dtype])
     assert ok, f"worst relative error {worst}"
     back = to_numpy(st)
     e0 = np.zeros(1 << n, dtype=complex)
@@ -153,7 +153,7 @@ def test_ring_many_tiles_per_block(jit, buffers, n, layers, max_blocks):
     np.testing.assert_allclose(to_numpy(st), oracle.run(circ, params), atol=AMP_TOL["c64"] * 4, rtol=0)
     del st
     g, st = gpu_grad(circ, params, terms, "fused", "c64", **kw)
-    ok, worst = grad_close(g, ref, G_REL["c64"], hnorm=W.observable_l1(terms))
+    ok, worst = grad_close(g, ref, G_REL["c64"])
     assert ok, f"worst relative error {worst}"
     back = to_numpy(st)
     e0 = np.zeros(1 << n, dtype=complex)
@@ -251,7 +251,7 @@ def test_autograd_function_paths(dtype):
     ref_e = oracle.energy(circ, params, terms)
     ref_g = oracle.grad_param_shift(circ, params, terms)
     e0 = S.expval_fn(params_tensor(params), c, terms, dtype=DTYPES[dtype])
-    assert not e0.requires_grad and abs(e0.item() - ref_e) < E_TOL[dtype] * 10
+    assert not e0.requires_grad and abs(e0.item() - ref_e) < E_TOL[dtype], (e0.item(), ref_e)
     p32 = torch.tensor(params, dtype=torch.float32, device="cuda", requires_grad=True)
     e = S.expval_fn(p32, c, terms, dtype=DTYPES[dtype])
     (-0.5 * e).backward()
@@ -259,13 +259,12 @@ def test_autograd_function_paths(dtype):
     # float32 angles: compare with the oracle at the rounded angles
     p_r = p32.detach().double().cpu().numpy()
     ok, worst = grad_close(p32.grad.double().cpu().numpy(), -0.5 * oracle.grad_param_shift(circ, p_r, terms),
-                           1e-4, hnorm=W.observable_l1(terms))
+                           1e-4)
     assert ok, worst
     p64 = params_tensor(params).requires_grad_(True)
     e = S.expval_fn(p64, c, terms, dtype=DTYPES[dtype])
     e.backward(retain_graph=False)
-    ok, worst = grad_close(p64.grad.cpu().numpy(), ref_g, G_REL[dtype],
-                           hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+    ok, worst = grad_close(p64.grad.cpu().numpy(), ref_g, G_REL[dtype])
     assert ok, worst
     with pytest.raises(RuntimeError):
         e.backward()
@@ -381,7 +380,7 @@ def tensor_core_case(n, blocks, seed, **kw):
     lam = S.State(n, torch.complex64)
     g = torch.zeros(circ.n_params, dtype=torch.float64, device="cuda")
     S.backward(st, lam, c, p, terms, g)
-    ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4, hnorm=W.observable_l1(terms))
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4)
     assert ok, worst
     # complex128 states take the tile path for the same plan
     st2, _, _ = gpu_state(circ, params, "tc", "c128", **kw)
@@ -414,8 +413,7 @@ def test_value_and_grad(mode, dtype, n, layers, extra):
         e, g = S.value_and_grad(psi, lam, c, p, terms)
         torch.cuda.synchronize()
         assert abs(e.item() - e_ref) < E_TOL[dtype], (rep, e.item(), e_ref)
-        ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype],
-                               hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+        ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype])
         assert ok, worst
     back = to_numpy(psi)
     e0 = np.zeros(1 << n, dtype=complex)
@@ -445,8 +443,7 @@ def test_value_and_grad_permutation_tail(dtype, checkpoints):
     e, g = S.value_and_grad(psi, lam, c, params_tensor(params), terms)
     torch.cuda.synchronize()
     assert abs(e.item() - e_ref) < E_TOL[dtype], (e.item(), e_ref)
-    ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype],
-                           hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype])
     assert ok, worst
     back = to_numpy(psi)
     assert abs(back[0] - 1) < AMP_TOL[dtype] * 200
@@ -485,8 +482,7 @@ def test_value_and_grad_checkpoints(dtype, checkpoints, jit):
         prof = {q["name"]: q for q in S.profile_read()}
         S.profile_enable(False)
         assert abs(e.item() - e_ref) < E_TOL[dtype], (rep, e.item(), e_ref)
-        ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype],
-                               hnorm=W.observable_l1(terms) if dtype == "c64" else None)
+        ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype])
         assert ok, worst
         # the passes that run: those before the ansatz's closing CNOT ladder
         # (a permutation the observable is conjugated through)
@@ -551,7 +547,7 @@ def test_value_and_grad_checkpoints_tensor_core():
     S.profile_enable(False)
     assert prof.get("tc_block", {}).get("launches", 0) >= 1
     assert abs(e.item() - e_ref) < 1e-5
-    ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4, hnorm=W.observable_l1(terms))
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4)
     assert ok, worst
     back = to_numpy(psi)
     assert back[0] == 1 and np.count_nonzero(back) == 1
