@@ -81,15 +81,18 @@ def workload(args):
     return W.workload_hea(2, args.n, args.layers, "ising")
 
 
-def config_of(args, w, plan):
+def config_of(args, w, plan, amplitudes="complex64"):
+    reductions = ("fp64 (the oracle's own sums)" if amplitudes == "complex128" else
+                  "gradients: fp32 inside one tile (a thread's 16 amplitudes, then the warp's 32 shares), fp64 "
+                  "across tiles and blocks; expectations: fp32 per-thread partials, fp64 across threads and blocks")
     return {
         "workload": f"hea ansatz n={args.n} layers={args.layers} ({w.circuit.n_params} angles), "
                     f"open-chain Ising H ({len(w.terms)} terms), forward + expval + adjoint gradient",
         "n_qubits": args.n, "layers": args.layers, "n_params": w.circuit.n_params,
         "gates": len(w.circuit.gates), "plan": plan, "tile_buffers": args.buffers or "default",
         "pass_kernels": {0: "default", 1: "generic", 2: "specialised"}[args.jit],
-        "amplitudes": "complex64",
-        "reductions": "fp64 beyond per-thread partials",
+        "amplitudes": amplitudes,
+        "reductions": reductions,
         "l2": "inputs larger than L2 (state 2^n x 8 B; no flush needed)",
         "parallelism": "replicas",
     }
@@ -222,21 +225,35 @@ def oracle_all_cores(n, layers, gate_sample=6, term_sample=2, procs=None, deadli
     run would spread them this way): the rate is the sum of the processes'
     extrapolated rates.  Plain subprocesses with a deadline: one that dies
     or overruns turns the measurement into an 'unavailable' note."""
-    procs = procs or os.cpu_count() or 1
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        cores = os.cpu_count() or 1
+    procs = procs or cores
     try:  # about 3 states per process (the state and numpy temporaries), in half the free memory
         avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
         procs = max(1, min(procs, int(avail / 2 // (3 * 16 << n))))
     except (ValueError, OSError, AttributeError):
         pass
+    # each process builds its inputs, then waits for a line on stdin before
+    # timing, so that the timed samples of all processes overlap
     code = ("import json, sys; sys.path.insert(0, {root!r}); import bench; "
             "from paper_2511_19291_gb300 import workloads as W; "
-            "v, _, t = bench.oracle_sample(W.workload_hea(2, {n}, {layers}, 'ising'), {g}, {t}); "
+            "wl = W.workload_hea(2, {n}, {layers}, 'ising'); sys.stdin.readline(); "
+            "v, _, t = bench.oracle_sample(wl, {g}, {t}); "
             "print(json.dumps([v, t]))").format(root=ROOT, n=n, layers=layers, g=gate_sample, t=term_sample)
-    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
-                           text=True) for _ in range(procs)]
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                           stderr=subprocess.DEVNULL, text=True) for _ in range(procs)]
     end = time.monotonic() + deadline_s
     values = []
     try:
+        time.sleep(min(5.0, deadline_s / 10))  # imports and inputs ready
+        for p in ps:
+            try:
+                p.stdin.write("go\n")
+                p.stdin.flush()
+            except (BrokenPipeError, OSError):
+                pass
         for p in ps:
             out, _ = p.communicate(timeout=max(0.01, end - time.monotonic()))
             if p.returncode != 0:
@@ -250,9 +267,11 @@ def oracle_all_cores(n, layers, gate_sample=6, term_sample=2, procs=None, deadli
                 p.kill()
                 p.wait()
     sample = (f"{gate_sample} gates and {term_sample} terms of the {n}-qubit workload in each of {procs} "
-              f"concurrent single-threaded processes (one per host core), each extrapolated to one "
-              f"parameter-shift gradient; rate = sum over processes")
-    return {"value": sum(values), "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample}
+              f"concurrent single-threaded processes ({cores} host cores available; processes capped by free "
+              f"memory), started together, each extrapolated to one parameter-shift gradient; rate = sum over "
+              f"processes")
+    return {"value": sum(values), "unit": UNIT, "cores": procs, "host_cores": cores, "kind": "oracle",
+            "sample": sample}
 
 
 def run_reference(args):
@@ -272,7 +291,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-        "data": "synthetic", "config": config_of(args, w, "oracle"),
+        "data": "synthetic", "config": config_of(args, w, "oracle", amplitudes="complex128"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -330,10 +349,16 @@ def sweep_bench(S, torch, dev, n, barrier, reps=5):
     del st
     torch.cuda.empty_cache()
     peak, src = peaks()
-    best = max(r["dram_gbs"] for r in rows)
-    worst = min(r["dram_gbs"] for r in rows)
-    return {"n_qubits": n, "rows": rows, "min_frac": worst / peak, "max_frac": best / peak,
-            "frac_bytes": "dram_gbs (reads in 128-byte lines, writes in 32-byte sectors)",
+    for r in rows:
+        r["frac"] = round(r["gbs"] / peak, 3)
+        r["frac_dram"] = round(r["dram_gbs"] / peak, 3)
+    return {"n_qubits": n, "rows": rows,
+            "min_frac": min(r["gbs"] for r in rows) / peak, "max_frac": max(r["gbs"] for r in rows) / peak,
+            "min_frac_dram": min(r["dram_gbs"] for r in rows) / peak,
+            "max_frac_dram": max(r["dram_gbs"] for r in rows) / peak,
+            "frac_bytes": "frac: algorithmic bytes (the amplitudes the gate changes, read and written); "
+                          "frac_dram: bytes HBM moves at its granularity (reads in 128-byte lines, writes in "
+                          "32-byte sectors)",
             "peak": peak, "peak_source": f"{src} hbm_gbs"}
 
 
@@ -505,6 +530,37 @@ def qft_bench(S, torch, dev, n, barrier, layers=8):
     return out
 
 
+# ----------------------------------------------------------- error statement
+def error_statement(args, e_step, e_check, g_step):
+    """The step's E against a separate tqd_expval of a fresh forward pass, and
+    E and the gradient against the stored complex128 oracle values of this
+    workload (tests/golden, written by tests/golden/make_golden.py from the
+    oracle alone: E, and parameter-shift derivatives at a sample of angles)."""
+    import numpy as np
+    out = {"energy_step": e_step, "energy_expval": e_check, "energy_step_vs_expval": abs(e_step - e_check)}
+    name = {(26, 20): "hea26x20_ising.json", (24, 10): "hea24x10_ising.json"}.get((args.n, args.layers))
+    path = os.path.join(ROOT, "tests", "golden", name) if name else None
+    if not path or not os.path.exists(path):
+        out["oracle"] = None
+        return out
+    with open(path) as f:
+        ref = json.load(f)
+    idx = np.array(ref["grad_indices"])
+    g_ref = np.array(ref["grad"])
+    dg = np.abs(g_step[idx] - g_ref)
+    big = np.abs(g_ref) >= 1e-2 * np.max(np.abs(g_ref))
+    out["oracle"] = {
+        "reference": f"complex128 oracle, tests/golden/{name}: E and dE/dtheta by parameter shift at "
+                     f"{len(idx)} angles {idx.tolist()}",
+        "energy": ref["energy"], "energy_abs_err": abs(e_step - ref["energy"]),
+        "grad_max_abs_err": float(np.max(dg)),
+        "grad_norm_rel_err": float(np.max(dg) / np.max(np.abs(g_ref))),
+        "grad_max_rel_err": float(np.max(dg[big] / np.abs(g_ref[big]))),
+        "tolerance": "1e-5 absolute on E; 1e-4 relative on the gradient (max|dg| / max|g|)",
+    }
+    return out
+
+
 # ------------------------------------------------------------- our path
 def main():
     args = parse()
@@ -626,10 +682,17 @@ def main():
         qft = qft_bench(S, torch, dev, args.qft_n, barrier)
         psi = S.State(n, torch.complex64, dev)
 
-    # sanity of the numbers being timed: E of this step against a fresh forward
+    # the numbers being timed: one clean step (the gradient buffer accumulates
+    # over steps), its E against a fresh forward's tqd_expval, and both E and
+    # the gradient against the oracle's stored values for this workload
+    grads.zero_()
+    step(circ)
+    e_step = float(e_out.item())
+    g_step = grads.cpu().numpy()
     psi.reset(0)
     S.apply(psi, circ, params)
     e_check = S.expval(psi, obs).item()
+    error = error_statement(args, e_step, e_check, g_step)
 
     if rank != 0:
         if world > 1:
@@ -684,7 +747,8 @@ def main():
         "qft32": qft,
         "clocks": clk.summary(),
         "kernels": kernels,
-        "energy": e_check,
+        "energy": e_step,
+        "error": error,
     }
     print(json.dumps(line))
     if world > 1:

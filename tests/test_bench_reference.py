@@ -31,6 +31,7 @@ def test_reference_arm_line():
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
     assert d["value"] > 0 and abs(d["ms_per_step"] - 1000.0 / d["value"]) < 1e-6 * d["ms_per_step"]
     assert d["config"]["n_qubits"] == 26 and d["config"]["layers"] == 20
+    assert d["dtype"] == "c128" and d["config"]["amplitudes"] == "complex128"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
@@ -50,6 +51,7 @@ def test_oracle_on_all_cores_small():
     import bench
     r = bench.oracle_all_cores(14, 2, gate_sample=4, term_sample=2, procs=2)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "grad-evals/s" and r["value"] > 0
+    assert r["host_cores"] == len(os.sched_getaffinity(0))
     slow = bench.oracle_all_cores(24, 10, gate_sample=6, term_sample=2, procs=2, deadline_s=0.01)
     assert "unavailable" in slow
     left = subprocess.run(["ps", "-eo", "args"], capture_output=True, text=True).stdout
