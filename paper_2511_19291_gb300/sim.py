@@ -460,12 +460,13 @@ class _MeasureFn(torch.autograd.Function):
         if psi is None:
             raise RuntimeError("this measurement's backward already ran (the saved state is consumed)")
         lam = State(psi.n, psi.tensor.dtype, psi.device)
-        # The per-term outputs carry no coefficient: weight_j = grad_j / coeff_j
-        # cancels the coefficient applied inside the library.
-        coeffs = torch.tensor([t.coeff for t in ctx.obs.terms], dtype=torch.float64, device=params.device)
-        w = (grad_out.to(torch.float64) / coeffs).contiguous()
+        # The per-term outputs <P_j> carry no coefficient, so the seed is
+        # sum_j grad_j P_j psi: the same Pauli strings with unit coefficients,
+        # weighted by the incoming gradient.
+        unit = Observable([W.PauliTerm(1.0, t.ops) for t in ctx.obs.terms])
+        w = grad_out.to(torch.float64).contiguous()
         grads = torch.zeros_like(params)
-        backward(psi, lam, ctx.circuit, params, ctx.obs, grads, weights=w)
+        backward(psi, lam, ctx.circuit, params, unit, grads, weights=w)
         ctx.psi = None
         return grads, None, None, None, None
 
