@@ -681,6 +681,7 @@ def main():
         torch.cuda.empty_cache()
         qft = qft_bench(S, torch, dev, args.qft_n, barrier)
         psi = S.State(n, torch.complex64, dev)
+        lam = S.State(n, torch.complex64, dev)
 
     # the numbers being timed: one clean step (the gradient buffer accumulates
     # over steps), its E against a fresh forward's tqd_expval, and both E and

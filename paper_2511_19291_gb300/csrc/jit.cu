@@ -198,6 +198,42 @@ void emit_apply(std::string &o, const TilePassDev &D, const TileOp &op, bool adj
             put(o, "op_d2rr<TV, %s, %s, %d, %d>(a, b, c.pool + %d);\n", dg, two, op.a, op.b, op.moff);
         break;
     case TOP_DG:
+        if (op.b) {
+            // gates on tile bits: at this tile, those on tile bits only or on
+            // a tile bit and a thread bit multiply the thread factor, those on
+            // a tile bit and register position r a phase e<r> on r
+            bool reg_used[TILE_R] = {false};
+            for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+                const TileSub &sb = D.subs[q];
+                if ((sb.a & 0xC0) == TILE_POS_TILE && sb.type == TOP_D2 && !(sb.b & 0xC0)) reg_used[sb.b] = true;
+            }
+            o += "{\n";
+            if (dg_has_thread_subs(D, op)) put(o, "TV tf = f%d;\n", op.moff);
+            else o += "TV tf = mkc<TV>(1, 0);\n";
+            for (int r = 0; r < TILE_R; ++r)
+                if (reg_used[r]) put(o, "TV e%d = mkc<TV>(1, 0);\n", r);
+            for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
+                const TileSub &sb = D.subs[q];
+                if ((sb.a & 0xC0) != TILE_POS_TILE) continue;
+                if (sb.type == TOP_D1)
+                    put(o, "tf = cmul(tf, pool_c<TV>(c.pool, %d + (tile_bit(c.torig, %d) ? 6 : 0)));\n", sb.moff,
+                        sb.a);
+                else if ((sb.b & 0xC0) == TILE_POS_TILE)
+                    put(o, "if (tile_bit(c.torig, %d) & tile_bit(c.torig, %d)) tf = cmul(tf, pool_c<TV>(c.pool, %d));\n",
+                        sb.a, sb.b, sb.moff);
+                else if (sb.b & 0x80)
+                    put(o, "if (tile_bit(c.torig, %d) & tbit(tid, %d)) tf = cmul(tf, pool_c<TV>(c.pool, %d));\n",
+                        sb.a, sb.b, sb.moff);
+                else
+                    put(o, "if (tile_bit(c.torig, %d)) e%d = cmul(e%d, pool_c<TV>(c.pool, %d));\n", sb.a, sb.b, sb.b,
+                        sb.moff);
+            }
+            put(o, "op_dg<TV, %s, %s, true>(a, b, c.dgt + %d * NR, tf);\n", dg, two, op.moff);
+            for (int r = 0; r < TILE_R; ++r)
+                if (reg_used[r]) put(o, "op_ph<TV, %s, %s, %d>(a, b, e%d);\n", dg, two, r, r);
+            o += "}\n";
+            break;
+        }
         // the table, times the run's thread factor (computed once per block by init)
         if (dg_has_thread_subs(D, op)) put(o, "op_dg<TV, %s, %s, true>(a, b, c.dgt + %d * NR, f%d);\n", dg, two, op.moff, op.moff);
         else put(o, "op_dg<TV, %s, %s, false>(a, b, c.dgt + %d * NR, mkc<TV>(1, 0));\n", dg, two, op.moff);
@@ -235,15 +271,17 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op, GradEmit 
         // and the per-register-bit sums ws[r] each costs at most one fma.
         o += "{\nTT w[NR];\nfor (int j = 0; j < NR; ++j) w[j] = im_cdot(b[j], a[j]);\n"
              "TT wt, ws[TILE_R];\ndiag_sums<TT>(w, wt, ws);\n";
+        // a thread or tile bit's value as an expression; "" for a register position
         auto bit = [](uint8_t p, char *buf, size_t len) {
             if (p & 0x80) snprintf(buf, len, "((tid >> %d) & 1u)", p & 0x7f);
+            else if ((p & 0xC0) == TILE_POS_TILE) snprintf(buf, len, "tile_bit(c.torig, %d)", p);
             else buf[0] = 0;
         };
         // descending: the pass's values arrive in descending slot order
         for (int q = op.sub0 + op.nsub - 1; q >= op.sub0; --q) {
             const TileSub &sb = D.subs[q];
             if (sb.gslot < 0) continue;
-            char ta[32], tb[32], e[160];
+            char ta[48], tb[48], e[200];
             bit(sb.a, ta, sizeof ta);
             if (sb.type == TOP_D1 && (sb.gen == GEN_Z || sb.gen == GEN_P1)) {
                 const bool z = sb.gen == GEN_Z;
@@ -254,9 +292,9 @@ void emit_grad(std::string &o, const TilePassDev &D, const TileOp &op, GradEmit 
                 if (ta[0] && tb[0]) snprintf(e, sizeof e, "((%s & %s) ? TT(-2) * wt : TT(0))", ta, tb);
                 else if (ta[0] || tb[0])
                     snprintf(e, sizeof e, "(%s ? TT(-2) * ws[%d] : TT(0))", ta[0] ? ta : tb, ta[0] ? sb.b : sb.a);
-                else snprintf(e, sizeof e, "grad_diag<TV>(%d, %d, %d, %d, w, tid)", sb.type, sb.a, sb.b, sb.gen);
+                else snprintf(e, sizeof e, "grad_diag<TV>(%d, %d, %d, %d, w, tid, c.torig)", sb.type, sb.a, sb.b, sb.gen);
             } else {
-                snprintf(e, sizeof e, "grad_diag<TV>(%d, %d, %d, %d, w, tid)", sb.type, sb.a, sb.b, sb.gen);
+                snprintf(e, sizeof e, "grad_diag<TV>(%d, %d, %d, %d, w, tid, c.torig)", sb.type, sb.a, sb.b, sb.gen);
             }
             emit_push(o, ge, sb.gslot, e);
         }

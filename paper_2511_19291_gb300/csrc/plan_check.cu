@@ -150,12 +150,34 @@ bool run_pass(const tqd_circuit *c, const TilePlanPass &P, int dt, const double 
             };
             for (int y = 0; y < TS; ++y) a[y] = tile[addr(y, !rev)];
             auto bit = [&](uint8_t pos) { return (pos & 0x80) ? (int)st.thr[pos & 0x7f] : (int)st.reg[pos]; };
+            auto is_tile = [](uint8_t pos) { return (pos & 0xC0) == TILE_POS_TILE; };
+            auto tile_bit = [&](uint8_t pos) { return (int)((origin >> (pos & 0x3f)) & 1u); };
             auto one = [&](int k) {
                 const TileOp &op = D.ops[k];
                 if (op.type == TOP_DG) {
                     for (int i = 0; i < op.nsub; ++i) {
                         const int q = rev ? op.sub0 + op.nsub - 1 - i : op.sub0 + i;
                         const TileSub &sb = D.subs[q];
+                        if (is_tile(sb.a)) {
+                            // a qubit outside the pass's set: its bit is the tile's
+                            const Mat &M = sub_m[q];
+                            const int ta = tile_bit(sb.a);
+                            if (sb.type == TOP_D1) {
+                                const cplx d = ta ? M.e[1][1] : M.e[0][0];
+                                for (auto &x : a) x *= rev ? std::conj(d) : d;
+                            } else if (is_tile(sb.b)) {
+                                if (ta && tile_bit(sb.b))
+                                    for (auto &x : a) x *= rev ? std::conj(M.e[3][3]) : M.e[3][3];
+                            } else if (ta) {
+                                Mat P1;
+                                P1.d = 2;
+                                P1.e[0][0] = 1;
+                                P1.e[0][1] = P1.e[1][0] = 0;
+                                P1.e[1][1] = M.e[3][3];
+                                apply_bits(a, P1, bit(sb.b), 0, rev);
+                            }
+                            continue;
+                        }
                         apply_bits(a, sub_m[q], bit(sb.a), sb.type == TOP_D2 ? bit(sb.b) : 0, rev);
                     }
                     return;

@@ -1,11 +1,18 @@
 // plan_tile.cu -- host planner of the fused tile passes.
 //
 // 1. Passes.  Starting at the first gate not yet done, the pass's qubit set Q
-//    is qubits 0..3 plus the first other qubits touched in gate order (up to
-//    12).  Gates are then absorbed in order: a gate joins the pass when all
-//    its wires are in Q and no earlier gate left out of the pass touches any
-//    of them.  Every gate left out therefore commutes with every absorbed gate
-//    after it, so executing the pass before the rest preserves the circuit.
+//    is qubits 0..3 plus the first other qubits touched, in gate order, by
+//    gates that are not diagonal (up to 12).  Gates are then absorbed in
+//    order: a gate joins the pass when no earlier gate left out of the pass
+//    touches any of its wires and either all its wires are in Q or it is
+//    diagonal.  A diagonal gate on a qubit outside Q multiplies each
+//    amplitude by a phase of its index bits, and the bits outside Q are the
+//    same for all amplitudes of a tile, so the kernels apply it from the
+//    tile's origin.  Every gate left out commutes with every absorbed gate
+//    after it, so executing the pass before the rest preserves the circuit;
+//    two absorbed gates on the same qubit outside Q are both diagonal and
+//    commute.  A pass whose ops do not fit the descriptor is cut back to a
+//    prefix of its gates (the rest stay for later passes).
 // 2. TMA box.  Q's qubits above 3 are grouped into runs; the tensor map has at
 //    most 5 dimensions, so runs that do not fit become "extra" bits, copied by
 //    2^extra TMA operations per tile.
@@ -340,6 +347,7 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
             if (done[g]) continue;
             ++scanned;
             const GateH &gh = c->gates[g];
+            if (gate_diagonal(gh.kind)) continue;  // needs none of its qubits in Q
             if (!try_add(gh.w, gh.nw) && g == first) break;
         }
         // fill: qubits that extend an existing run first, then any
@@ -349,24 +357,27 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
         if (qn < TILE_K || !tile_layout(n, inQ, lay)) return {};
         {
             const GateH &g0 = c->gates[first];
-            for (int a = 0; a < g0.nw; ++a)
+            for (int a = 0; a < g0.nw && !gate_diagonal(g0.kind); ++a)
                 if (!inQ[g0.w[a]]) return {};
         }
         // --- absorb gates
         TilePlanPass P;
         P.layout = lay;
         std::vector<char> blocked(n, 0);
-        int blocked_in_q = 0, ngrad = 0;
+        int blocked_in_q = 0, ngrad = 0, ndiag = 0;
         for (int g = first; g < L; ++g) {
             if (done[g]) continue;
             const GateH &gh = c->gates[g];
             const bool is_grad = c->grad_slot[g] >= 0;
-            bool ok = (int)P.gates.size() < TILE_MAX_OPS && (!is_grad || ngrad < TILE_MAX_GRAD);
-            for (int a = 0; a < gh.nw && ok; ++a) ok = inQ[gh.w[a]] && !blocked[gh.w[a]];
+            const bool diag = gate_diagonal(gh.kind);
+            bool ok = (int)P.gates.size() < TILE_MAX_GATES && (!is_grad || ngrad < TILE_MAX_GRAD) &&
+                      (diag ? ndiag < TILE_MAX_SUBS : (int)P.gates.size() - ndiag < TILE_MAX_OPS);
+            for (int a = 0; a < gh.nw && ok; ++a) ok = (diag || inQ[gh.w[a]]) && !blocked[gh.w[a]];
             if (ok) {
                 P.gates.push_back(g);
                 done[g] = 1;
                 if (is_grad) ++ngrad;
+                if (diag) ++ndiag;
             } else {
                 for (int a = 0; a < gh.nw; ++a) {
                     if (!blocked[gh.w[a]]) {
@@ -375,6 +386,19 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
                     }
                 }
                 if (blocked_in_q == TILE_K) break;
+            }
+        }
+        // a pass whose ops do not fit the descriptor (too many diagonal runs,
+        // sub-ops or stages) keeps a prefix of its gates, in circuit order:
+        // the gates cut off run in later passes, after every gate kept
+        {
+            TilePlanPass T = P;
+            while (!encode_tile_pass(c, T)) {
+                if (P.gates.size() <= 1) return {};
+                const size_t keep = P.gates.size() * 3 / 4;
+                for (size_t i = keep; i < P.gates.size(); ++i) done[P.gates[i]] = 0;
+                P.gates.resize(keep);
+                T = P;
             }
         }
         passes.push_back(P);
@@ -420,6 +444,7 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
             const GateH &g = c->gates[P.gates[i]];
             for (int a = 0; a < g.nw; ++a) {
                 const int lb = loc[g.w[a]];
+                if (lb < 0) continue;  // outside Q: diagonal gates, which commute
                 if (last[lb] >= 0) preds[i].push_back(last[lb]);
                 last[lb] = i;
             }
@@ -629,6 +654,11 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                     if (ts.thr[u] == lb) return (uint8_t)(0x80 | u);
                 return 0xff;
             };
+            // position of qubit q: a local bit's, or a tile bit's outside Q
+            auto posq = [&](int q) -> uint8_t {
+                return loc[q] >= 0 ? pos(loc[q]) : (uint8_t)(TILE_POS_TILE | q);
+            };
+            auto is_tile = [](uint8_t p) { return (p & 0xC0) == TILE_POS_TILE; };
             auto grad_of = [&](int gi, uint8_t &gen, int16_t &gslot) -> bool {
                 const int slot = c->grad_slot[gi];
                 gen = slot >= 0 ? (uint8_t)gate_gen(c->gates[gi].kind) : 0;
@@ -641,31 +671,45 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                 }
                 return true;
             };
-            // a diagonal gate that can join a run: 1-qubit, or 2-qubit with both
-            // positions on register bits or both on thread bits
+            // a diagonal gate that can join a run: 1-qubit, or 2-qubit with a
+            // tile bit, or with both positions on register bits or both on
+            // thread bits
             auto runnable = [&](int gi) {
                 const GateH &g = c->gates[gi];
                 if (!gate_diagonal(g.kind)) return false;
                 if (g.nw == 1) return true;
-                const uint8_t pa = pos(loc[g.w[0]]), pb = pos(loc[g.w[1]]);
+                const uint8_t pa = posq(g.w[0]), pb = posq(g.w[1]);
+                if (is_tile(pa) || is_tile(pb)) return true;
                 return ((pa & 0x80) != 0) == ((pb & 0x80) != 0);
+            };
+            // gates on tile bits exist only inside runs (a run of one, if need be)
+            auto on_tile = [&](int gi) {
+                const GateH &g = c->gates[gi];
+                for (int a = 0; a < g.nw; ++a)
+                    if (loc[g.w[a]] < 0) return true;
+                return false;
             };
             ts.op_begin = (uint16_t)nops;
             int k = lead_end;
             while (k < trail_begin) {
                 const int gi0 = P.gates[order[k]];
                 int run_end = k;
-                while (run_end < trail_begin && runnable(P.gates[order[run_end]])) ++run_end;
+                bool run_tile = false;
+                while (run_end < trail_begin && runnable(P.gates[order[run_end]])) {
+                    run_tile = run_tile || on_tile(P.gates[order[run_end]]);
+                    ++run_end;
+                }
                 if (nops >= TILE_MAX_OPS) return false;
                 TileOp &op = D.ops[nops];
                 memset(&op, 0, sizeof(op));
                 op.moff = -1;
                 op.gslot = -1;
                 op.sub0 = -1;
-                if (run_end - k >= 2) {
-                    // diagonal run
+                if (run_end - k >= 2 || run_tile) {
+                    // diagonal run (b = 1: some of its gates are on tile bits)
                     if (D.h.n_dg >= TILE_MAX_DG || nsubs + (run_end - k) > TILE_MAX_SUBS) return false;
                     op.type = TOP_DG;
+                    op.b = run_tile ? 1 : 0;
                     op.moff = (int16_t)D.h.n_dg;
                     op.sub0 = (int16_t)nsubs;
                     op.nsub = (int16_t)(run_end - k);
@@ -675,8 +719,16 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
                         const GateH &g = c->gates[gi];
                         TileSub &sb = D.subs[nsubs];
                         sb.type = g.nw == 1 ? TOP_D1 : TOP_D2;
-                        sb.a = pos(loc[g.w[0]]);
-                        sb.b = g.nw > 1 ? pos(loc[g.w[1]]) : 0;
+                        sb.a = posq(g.w[0]);
+                        sb.b = g.nw > 1 ? posq(g.w[1]) : 0;
+                        // a two-qubit gate on a tile bit has it in a (the phase
+                        // is symmetric in the two bits)
+                        if (g.nw > 1 && is_tile(sb.b) && !is_tile(sb.a)) {
+                            const uint8_t t = sb.a;
+                            sb.a = sb.b;
+                            sb.b = t;
+                        }
+                        if (sb.a == 0xff || (g.nw > 1 && sb.b == 0xff)) return false;
                         if (!grad_of(gi, sb.gen, sb.gslot)) return false;
                         const int len = sb.type == TOP_D1 ? 8 : 2;
                         sb.moff = (int16_t)pool;

@@ -41,6 +41,7 @@ constexpr int TILE_THREADS = 1 << TILE_T;
 constexpr int TILE_LOW = 4;       // qubits 0..3 are in every tile (128-byte runs for c64)
 constexpr int TILE_MAX_STAGES = 40;
 constexpr int TILE_MAX_OPS = 240;
+constexpr int TILE_MAX_GATES = 480;  // gates absorbed by one pass (ops and diagonal sub-ops)
 constexpr int TILE_MAX_DIMS = 5;  // TMA tensor rank limit
 
 // Launch flags of a tile pass.  TILE_PSI_RO (reverse sweep): psi is read from
@@ -50,9 +51,12 @@ constexpr int TILE_MAX_DIMS = 5;  // TMA tensor rank limit
 constexpr int TILE_PSI_RO = 1;
 constexpr int TILE_STALL_TEST = 2;
 
-// Op types.  Positions are resolved per stage: `pos` < 0x80 is a register
+// Op types.  Positions are resolved per stage: `pos` < 0x40 is a register
 // position (bit of the register index), `pos` >= 0x80 is thread-index bit
-// (pos & 0x7f).
+// (pos & 0x7f), and 0x40 <= `pos` < 0x80 is a qubit outside the pass's set,
+// qubit (pos & 0x3f): a tile bit, the same for every amplitude of a tile (a
+// bit of the tile's global origin).  Only diagonal gates of a run (TOP_DG)
+// have tile bits; a two-qubit one has its tile bit in `a`.
 enum TileOpType : uint8_t {
     TOP_G1 = 0,  // dense 2x2 on register position a
     TOP_D1 = 1,  // diagonal diag(m00, m11) on position a (register or thread)
@@ -83,7 +87,8 @@ struct TileSub {
     int16_t gslot;
 };
 
-constexpr int TILE_MAX_SUBS = 160;
+constexpr int TILE_MAX_SUBS = 448;
+constexpr uint8_t TILE_POS_TILE = 0x40;  // tile-bit position flag (see the op types)
 constexpr int TILE_MAX_DG = 64;
 
 // Shared-memory addresses of a stage.  Register j of thread (lane, warp)

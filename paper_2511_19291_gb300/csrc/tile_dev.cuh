@@ -355,6 +355,48 @@ __device__ __forceinline__ void op_dg(V (&a)[NR], V (&b)[NR], const V *t, V f) {
 
 __device__ __forceinline__ uint32_t tbit(uint32_t tid, uint8_t pos) { return (tid >> (pos & 0x7f)) & 1u; }
 
+// Tile-bit positions (qubits outside the pass's set): the bit of the tile's
+// global origin.
+__device__ __forceinline__ bool is_tile_pos(uint8_t pos) { return (pos & 0xC0) == TILE_POS_TILE; }
+__device__ __forceinline__ uint32_t tile_bit(uint64_t torig, uint8_t pos) {
+    return (uint32_t)(torig >> (pos & 0x3f)) & 1u;
+}
+
+// Phase e on the |1> half of register position P (psi, and lambda when TWO).
+template <typename V, bool DAG, bool TWO, int P>
+__device__ __forceinline__ void op_ph(V (&a)[NR], V (&b)[NR], V e) {
+    if (DAG) e = conjv(e);
+    rph<P>(a, e);
+    if (TWO) rph<P>(b, e);
+}
+
+// The gates of a diagonal run that have a tile bit, at the current tile:
+// those on tile bits only, or on a tile bit and a thread bit, multiply this
+// thread's factor f; those on a tile bit and register position r multiply
+// e[r] (bit r of emask set).  Tile bits are in sub-op position a.
+template <typename V>
+__device__ __forceinline__ void dg_tile_part(const TileOp &op, const TileSub *subs, const RT<V> *pool, uint32_t tid,
+                                             uint64_t torig, V &f, V (&e)[TILE_R], uint32_t &emask) {
+    for (int i = op.sub0; i < op.sub0 + op.nsub; ++i) {
+        const TileSub sb = subs[i];
+        if (!is_tile_pos(sb.a)) continue;
+        const uint32_t ta = tile_bit(torig, sb.a);
+        if (sb.type == TOP_D1) {
+            f = cmul(f, pool_c<V>(pool, sb.moff + (ta ? 6 : 0)));
+        } else if (ta) {
+            const V ph = pool_c<V>(pool, sb.moff);
+            if (is_tile_pos(sb.b)) {
+                if (tile_bit(torig, sb.b)) f = cmul(f, ph);
+            } else if (sb.b & 0x80) {
+                if (tbit(tid, sb.b)) f = cmul(f, ph);
+            } else {
+                e[sb.b] = (emask >> sb.b) & 1u ? cmul(e[sb.b], ph) : ph;
+                emask |= 1u << sb.b;
+            }
+        }
+    }
+}
+
 // Per-thread factor of a diagonal run: the product of its gates whose
 // positions are all thread bits.  *any tells whether there is one.
 template <typename V>
@@ -379,7 +421,7 @@ __device__ __forceinline__ V dg_thread_factor(const TileOp &op, const TileSub *s
 // The generic kernel's op: positions read from the descriptor.
 template <typename V, bool DAG, bool TWO>
 __device__ __forceinline__ void apply_op(const TileOp &op, V (&a)[NR], V (&b)[NR], const RT<V> *pool, uint32_t tid,
-                                         const TileSub *subs, const V *dgt) {
+                                         const TileSub *subs, const V *dgt, uint64_t torig) {
     const RT<V> *m = pool + op.moff;
     switch (op.type) {
     case TOP_G1R:
@@ -387,9 +429,21 @@ __device__ __forceinline__ void apply_op(const TileOp &op, V (&a)[NR], V (&b)[NR
         break;
     case TOP_DG: {
         bool any;
-        const V f = dg_thread_factor<V>(op, subs, pool, tid, any);
-        if (any) op_dg<V, DAG, TWO, true>(a, b, dgt + op.moff * NR, f);
-        else op_dg<V, DAG, TWO, false>(a, b, dgt + op.moff * NR, f);
+        V f = dg_thread_factor<V>(op, subs, pool, tid, any);
+        if (op.b) {  // gates on tile bits
+            V e[TILE_R];
+            uint32_t em = 0;
+            dg_tile_part<V>(op, subs, pool, tid, torig, f, e, em);
+            op_dg<V, DAG, TWO, true>(a, b, dgt + op.moff * NR, f);
+            if (em & 1u) op_ph<V, DAG, TWO, 0>(a, b, e[0]);
+            if (em & 2u) op_ph<V, DAG, TWO, 1>(a, b, e[1]);
+            if (em & 4u) op_ph<V, DAG, TWO, 2>(a, b, e[2]);
+            if (em & 8u) op_ph<V, DAG, TWO, 3>(a, b, e[3]);
+        } else if (any) {
+            op_dg<V, DAG, TWO, true>(a, b, dgt + op.moff * NR, f);
+        } else {
+            op_dg<V, DAG, TWO, false>(a, b, dgt + op.moff * NR, f);
+        }
         break;
     }
     case TOP_G1:
@@ -462,11 +516,13 @@ __device__ __forceinline__ RT<V> grad_g1(int gen, const V (&a)[NR], const V (&b)
 // (unchanged by diagonal gates, so one w serves a whole run).
 template <typename V>
 __device__ __forceinline__ RT<V> grad_diag(uint8_t type, uint8_t pa, uint8_t pb, uint8_t gen, const RT<V> (&w)[NR],
-                                           uint32_t tid) {
+                                           uint32_t tid, uint64_t torig = 0) {
     using T = RT<V>;
     T s = 0;
     auto bit_of = [&](uint8_t pos, int j) -> int {
-        return (pos & 0x80) ? (int)((tid >> (pos & 0x7f)) & 1u) : ((j >> pos) & 1);
+        return (pos & 0x80)       ? (int)((tid >> (pos & 0x7f)) & 1u)
+               : is_tile_pos(pos) ? (int)tile_bit(torig, pos)
+                                  : ((j >> pos) & 1);
     };
     if (type == TOP_D1) {
 #pragma unroll
@@ -611,6 +667,7 @@ template <typename V> struct TileCtx {
     int lane, warp;
     int gcols, gcol;         // gradient columns of the block; this warp's column
     int n_grad;              // gradient ops of the pass
+    uint64_t torig;          // global index of the current tile's local index 0 (its tile bits)
     uint32_t bar_id;         // named barrier of that group (0 = the whole block of 256)
     bool end_sync;           // the last stage ends with the group's barrier too (else each
                              // thread signals the tile's end itself, after its fence)
@@ -862,7 +919,7 @@ template <typename V, bool ADJ> struct InterpRunner {
             }
             if (!ADJ) {
                 for (int k = st.op_begin; k < st.op_end; ++k)
-                    apply_op<V, false, false>(c.ops[k], a, b, c.pool, c.tid, c.subs, c.dgt);
+                    apply_op<V, false, false>(c.ops[k], a, b, c.pool, c.tid, c.subs, c.dgt, c.torig);
             } else {
                 for (int k = (int)st.op_end - 1; k >= (int)st.op_begin; --k) {
                     const TileOp op = c.ops[k];
@@ -875,12 +932,12 @@ template <typename V, bool ADJ> struct InterpRunner {
                         for (int q = op.sub0 + op.nsub - 1; q >= op.sub0; --q) {
                             const TileSub sb = c.subs[q];
                             if (sb.gslot < 0) continue;
-                            gpush_rt<V>(ga, grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, c.tid), c);
+                            gpush_rt<V>(ga, grad_diag<V>(sb.type, sb.a, sb.b, sb.gen, w, c.tid, c.torig), c);
                         }
                     } else if (op.gslot >= 0) {
                         gpush_rt<V>(ga, grad_op<V>(op, a, b, c.tid), c);
                     }
-                    apply_op<V, true, true>(op, a, b, c.pool, c.tid, c.subs, c.dgt);
+                    apply_op<V, true, true>(op, a, b, c.pool, c.tid, c.subs, c.dgt, c.torig);
                 }
             }
             stage_sync(c, st.sync_mid);
@@ -981,7 +1038,7 @@ __device__ __forceinline__ TileShared<V> tile_setup(const TileHead &P, const Til
         V t = mkc<V>(1, 0);
         for (int q = op.sub0; q < op.sub0 + op.nsub; ++q) {
             const TileSub sb = S.subs[q];
-            if (sb.a & 0x80) continue;
+            if (sb.a & 0xC0) continue;  // thread or tile bits
             if (sb.type == TOP_D1) t = cmul(t, pool_c<V>(S.pool, sb.moff + (((j >> sb.a) & 1) ? 6 : 0)));
             else if (((j >> sb.a) & 1) && ((j >> sb.b) & 1)) t = cmul(t, pool_c<V>(S.pool, sb.moff));
         }
@@ -1000,6 +1057,14 @@ __device__ __forceinline__ void tile_coords(const TileHead &P, uint64_t tile, in
 #pragma unroll
     for (int d = 0; d < TILE_MAX_DIMS; ++d)
         c[d] = d < P.rank ? (int)((g >> P.dim_lo[d]) & ((1ull << P.dim_len[d]) - 1)) : 0;
+}
+
+// Global index of local index 0 of a tile (the values of the qubits outside
+// the pass's set).
+__device__ __forceinline__ uint64_t tile_origin(const TileHead &P, uint64_t tile) {
+    uint64_t g = 0;
+    for (int i = 0; i < P.n_tiles_log2; ++i) g |= ((tile >> i) & 1ull) << P.out_bits[i];
+    return g;
 }
 
 // One thread: TMA loads of a tile (psi, and lambda when ADJ) into `dst`,
@@ -1167,6 +1232,7 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
         }
         ctx.tile_a = S.tiles + (size_t)cur * NSTATE * TS;
         ctx.tile_b = ctx.tile_a + TS;
+        ctx.torig = tile_origin(P, tile);
         runner.run(ctx);
         if (tid == 0) tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile, flags);
         runner.finish(ctx);
@@ -1355,6 +1421,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
             if (gtid != 0) mbar_try_wait(fullb + slot, round & 1u);
             ctx.tile_a = S.tiles + (size_t)slot * NSTATE * TS;
             ctx.tile_b = ctx.tile_a + TS;
+            ctx.torig = tile_origin(P, blockIdx.x + k * gridDim.x);
             runner.run(ctx);
             if (TMAW) {
                 // each thread has written its part of the tile and fenced it for

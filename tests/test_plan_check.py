@@ -101,3 +101,52 @@ def test_ansatz_plans_20_qubits(n, layers):
     26-qubit workload's kind (overlapping 8-qubit sets) appear."""
     circ = W.hea_ansatz(n, layers)
     check(circ, W.config_rng(5).angles(circ.n_params))
+
+
+def diagonal_heavy(seed, n, ng):
+    """Diagonal gates of every kind (RZ, PHASE, CPHASE, CZ, Z, S, T) on any
+    qubits, among RY and H: many diagonal gates land on qubits outside a
+    pass's set and are applied from the tile's index bits."""
+    rng = W.SplitMix64(seed)
+    gates, n_params = [], 0
+    for _ in range(ng):
+        r = rng.randint(0, 11)
+        a = rng.randint(0, n - 1)
+        b = (a + 1 + rng.randint(0, n - 2)) % n
+        if r <= 2:
+            gates.append(W.Gate("CPHASE", (a, b), param=n_params))
+            n_params += 1
+        elif r == 3:
+            gates.append(W.Gate("CZ", (a, b)))
+        elif r == 4:
+            gates.append(W.Gate("RZ", (a,), param=n_params))
+            n_params += 1
+        elif r == 5:
+            gates.append(W.Gate("PHASE", (a,), param=n_params))
+            n_params += 1
+        elif r == 6:
+            gates.append(W.Gate(("Z", "S", "T")[rng.randint(0, 2)], (a,)))
+        elif r == 7:
+            gates.append(W.Gate("CPHASE", (a, b), angle=rng.angle()))
+        elif r <= 9:
+            gates.append(W.Gate("RY", (a,), param=n_params))
+            n_params += 1
+        else:
+            gates.append(W.Gate("H", (a,)))
+    return W.Circuit(n, gates, n_params), rng.angles(max(1, n_params))
+
+
+@pytest.mark.parametrize("n,ng,seed", [(12, 200, 1), (16, 300, 2), (18, 400, 3), (20, 250, 4)])
+def test_diagonal_heavy_plans(n, ng, seed):
+    circ, params = diagonal_heavy(9400 + seed, n, ng)
+    check(circ, params, seed)
+
+
+@pytest.mark.parametrize("n", [16, 18, 20])
+def test_qft_passes(n):
+    """The QFT's controlled phases on qubits outside a pass's set are applied
+    from the tile's bits, so each pass takes the Hadamards of 8 new qubits
+    (Q = qubits 0..3 and 8 others): ceil((n - 4) / 8) + 1 passes, the last of
+    them the bit-reversal swaps."""
+    r = check(W.qft_circuit(n), np.zeros(1))
+    assert r["passes"] <= -(-(n - 4) // 8) + 2, r
