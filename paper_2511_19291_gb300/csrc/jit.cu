@@ -717,6 +717,7 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
         return TQD_ERR_UNSUPPORTED;
     }
     c->opts.mode = TQD_PLAN_FUSED;
+    relabel_swaps(c->gates, c->n);
     assign_grad_slots(c);
     int prefix = 0;
     std::vector<TilePlanPass> passes = plan_fused(c, &prefix);

@@ -46,6 +46,9 @@ std::vector<std::vector<int>> assign_grad_slots(tqd_circuit *c) {
 }
 
 tqd_status build_circuit(tqd_circuit *c) {
+    // fused plans keep the qubit order lazily: SWAPs relabel the gates after them
+    if ((c->opts.mode == TQD_PLAN_FUSED || c->opts.mode == TQD_PLAN_TC) && c->n >= TILE_K)
+        relabel_swaps(c->gates, c->n);
     const int ng = (int)c->gates.size();
     int dev = 0;
     cudaGetDevice(&dev);

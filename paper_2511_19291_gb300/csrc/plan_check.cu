@@ -34,8 +34,7 @@ struct Mat {
     int d;
 };
 
-Mat matrix_of(const tqd_circuit *c, int g, const double *params) {
-    const GateH &h = c->gates[g];
+Mat matrix_of_gate(const tqd_circuit *c, const GateH &h, const double *params) {
     double m[MAT_STRIDE];
     gate_matrix(h.kind, h.param >= 0 ? params[h.param] : h.fixed, c->table.data(), h.mat, m);
     Mat r;
@@ -44,6 +43,7 @@ Mat matrix_of(const tqd_circuit *c, int g, const double *params) {
         for (int j = 0; j < r.d; ++j) r.e[i][j] = cplx(m[2 * (i * r.d + j)], m[2 * (i * r.d + j) + 1]);
     return r;
 }
+Mat matrix_of(const tqd_circuit *c, int g, const double *params) { return matrix_of_gate(c, c->gates[g], params); }
 
 // v <- M v (or M^dagger v) on bit positions b0 (most significant) and b1.
 void apply_bits(std::vector<cplx> &v, const Mat &M, int b0, int b1, bool dag) {
@@ -210,6 +210,10 @@ bool run_pass(const tqd_circuit *c, const TilePlanPass &P, int dt, const double 
 tqd_status plan_check_host(tqd_circuit *c, const double *params, uint64_t seed, double *err_fwd, double *err_rev,
                            int *n_passes, int *n_stages) {
     c->opts.mode = TQD_PLAN_FUSED;
+    // the reference applies the gate list as given; the plan runs it with
+    // the qubit order kept lazily (SWAPs relabel the gates after them)
+    const std::vector<GateH> given = c->gates;
+    relabel_swaps(c->gates, c->n);
     assign_grad_slots(c);
     int prefix = 0;
     std::vector<TilePlanPass> passes = plan_fused(c, &prefix);
@@ -236,10 +240,7 @@ tqd_status plan_check_host(tqd_circuit *c, const double *params, uint64_t seed, 
     }
     for (auto &x : psi0) x /= sqrt(nrm);
     std::vector<cplx> ref = psi0;
-    for (size_t g = 0; g < c->gates.size(); ++g) {
-        const GateH &h = c->gates[g];
-        apply_bits(ref, matrix_of(c, (int)g, params), h.w[0], h.nw > 1 ? h.w[1] : 0, false);
-    }
+    for (const GateH &h : given) apply_bits(ref, matrix_of_gate(c, h, params), h.w[0], h.nw > 1 ? h.w[1] : 0, false);
     double ef = 0, er = 0;
     for (int dt = 0; dt < 2; ++dt) {
         std::vector<cplx> psi = psi0;

@@ -407,6 +407,52 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
     return passes;
 }
 
+// Lazy qubit order (the idea of Algorithm 2, MoveDim^-1 deferred: keep the
+// permutation pending instead of moving data).  pi[q] is the bit of the
+// stored index that holds qubit q.  A SWAP(a, b) exchanges pi[a] and pi[b]
+// and moves no amplitude; every other gate acts on the bits pi of its wires.
+// At the end the stored state is the true one with its index bits permuted
+// by pi; the SWAPs appended here put every qubit back on its own bit.  They
+// end the circuit, so they are its permutation tail: tqd_value_and_grad
+// conjugates the observable through them instead of running them, and a run
+// of the whole circuit moves the amplitudes once at the end.
+bool relabel_swaps(std::vector<GateH> &gates, int n) {
+    bool any = false;
+    for (const GateH &g : gates) any = any || g.kind == TQD_SWAP;
+    if (!any) return false;
+    std::vector<int> pi(n);
+    for (int q = 0; q < n; ++q) pi[q] = q;
+    std::vector<GateH> out;
+    out.reserve(gates.size() + n);
+    for (GateH g : gates) {
+        if (g.kind == TQD_SWAP) {
+            std::swap(pi[g.w[0]], pi[g.w[1]]);
+            continue;
+        }
+        for (int a = 0; a < g.nw; ++a) g.w[a] = pi[g.w[a]];
+        out.push_back(g);
+    }
+    for (int q = 0; q < n; ++q) {
+        if (pi[q] == q) continue;
+        int r = 0;  // the qubit held by bit q
+        while (pi[r] != q) ++r;
+        GateH s;
+        s.kind = TQD_SWAP;
+        s.nw = 2;
+        s.w[0] = q;
+        s.w[1] = pi[q];
+        s.w[2] = 0;
+        s.param = -1;
+        s.fixed = 0.0;
+        s.mat = -1;
+        out.push_back(s);
+        pi[r] = pi[q];
+        pi[q] = q;
+    }
+    gates.swap(out);
+    return true;
+}
+
 int permutation_tail(const tqd_circuit *c) {
     int t = (int)c->gates.size();
     while (t > 0 && is_perm_gate(c->gates[t - 1].kind)) --t;

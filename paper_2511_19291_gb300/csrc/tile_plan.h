@@ -14,6 +14,12 @@ bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L);
 // to the end).
 std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin = 0, int g_end = -1);
 
+// Lazy qubit order for the fused plans: every SWAP of the gate list becomes a
+// relabelling of the qubits of the gates after it, and the permutation left
+// at the end is appended as SWAP gates (part of the permutation tail).
+// Returns whether the list changed.
+bool relabel_swaps(std::vector<GateH> &gates, int n);
+
 // First gate of the circuit's permutation tail: the longest suffix of CNOT,
 // SWAP and X gates (gates.size() when the circuit does not end with one).
 int permutation_tail(const tqd_circuit *c);
