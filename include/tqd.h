@@ -355,15 +355,22 @@ tqd_status tqd_shots_gaussian_backward(tqd_state *state, double n_shots, const d
  * E_c = <H_c>, and the adjoint gradient of every E_c, all from one CUDA-graph
  * launch.  Circuits of complex64 width up to `small_max_qubits` run whole in
  * one block's shared memory (psi and lambda resident) from a persistent
- * work-queue kernel; wider circuits run their fused tile passes on
- * `streams` concurrent streams inside the same graph. */
+ * work-queue kernel.  Wider circuits run from a second persistent kernel:
+ * each circuit's stages (reset, its fused tile passes, lambda = H psi with
+ * E, its reverse passes, the closing sums) are split into work items of a
+ * few tiles; a device work queue hands items to the blocks, and the block
+ * that completes a stage queues the next one.  Wider circuits whose plan is
+ * not all complex64 tile passes (or a tensor-core block) run their passes on
+ * `streams` concurrent streams inside the same graph instead. */
 typedef struct tqd_batch tqd_batch;
 
 typedef struct {
     uint32_t small_max_qubits; /* 0 = default (13) or the autotuned value */
     uint32_t small_threads;    /* block size of the small-circuit kernel; 0 = default / autotuned */
     uint32_t streams;          /* concurrent streams for the wider circuits; 0 = default (16) */
-    uint32_t autotune;         /* non-zero: time the candidates once at creation and keep the best */
+    uint32_t autotune;         /* non-zero: time the candidates once at creation and keep the best
+                                  (the small kernel's block size, its width cutoff, then the tiles
+                                  per work item of the wider circuits, width by width) */
     uint32_t plain;            /* non-zero: every circuit gate by gate, one launch per gate (baseline) */
     uint32_t reserved[3];      /* must be zero */
 } tqd_batch_opts;
@@ -390,6 +397,12 @@ tqd_status tqd_batch_run(tqd_batch *batch, void *stream);
 
 tqd_status tqd_batch_info(const tqd_batch *batch, int *n_small, int *n_large, int *small_max_qubits,
                           int *small_threads, int *graph_nodes);
+
+/* Work items of the wider circuits of width `width` (0..26) on the
+ * persistent kernel: *tiles_per_item tiles of 2^12 amplitudes per item and
+ * *items_per_stage items per stage; both 0 when no circuit of that width runs
+ * there.  The paper has no counterpart: this reports the batch's schedule. */
+tqd_status tqd_batch_tiling(const tqd_batch *batch, int width, int *tiles_per_item, int *items_per_stage);
 
 tqd_status tqd_batch_free(tqd_batch *batch);
 

@@ -34,7 +34,8 @@ EXPORTS = (
     "tqd_apply_circuit",
     "tqd_expval", "tqd_expval_terms", "tqd_expval_noalloc", "tqd_apply_observable",
     "tqd_backward", "tqd_value_and_grad", "tqd_backward_seeded", "tqd_probabilities", "tqd_sample",
-    "tqd_shots_gaussian", "tqd_shots_gaussian_backward", "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info", "tqd_batch_free",
+    "tqd_shots_gaussian", "tqd_shots_gaussian_backward", "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info", "tqd_batch_tiling",
+    "tqd_batch_free",
     "tqd_profile_enable", "tqd_profile_read", "tqd_last_error", "tqd_version",
 )
 
@@ -130,6 +131,7 @@ def load(path: str | None = None):
         L.tqd_batch_run.argtypes = [vp, vp]
         L.tqd_batch_info.argtypes = [vp] + [C.POINTER(i32)] * 5
         L.tqd_batch_free.argtypes = [vp]
+        L.tqd_batch_tiling.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
         L.tqd_profile_enable.argtypes = [i32]
         L.tqd_profile_read.argtypes = [vp, i32, C.POINTER(i32)]
         for name in ("tqd_state_alloc", "tqd_state_reset", "tqd_state_free", "tqd_circuit_create",
@@ -139,6 +141,7 @@ def load(path: str | None = None):
                      "tqd_backward_seeded", "tqd_probabilities", "tqd_sample", "tqd_shots_gaussian",
                      "tqd_shots_gaussian_backward",
                      "tqd_batch_create", "tqd_batch_buffers", "tqd_batch_run", "tqd_batch_info",
+                     "tqd_batch_tiling",
                      "tqd_batch_free", "tqd_profile_enable", "tqd_jit_check", "tqd_plan_check",
                      "tqd_profile_read"):
             getattr(L, name).restype = st

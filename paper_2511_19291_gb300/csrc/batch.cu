@@ -22,6 +22,8 @@
 #include "launch.h"
 #include "plan.h"
 #include "prof.h"
+#include "tile_dev.cuh"
+#include "tile_plan.h"
 
 namespace tqd {
 
@@ -180,6 +182,153 @@ __global__ void k_batch_small(const SmallCirc *__restrict__ circs, int ncirc, co
     }
 }
 
+// ---------------------------------------------------------- wider circuits
+// The wider circuits run from one persistent kernel that pulls work items
+// from a queue in device memory.  A circuit goes through stages: reset psi,
+// its forward passes, lambda = H psi with E, its reverse passes, then a
+// closing step (E and the gradient summed).  Every stage but the last is
+// split into `chunks` items over the circuit's tiles (or amplitudes); the
+// block that finishes the last item of a stage pushes the items of the next
+// one, so a block only ever waits for the queue itself, and other circuits'
+// items fill the machine while a stage completes.  An item is processed by
+// one block of two groups of 256 threads on a ring of tile buffers (the
+// fused pass body of the single-circuit kernels, generic runner).
+struct WideCirc {
+    float2 *psi, *lam;          // its states
+    const float *mats;          // its per-gate matrices (complex64 scalars)
+    double *partials;           // [slot][pblk] gradient partials
+    const int *param_ptr;       // CSR: parameter -> gradient slots
+    const int *param_slots;
+    int *err;                   // its device error word
+    int n, n_params, pblk;
+    int passes, pass0;          // its passes: WidePass[pass0 .. pass0 + passes)
+    int chunks, tpc;            // items per stage, tiles per item
+    int term0, nterm;           // its observable (BTerm)
+    int poff, index;            // angle offset; position in the batch
+    int stage0;                 // its first stage counter
+    int e0;                     // its first energy partial
+};
+
+struct WidePass {
+    const TilePassDev *desc;    // complex64 descriptor
+    int map;                    // its psi tensor map (lambda's: map + 1)
+    int pad;
+};
+
+constexpr int WIDE_THREADS = 2 * TILE_THREADS;
+constexpr int WIDE_FWD_B = 6;   // forward ring: 6 buffers of 32 KiB
+constexpr int WIDE_REV_B = 3;   // reverse ring: 3 buffers of 64 KiB (psi and lambda)
+constexpr unsigned long long WIDE_VALID = 1ull << 63;
+
+__host__ __device__ inline unsigned long long wide_item(int circ, int stage, int chunk) {
+    return WIDE_VALID | ((unsigned long long)chunk << 40) | ((unsigned long long)stage << 20) | (unsigned)circ;
+}
+
+__global__ void __launch_bounds__(WIDE_THREADS, 1)
+    k_batch_wide(const WideCirc *__restrict__ circs, const WidePass *__restrict__ passes,
+                 const CUtensorMap *__restrict__ maps, const BTerm *__restrict__ terms,
+                 unsigned long long *queue, unsigned *qctl, int *done, int total, double *eparts,
+                 double *__restrict__ energies, double *__restrict__ grads, int *qerr) {
+    __shared__ unsigned long long s_item;
+    __shared__ double s_red[WIDE_THREADS / 32];
+    const uint32_t tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            // next position of the queue; its item may not be pushed yet
+            const unsigned pos = atomicAdd(qctl, 1u);
+            unsigned long long it = 0;
+            if (pos < (unsigned)total) {
+                volatile unsigned long long *q = queue + pos;
+                it = *q;
+                if (!(it & WIDE_VALID)) {
+                    const uint64_t t0 = gtimer_ns();
+                    while (!((it = *q) & WIDE_VALID))
+                        if (gtimer_ns() - t0 > WAIT_LIMIT_NS) {
+                            atomicExch(qerr, 1);
+                            it = 0;
+                            break;
+                        }
+                }
+                __threadfence();  // the item's data was written before it was pushed
+            }
+            s_item = it;
+        }
+        __syncthreads();
+        const unsigned long long it = s_item;
+        __syncthreads();
+        if (!(it & WIDE_VALID)) return;
+        // the tile copies below (async proxy) come after the acquire above
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const int ci = (int)(it & 0xFFFFF), stage = (int)((it >> 20) & 0xFFFFF), k = (int)((it >> 40) & 0xFFFFF);
+        const WideCirc &C = circs[ci];
+        const int P = C.passes;
+        const uint64_t A = (uint64_t)1 << C.n;
+        if (stage == 0) {
+            // psi = |0...0> over this item's share of the amplitudes
+            const uint64_t lo = A * k / C.chunks, hi = A * (k + 1) / C.chunks;
+            for (uint64_t b = lo + tid; b < hi; b += blockDim.x) C.psi[b] = make_float2(b == 0 ? 1.f : 0.f, 0.f);
+        } else if (stage <= P) {
+            const WidePass W = passes[C.pass0 + stage - 1];
+            tile_ring_tiles<float2, false, 2, WIDE_FWD_B, false, InterpRunner<float2, false>, true>(
+                maps + W.map, maps + W.map, W.desc, C.mats, nullptr, 0, C.err, 0, (uint64_t)k * C.tpc, 1, C.tpc, 0);
+        } else if (stage == P + 1) {
+            // lambda = H psi on this item's amplitudes, and its share of
+            // E = Re <psi|lambda> in FP64
+            const uint64_t lo = A * k / C.chunks, hi = A * (k + 1) / C.chunks;
+            double e = 0;
+            for (uint64_t b = lo + tid; b < hi; b += blockDim.x) {
+                float2 l = make_float2(0.f, 0.f);
+                for (int t = C.term0; t < C.term0 + C.nterm; ++t) {
+                    const BTerm T = terms[t];
+                    const uint64_t src = b ^ T.x;
+                    const float sg = (__popcll(src & T.z) & 1) ? -1.f : 1.f;
+                    l = cfma(make_float2(sg * (float)T.cre, sg * (float)T.cim), C.psi[src], l);
+                }
+                C.lam[b] = l;
+                e += (double)re_cdot(C.psi[b], l);
+            }
+            const double tot = block_sum(e, s_red);
+            if (tid == 0) eparts[C.e0 + k] = tot;
+        } else if (stage <= 2 * P + 1) {
+            const WidePass W = passes[C.pass0 + (2 * P + 1 - stage)];
+            tile_ring_tiles<float2, true, 2, WIDE_REV_B, false, InterpRunner<float2, true>, true>(
+                maps + W.map, maps + W.map + 1, W.desc, C.mats, C.partials, C.pblk, C.err, 0, (uint64_t)k * C.tpc, 1,
+                C.tpc, k);
+        } else {
+            // closing step: E and every parameter's derivative, summed in
+            // FP64 in a fixed order (items, then the parameter's slots)
+            if (tid == 0) {
+                double e = 0;
+                for (int j = 0; j < C.chunks; ++j) e += eparts[C.e0 + j];
+                energies[C.index] = e;
+            }
+            for (int p = tid; p < C.n_params; p += blockDim.x) {
+                double g = 0;
+                for (int j = C.param_ptr[p]; j < C.param_ptr[p + 1]; ++j) {
+                    const double *row = C.partials + (size_t)C.param_slots[j] * C.pblk;
+                    for (int q = 0; q < C.chunks; ++q) g += row[q];
+                }
+                grads[C.poff + p] += g;
+            }
+        }
+        // this item is done: the block that completes its stage pushes the
+        // next stage's items (after its own writes and, through the stage
+        // counter, everyone else's)
+        __syncthreads();
+        if (tid == 0 && stage < 2 * P + 2) {
+            __threadfence();
+            const int old = atomicAdd(done + C.stage0 + stage, 1);
+            if (old == C.chunks - 1) {
+                __threadfence();
+                const int ns = stage + 1;
+                const int cnt = ns == 2 * P + 2 ? 1 : C.chunks;
+                const unsigned pos = atomicAdd(qctl + 1, (unsigned)cnt);
+                for (int j = 0; j < cnt; ++j) atomicExch(queue + pos + j, wide_item(ci, ns, j));
+            }
+        }
+    }
+}
+
 }  // namespace tqd
 
 using namespace tqd;
@@ -207,6 +356,23 @@ struct tqd_batch {
     // wider circuits
     void *d_arena;
     std::vector<tqd_state *> st_psi, st_lam;
+    // ... on the persistent work-queue kernel (wide == true), else on streams
+    bool wide;
+    int tpc[27];                      // tiles per work item, by width
+    WideCirc *d_wcircs;
+    WidePass *d_wpasses;
+    CUtensorMap *d_wmaps;
+    BTerm *d_wterms;
+    GateDev *d_wgdev;
+    double *d_wtable, *d_wm64;
+    float *d_wm32;
+    int n_wgates;
+    unsigned long long *d_queue, *d_qinit;
+    unsigned *d_qctl, *d_qctl_init;
+    int *d_done, *d_qerr;
+    double *d_eparts;
+    int total_items, n_init, n_counters, wide_smem;
+    int tpc_used[27], items_used[27];  // the tiling each width got (0: none there)
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
     cudaGraph_t graph;
@@ -216,6 +382,36 @@ struct tqd_batch {
 };
 
 namespace {
+
+void free_wide(tqd_batch *b) {
+    cudaFree(b->d_wcircs);
+    cudaFree(b->d_wpasses);
+    cudaFree(b->d_wmaps);
+    cudaFree(b->d_wterms);
+    cudaFree(b->d_wgdev);
+    cudaFree(b->d_wtable);
+    cudaFree(b->d_wm64);
+    cudaFree(b->d_wm32);
+    cudaFree(b->d_queue);
+    cudaFree(b->d_qinit);
+    cudaFree(b->d_qctl);
+    cudaFree(b->d_qctl_init);
+    cudaFree(b->d_done);
+    cudaFree(b->d_qerr);
+    cudaFree(b->d_eparts);
+    b->d_wcircs = nullptr;
+    b->d_wpasses = nullptr;
+    b->d_wmaps = nullptr;
+    b->d_wterms = nullptr;
+    b->d_wgdev = nullptr;
+    b->d_wtable = b->d_wm64 = nullptr;
+    b->d_wm32 = nullptr;
+    b->d_queue = b->d_qinit = nullptr;
+    b->d_qctl = b->d_qctl_init = nullptr;
+    b->d_done = b->d_qerr = nullptr;
+    b->d_eparts = nullptr;
+    b->wide = false;
+}
 
 void free_batch_device(tqd_batch *b) {
     cudaFree(b->d_params);
@@ -234,6 +430,7 @@ void free_batch_device(tqd_batch *b) {
     b->st_psi.clear();
     b->st_lam.clear();
     cudaFree(b->d_arena);
+    free_wide(b);
     b->d_params = b->d_energies = b->d_grads = nullptr;
     b->d_small = nullptr;
     b->d_bgates = nullptr;
@@ -258,6 +455,152 @@ cudaError_t up(T **dst, const std::vector<T> &v) {
     cudaError_t e = cudaMalloc((void **)dst, v.size() * sizeof(T));
     if (e != cudaSuccess) return e;
     return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Tiles per work item of the wider circuits' stages, by default: at least 2
+// (one per group of the block), about 8 items per stage, at most 16 tiles.
+int default_tpc(int n) {
+    const int tiles = 1 << std::max(0, n - TILE_K);
+    return std::max(std::min(tiles, 2), std::min(16, tiles / 8));
+}
+
+// The persistent kernel's tables for the wider circuits: circuits, passes,
+// tensor maps, concatenated gate records (one matrix preparation launch for
+// all of them), observables, and the work queue.  Leaves b->wide false (the
+// circuits then run on streams) when a circuit has no fused plan of complex64
+// tile passes or a pass's ring does not fit in shared memory.
+cudaError_t build_wide(tqd_batch *b) {
+    free_wide(b);
+    if (b->large.empty()) return cudaSuccess;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    std::vector<WideCirc> wc;
+    std::vector<WidePass> wp;
+    std::vector<CUtensorMap> maps;
+    std::vector<BTerm> bt;
+    std::vector<GateDev> gd;
+    std::vector<double> table;
+    std::vector<int> goff;
+    int smem = 0, counters = 0, eparts = 0, total = 0;
+    for (int w = 0; w < 27; ++w) b->tpc_used[w] = b->items_used[w] = 0;
+    for (size_t i = 0; i < b->large.size(); ++i) {
+        const tqd_circuit *C = b->circuits[b->large[i]];
+        if (!C->fused || C->tile_passes.empty()) return cudaSuccess;
+        for (const auto &pp : C->tile_passes)
+            if (pp.tc >= 0) return cudaSuccess;
+        const int c = b->large[i];
+        WideCirc w;
+        memset(&w, 0, sizeof(w));
+        w.psi = (float2 *)b->st_psi[i]->amps;
+        w.lam = (float2 *)b->st_lam[i]->amps;
+        w.partials = C->d_partials;
+        w.param_ptr = C->d_param_ptr;
+        w.param_slots = C->d_param_slots;
+        w.err = C->d_err;
+        w.n = C->n;
+        w.n_params = C->n_params;
+        w.pblk = C->pblk;
+        w.passes = (int)C->tile_passes.size();
+        w.pass0 = (int)wp.size();
+        const int tiles = 1 << (C->n - TILE_K);
+        w.tpc = std::min(tiles, std::max(1, b->tpc[C->n] > 0 ? b->tpc[C->n] : default_tpc(C->n)));
+        w.chunks = std::min((tiles + w.tpc - 1) / w.tpc, std::max(1, C->pblk));
+        w.tpc = (tiles + w.chunks - 1) / w.chunks;
+        w.chunks = (tiles + w.tpc - 1) / w.tpc;
+        b->tpc_used[C->n] = w.tpc;
+        b->items_used[C->n] = w.chunks;
+        w.term0 = (int)bt.size();
+        w.poff = (int)b->poff[c];
+        w.index = c;
+        w.stage0 = counters;
+        w.e0 = eparts;
+        counters += 2 * w.passes + 2;
+        eparts += w.chunks;
+        total += w.chunks * (2 * w.passes + 2) + 1;
+        for (int p = 0; p < w.passes; ++p) {
+            const TilePlanPass &pp = C->tile_passes[p];
+            const TileHead &h = pp.dev[0].h;
+            smem = std::max<int>(smem, (int)tile_smem_ring<float2, false, WIDE_FWD_B>(h).total);
+            smem = std::max<int>(smem, (int)tile_smem_ring<float2, true, WIDE_REV_B>(h).total);
+            WidePass x;
+            x.desc = C->d_tile_desc + 2 * p;
+            x.map = (int)maps.size();
+            x.pad = 0;
+            wp.push_back(x);
+            CUtensorMap m[2];
+            cudaError_t e = tile_tensor_map(&m[0], w.psi, pp, 0);
+            if (e == cudaSuccess) e = tile_tensor_map(&m[1], w.lam, pp, 0);
+            if (e != cudaSuccess) return cudaSuccess;  // no tensor map: streams
+            maps.push_back(m[0]);
+            maps.push_back(m[1]);
+        }
+        int nt = 0;
+        for (const auto &grp : b->groups[c])
+            for (const auto &t : grp.terms) {
+                BTerm T;
+                T.x = grp.xmask;
+                T.z = t.zmask;
+                T.cre = t.pre * t.coeff;
+                T.cim = t.pim * t.coeff;
+                bt.push_back(T);
+                ++nt;
+            }
+        w.nterm = nt;
+        goff.push_back((int)gd.size());
+        const int toff = (int)table.size() / 2;
+        table.insert(table.end(), C->table.begin(), C->table.end());
+        for (const GateH &h : C->gates) {
+            GateDev d;
+            d.kind = h.kind;
+            d.param = h.param >= 0 ? (int)(h.param + b->poff[c]) : -1;
+            d.mat = h.mat >= 0 ? h.mat + toff : -1;
+            d.pad = 0;
+            d.fixed = h.fixed;
+            gd.push_back(d);
+        }
+        wc.push_back(w);
+    }
+    // the ring's static part (descriptor head, barriers, counters) comes on top
+    if (smem + 4096 > optin) return cudaSuccess;
+    cudaError_t e;
+    b->n_wgates = (int)gd.size();
+    if ((e = up(&b->d_wgdev, gd)) != cudaSuccess) return e;
+    if ((e = up(&b->d_wtable, table.empty() ? std::vector<double>(2, 0.0) : table)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&b->d_wm64, gd.size() * MAT_STRIDE * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&b->d_wm32, gd.size() * MAT_STRIDE * sizeof(float))) != cudaSuccess) return e;
+    for (size_t i = 0; i < wc.size(); ++i) wc[i].mats = b->d_wm32 + (size_t)goff[i] * MAT_STRIDE;
+    if ((e = up(&b->d_wcircs, wc)) != cudaSuccess) return e;
+    if ((e = up(&b->d_wpasses, wp)) != cudaSuccess) return e;
+    if ((e = up(&b->d_wmaps, maps)) != cudaSuccess) return e;
+    if ((e = up(&b->d_wterms, bt.empty() ? std::vector<BTerm>(1) : bt)) != cudaSuccess) return e;
+    // the first items: every circuit's reset, the costliest circuits first
+    std::vector<int> order(wc.size());
+    for (size_t i = 0; i < wc.size(); ++i) order[i] = (int)i;
+    auto cost = [&](int i) {
+        return (double)((uint64_t)1 << wc[i].n) * (double)b->circuits[b->large[i]]->gates.size();
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<unsigned long long> init;
+    for (int i : order)
+        for (int k = 0; k < wc[i].chunks; ++k) init.push_back(wide_item(i, 0, k));
+    if ((e = up(&b->d_qinit, init)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&b->d_queue, (size_t)total * sizeof(unsigned long long))) != cudaSuccess) return e;
+    const std::vector<unsigned> qctl = {0u, (unsigned)init.size()};
+    if ((e = up(&b->d_qctl_init, qctl)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&b->d_qctl, 2 * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&b->d_done, (size_t)counters * sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&b->d_eparts, (size_t)std::max(1, eparts) * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&b->d_qerr, sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMemset(b->d_qerr, 0, sizeof(int))) != cudaSuccess) return e;
+    b->total_items = total;
+    b->n_init = (int)init.size();
+    b->n_counters = counters;
+    b->wide_smem = smem + 1024;
+    if ((e = cudaFuncSetAttribute(k_batch_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, b->wide_smem)) !=
+        cudaSuccess)
+        return e;
+    b->wide = true;
+    return cudaSuccess;
 }
 
 // Split circuits into the small set and the wider set, build the
@@ -356,7 +699,7 @@ cudaError_t layout_batch(tqd_batch *b, int small_max) {
         b->st_psi.push_back(p);
         b->st_lam.push_back(l);
     }
-    return cudaSuccess;
+    return b->opts.plain ? cudaSuccess : build_wide(b);
 }
 
 // Everything one batch run does, enqueued on `s` (and the worker streams).
@@ -386,6 +729,33 @@ cudaError_t enqueue_batch(tqd_batch *b, cudaStream_t s) {
         k_batch_small<<<grid, threads, smem, s>>>(b->d_small, (int)b->small.size(), b->d_bgates, b->d_bm32,
                                                   b->d_bterms, b->d_energies, b->d_grads, b->d_counter);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // wider circuits: the persistent work-queue kernel
+    if (b->wide) {
+        ProfScope ps(PK_BATCH, 0.0, s);
+        const size_t qbytes = (size_t)b->total_items * sizeof(unsigned long long);
+        if ((e = cudaMemsetAsync(b->d_queue, 0, qbytes, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(b->d_queue, b->d_qinit, (size_t)b->n_init * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpyAsync(b->d_qctl, b->d_qctl_init, 2 * sizeof(unsigned), cudaMemcpyDeviceToDevice, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(b->d_done, 0, (size_t)b->n_counters * sizeof(int), s)) != cudaSuccess) return e;
+        if ((e = launch_prep_raw(b->d_wgdev, b->n_wgates, b->d_params, b->d_wtable, b->d_wm64, b->d_wm32, s)) !=
+            cudaSuccess)
+            return e;
+        k_batch_wide<<<device_sm_count(), WIDE_THREADS, b->wide_smem, s>>>(
+            b->d_wcircs, b->d_wpasses, b->d_wmaps, b->d_wterms, b->d_queue, b->d_qctl, b->d_done, b->total_items,
+            b->d_eparts, b->d_energies, b->d_grads, b->d_qerr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (nstreams > 0) {
+            for (int i = 0; i < nstreams; ++i) {
+                if ((e = cudaEventRecord(b->events[1 + i], b->streams[i])) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(s, b->events[1 + i], 0)) != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
     }
     // wider circuits round-robin over the worker streams
     for (size_t i = 0; i < b->large.size(); ++i) {
@@ -550,6 +920,27 @@ tqd_status tqd_batch_create(int n_circuits, const tqd_circuit *const *circuits, 
         if ((e = cudaMalloc((void **)&b->d_energies, n_circuits * sizeof(double))) != cudaSuccess) return fail(e);
         if ((e = cudaMalloc((void **)&b->d_counter, sizeof(int))) != cudaSuccess) return fail(e);
         if ((e = layout_batch(b, (int)best_q)) != cudaSuccess) return fail(e);
+        // the wider circuits' work items: tiles per item, width by width
+        if (b->wide) {
+            cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+            for (int w = TILE_K; w <= 26; ++w) {
+                if (!b->items_used[w]) continue;
+                const int tiles = 1 << (w - TILE_K);
+                int best_c = b->tpc_used[w];
+                best = 1e30;
+                for (int cand = 1; cand <= 32 && cand <= tiles; cand *= 2) {
+                    b->tpc[w] = cand;
+                    if ((e = build_wide(b)) != cudaSuccess) return fail(e);
+                    if (!b->wide) break;
+                    time_batch(b, ts);
+                    const double dt = time_batch(b, ts);
+                    if (dt < best) { best = dt; best_c = cand; }
+                }
+                b->tpc[w] = best_c;
+            }
+            if ((e = build_wide(b)) != cudaSuccess) return fail(e);
+            cudaStreamDestroy(ts);
+        }
     }
     *out = b;
     return TQD_OK;
@@ -629,6 +1020,17 @@ tqd_status tqd_batch_info(const tqd_batch *b, int *n_small, int *n_large, int *s
     if (small_max_qubits) *small_max_qubits = (int)b->opts.small_max_qubits;
     if (small_threads) *small_threads = (int)b->opts.small_threads;
     if (graph_nodes) *graph_nodes = b->graph_nodes;
+    return TQD_OK;
+}
+
+tqd_status tqd_batch_tiling(const tqd_batch *b, int width, int *tiles_per_item, int *items_per_stage) {
+    if (!b || width < 0 || width > 26) {
+        set_error("tqd_batch_tiling: NULL batch or width outside 0..26");
+        return TQD_ERR_INVALID_ARG;
+    }
+    const bool on = b->wide && b->items_used[width] > 0;
+    if (tiles_per_item) *tiles_per_item = on ? b->tpc_used[width] : 0;
+    if (items_per_stage) *items_per_stage = on ? b->items_used[width] : 0;
     return TQD_OK;
 }
 

@@ -52,7 +52,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static cudaError_t make_map(CUtensorMap *map, void *base, const TilePlanPass &pp, int dt) {
+cudaError_t tile_tensor_map(CUtensorMap *map, void *base, const TilePlanPass &pp, int dt) {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const TileLayout &L = pp.layout;
@@ -247,10 +247,10 @@ static cudaError_t launch_t(const void *psi_src, void *psi_dst, tqd_state *lam, 
     const int dt = sizeof(V) == 8 ? 0 : 1;
     const TilePlanPass &pp = c->tile_passes[pass];
     CUtensorMap ma, mb;
-    cudaError_t e = make_map(&ma, const_cast<void *>(psi_src), pp, dt);
+    cudaError_t e = tile_tensor_map(&ma, const_cast<void *>(psi_src), pp, dt);
     if (e != cudaSuccess) return e;
-    if (ADJ) e = make_map(&mb, lam->amps, pp, dt);
-    else if (psi_dst != psi_src) e = make_map(&mb, psi_dst, pp, dt);
+    if (ADJ) e = tile_tensor_map(&mb, lam->amps, pp, dt);
+    else if (psi_dst != psi_src) e = tile_tensor_map(&mb, psi_dst, pp, dt);
     else mb = ma;
     if (e != cudaSuccess) return e;
     const int tb = buffers_for<V, ADJ>(c, dt);

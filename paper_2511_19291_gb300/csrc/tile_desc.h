@@ -23,6 +23,7 @@ typedef short int16_t;
 typedef int int32_t;
 typedef unsigned int uint32_t;
 typedef unsigned long long uint64_t;
+typedef long long int64_t;
 #else
 #include <stdint.h>
 #endif

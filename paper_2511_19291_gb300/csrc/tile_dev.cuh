@@ -64,6 +64,9 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity
         : "memory");
     return ok;
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sptr(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(bar)) : "memory");
 }
@@ -1125,13 +1128,13 @@ __device__ __forceinline__ int mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 // summed in FP64, one warp per gradient op.  Ends the pass.  nw: the warps taking
 // part (the block's first nw).
 __device__ __forceinline__ void tile_write_partials(const TileHead &P, const TilePassDev *Pg, const double *gacc,
-                                                    int gcols, double *partials, int pblk, int nw) {
+                                                    int gcols, double *partials, int pblk, int nw, int pcol) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = warp; k < P.n_grad; k += nw) {
         double t = 0;
         for (int i = lane; i < gcols; i += 32) t += gacc[i * P.n_grad + k];
         t = warp_sum(t);
-        if (lane == 0) partials[(size_t)Pg->grad_gate_slot[k] * pblk + blockIdx.x] = t;
+        if (lane == 0) partials[(size_t)Pg->grad_gate_slot[k] * pblk + pcol] = t;
     }
 }
 
@@ -1241,7 +1244,7 @@ __device__ __forceinline__ void tile_pass_body(const void *map_psi, const void *
     if (ADJ) {
         __syncthreads();
         // the warps' FP64 columns, summed in FP64, one warp per gradient op
-        tile_write_partials(P, Pg, S.gacc, TILE_WARPS, partials, pblk, TILE_WARPS);
+        tile_write_partials(P, Pg, S.gacc, TILE_WARPS, partials, pblk, TILE_WARPS, blockIdx.x);
     }
 }
 
@@ -1275,11 +1278,18 @@ template <int N> __device__ __forceinline__ void reg_alloc() {
 // between groups when B is not a multiple of G: the waiter for tile k + B
 // first waits until tile k has been taken (gen[buffer] counts the tiles taken
 // from each buffer), so the barrier parity it waits on is never a phase stale.
-template <typename V, bool ADJ, int G, int B, bool TMAW, typename Runner>
-__device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
-                                               const RT<V> *mats, double *partials, int pblk, int *err,
-                                               int flags) {
+//
+// The tiles are tbase + k * tstride for k < count (count < 0: every tile of
+// the pass from tbase on), and the block's gradient partials go to column
+// pcol.  REUSE: the function is called again by the same block (a persistent
+// kernel); its barriers are invalidated at the end so that the next call
+// initialises them afresh, and every thread of the block takes part.
+template <typename V, bool ADJ, int G, int B, bool TMAW, typename Runner, bool REUSE = false>
+__device__ __forceinline__ void tile_ring_tiles(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
+                                                const RT<V> *mats, double *partials, int pblk, int *err, int flags,
+                                                uint64_t tbase, uint64_t tstride, int64_t count, int pcol) {
     static_assert(B >= G, "a ring needs a buffer per group");
+    static_assert(!(REUSE && TMAW), "a reused ring has no TMA warpgroup");
     static_assert(!TMAW || G == RingCfg<ADJ>::G, "the register shares are set for RingCfg's groups");
     __shared__ TileHead P;
     __shared__ uint64_t fullb[B];
@@ -1306,7 +1316,8 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     constexpr int TS = 1 << TILE_K;
     constexpr uint32_t NSTATE = ADJ ? 2u : 1u;
     const uint64_t n_tiles = (uint64_t)1 << P.n_tiles_log2;
-    const uint64_t n_local = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint64_t n_local = count >= 0 ? (uint64_t)count
+                                        : (n_tiles > tbase ? (n_tiles - 1 - tbase) / tstride + 1 : 0);
     const int grp = (int)(tid >> 8);  // G: the TMA warp
     const bool stall = (flags & TILE_STALL_TEST) && blockIdx.x == 0;
 
@@ -1322,7 +1333,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     if (!TMAW && tid == 0)
         for (int k = 0; k < B && (uint64_t)k < n_local; ++k)
             tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
-                                    blockIdx.x + (uint64_t)k * gridDim.x, stall && k == 0);
+                                    tbase + (uint64_t)k * tstride, stall && k == 0);
     if (TMAW && grp == G) {
         // the TMA warpgroup gives registers to the groups and leaves when its
         // copies are done (the groups write the gradient partials)
@@ -1338,7 +1349,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
         if ((tid & 31) == 0 && pw < (uint32_t)NP) {
             for (int k = (int)pw; k < B && (uint64_t)k < n_local; k += NP)
                 tile_issue_load<V, ADJ>(P, map_psi, map_lam, S.tiles + (size_t)k * NSTATE * TS, fullb + k,
-                                        blockIdx.x + (uint64_t)k * gridDim.x, stall && k == 0);
+                                        tbase + (uint64_t)k * tstride, stall && k == 0);
             uint64_t k = pw;
             for (; k < n_local; k += NP) {
                 const int slot = (int)(k % B);
@@ -1347,11 +1358,11 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
                     atomicExch(err, 1);
                     break;
                 }
-                const uint64_t tile = blockIdx.x + k * gridDim.x;
+                const uint64_t tile = tbase + k * tstride;
                 tile_issue_store<V, ADJ>(P, map_psi, map_lam, buf, tile, flags);
                 if (k + B < n_local) {
                     bulk_wait_read0();
-                    tile_issue_load<V, ADJ>(P, map_psi, map_lam, buf, fullb + slot, tile + (uint64_t)B * gridDim.x);
+                    tile_issue_load<V, ADJ>(P, map_psi, map_lam, buf, fullb + slot, tile + (uint64_t)B * tstride);
                 }
             }
             // the loads this thread issued and nobody took: tiles k .. k + B - 1
@@ -1421,7 +1432,7 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
             if (gtid != 0) mbar_try_wait(fullb + slot, round & 1u);
             ctx.tile_a = S.tiles + (size_t)slot * NSTATE * TS;
             ctx.tile_b = ctx.tile_a + TS;
-            ctx.torig = tile_origin(P, blockIdx.x + k * gridDim.x);
+            ctx.torig = tile_origin(P, tbase + k * tstride);
             runner.run(ctx);
             if (TMAW) {
                 // each thread has written its part of the tile and fenced it for
@@ -1432,12 +1443,12 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
             } else if (gtid == 0) {
                 // without a TMA warp the group's first thread stores the tile,
                 // waits until the store has read the buffer and refills it
-                const uint64_t tile = blockIdx.x + k * gridDim.x;
+                const uint64_t tile = tbase + k * tstride;
                 tile_issue_store<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, tile, flags);
                 if (k + B < n_local) {
                     bulk_wait_read0();
                     tile_issue_load<V, ADJ>(P, map_psi, map_lam, ctx.tile_a, fullb + slot,
-                                            tile + (uint64_t)B * gridDim.x);
+                                            tile + (uint64_t)B * tstride);
                 }
             }
             // the tile's last gradient values go to the warps' FP64 columns
@@ -1449,8 +1460,29 @@ __device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *
     if (ADJ) {
         // the groups only (the TMA warpgroup has left): named barrier 15
         asm volatile("bar.sync 15, %0;" ::"n"(G * TILE_THREADS) : "memory");
-        tile_write_partials(P, Pg, S.gacc, G * TILE_WARPS, partials, pblk, G * TILE_WARPS);
+        tile_write_partials(P, Pg, S.gacc, G * TILE_WARPS, partials, pblk, G * TILE_WARPS, pcol);
     }
+    if (REUSE) {
+        // every copy has landed or been waited out and every wait is over:
+        // the stores (async proxy) are ordered before what the caller does
+        // next, and the barriers go back to uninitialised for the next call
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncthreads();
+        if (tid == 0)
+            for (int i = 0; i < B; ++i) {
+                mbar_inval(fullb + i);
+                mbar_inval(doneb + i);
+            }
+        __syncthreads();
+    }
+}
+
+template <typename V, bool ADJ, int G, int B, bool TMAW, typename Runner>
+__device__ __forceinline__ void tile_pass_ring(const void *map_psi, const void *map_lam, const TilePassDev *Pg,
+                                               const RT<V> *mats, double *partials, int pblk, int *err,
+                                               int flags) {
+    tile_ring_tiles<V, ADJ, G, B, TMAW, Runner>(map_psi, map_lam, Pg, mats, partials, pblk, err, flags, blockIdx.x,
+                                                gridDim.x, -1, blockIdx.x);
 }
 
 }  // namespace tqd

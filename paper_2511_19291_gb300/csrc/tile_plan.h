@@ -1,6 +1,8 @@
 // tile_plan.h -- host-side plan of the fused tile passes (internal).
 #pragma once
 
+#include <cuda.h>
+
 #include <vector>
 
 #include "internal.h"
@@ -38,6 +40,8 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P);
 cudaError_t launch_tile_pass(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, int pass, cudaStream_t s,
                              const void *psi_src = nullptr, void *psi_dst = nullptr);
 int tile_grid(const tqd_circuit *c, int dtype, bool adj);
+// The TMA tensor map of pass pp over a state at `base` (dt 0: complex64).
+cudaError_t tile_tensor_map(CUtensorMap *map, void *base, const TilePlanPass &pp, int dt);
 
 // Host execution of circuit c's fused plan from its descriptors against the
 // gates applied one by one (tqd_plan_check).

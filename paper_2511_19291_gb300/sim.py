@@ -559,7 +559,16 @@ class Batch:
     def info(self) -> dict:
         v = [C.c_int() for _ in range(5)]
         _lib.check(_L().tqd_batch_info(self._h, *[C.byref(x) for x in v]))
-        return dict(zip(["small", "large", "small_max_qubits", "small_threads", "graph_nodes"], [x.value for x in v]))
+        out = dict(zip(["small", "large", "small_max_qubits", "small_threads", "graph_nodes"], [x.value for x in v]))
+        # the wider circuits' work items on the persistent kernel, by width
+        tiling = {}
+        for w in range(27):
+            t, k = C.c_int(), C.c_int()
+            _lib.check(_L().tqd_batch_tiling(self._h, w, C.byref(t), C.byref(k)))
+            if k.value:
+                tiling[w] = {"tiles_per_item": t.value, "items_per_stage": k.value}
+        out["tiling"] = tiling
+        return out
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -59,6 +59,24 @@ def test_batch_mixed_widths(small_max):
     b = S.Batch(circs, [t for _, _, t in items], small_max_qubits=small_max, streams=4)
     info = b.info()
     assert info["small"] + info["large"] == len(items)
+    # every wider circuit runs on the persistent work-queue kernel
+    wide = sorted({c.n_qubits for c, _, _ in items if c.n_qubits > info["small_max_qubits"]})
+    assert sorted(info["tiling"]) == wide, info
+    for w, t in info["tiling"].items():
+        tiles = 1 << (w - 12)
+        assert 1 <= t["tiles_per_item"] <= tiles and t["items_per_stage"] * t["tiles_per_item"] >= tiles
+    check_batch(items, b)
+
+
+def test_batch_wide_fallback_to_streams():
+    """A wider circuit without a fused plan (here a gate-by-gate one) sends
+    the batch's wider circuits back to their per-pass launches on streams:
+    same results, no persistent-kernel tiling."""
+    S = sim()
+    items = ragged(92, 8, 12, 15, 1, 2)  # widths 14, 12, 14, 13, 15, 13, 15, 14
+    circs = [S.Circuit(c, mode="plain" if k == 0 else "fused") for k, (c, _, _) in enumerate(items)]
+    b = S.Batch(circs, [t for _, _, t in items], small_max_qubits=11, streams=4)
+    assert b.info()["tiling"] == {}
     check_batch(items, b)
 
 
@@ -78,6 +96,8 @@ def test_batch_autotune():
     b = S.Batch(circs, [t for _, _, t in items], autotune=True, streams=4)
     info = b.info()
     assert info["small_threads"] in (128, 256, 512) and info["small_max_qubits"] in (11, 12, 13)
+    for w, t in info["tiling"].items():
+        assert t["tiles_per_item"] in (1, 2, 4)  # 2^(w - 12) tiles for w <= 14
     check_batch(items, b)
 
 
