@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=512, help="circuits of the batched measurement (0 = skip)")
     ap.add_argument("--tc-gates", type=int, default=200, help="gates of the tensor-core block measurement (0 = skip)")
     ap.add_argument("--qft-n", type=int, default=32, help="qubits of the QFT + ansatz measurement (0 = skip)")
+    ap.add_argument("--forward-expval", type=int, default=1, choices=[0, 1],
+                    help="time the workload's forward evaluation with E = <H> alone, fused and gate by gate (0 = skip)")
     ap.add_argument("--grad-fn", type=int, default=1, choices=[0, 1],
                     help="time the 24-qubit workload's gradient through the autograd.Function (0 = skip)")
     return ap.parse_args()
@@ -446,6 +448,54 @@ def grad_fn_bench(S, torch, dev, barrier, reps=10):
 
 
 # ------------------------------------------------ tensor-core block measurement
+def forward_expval_bench(S, torch, dev, w, barrier, reps=5):
+    """Forward evaluation of the workload without a gradient (reset, the
+    circuit, E = <H> by tqd_expval): time per evaluation for the fused plan
+    and the gate-by-gate one, and the expectation kernels' own time and
+    bandwidth (the bytes they read: psi once per 12-qubit set of x masks)."""
+    n = w.circuit.n_qubits
+    obs = S.Observable(w.terms)
+    params = torch.tensor(w.params, dtype=torch.float64, device=dev)
+    st = S.State(n, torch.complex64, dev)
+    out = {"workload": w.name, "observable_terms": len(w.terms)}
+    peak, src = peaks()
+    for mode in ("fused", "plain"):
+        c = S.Circuit(w.circuit, mode=mode, device=dev)
+        k = reps if mode == "fused" else 1
+        e = torch.zeros((), dtype=torch.float64, device=dev)
+
+        def one():
+            st.reset(0)
+            S.apply(st, c, params)
+            S.expval(st, obs, out=e)
+
+        one()
+        barrier()
+        S.profile_enable(True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k):
+            one()
+        b.record()
+        torch.cuda.synchronize(dev)
+        prof = {p["name"]: p for p in S.profile_read()}
+        S.profile_enable(False)
+        r = {"ms_per_eval": a.elapsed_time(b) / k, "energy": float(e.item())}
+        if mode == "fused" and "expval" in prof:
+            p = prof["expval"]
+            ms = p["ms"] / k
+            r["expval"] = {"ms_per_eval": ms, "launches_per_eval": p["launches"] // k,
+                           "gbs": p["bytes"] / (p["ms"] / 1000.0) / 1e9,
+                           "frac": p["bytes"] / (p["ms"] / 1000.0) / 1e9 / peak, "peak_source": f"{src} hbm_gbs"}
+        out[mode] = r
+        del c
+    out["fused_over_plain"] = out["plain"]["ms_per_eval"] / out["fused"]["ms_per_eval"]
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
 def tc_bench(S, torch, dev, n, n_gates, barrier, reps=5):
     """One run of `n_gates` gates on qubits 0..5 of an n-qubit complex64 state:
     the fused 64 x 64 block on the tensor cores against the same gates in one
@@ -675,6 +725,8 @@ def main():
 
     grad_fn = grad_fn_bench(S, torch, dev, barrier) if args.grad_fn else None
 
+    fwd_e = forward_expval_bench(S, torch, dev, w, barrier) if args.forward_expval else None
+
     qft = None
     if args.qft_n > 0:
         del psi, lam
@@ -745,6 +797,7 @@ def main():
         "batched": batched,
         "tc_block": tcb,
         "grad24": grad_fn,
+        "forward_expval": fwd_e,
         "qft32": qft,
         "clocks": clk.summary(),
         "kernels": kernels,

@@ -172,8 +172,10 @@ tqd_status tqd_circuit_free(tqd_circuit *circuit);
  * tqd_plan_opts.jit) and compiles the distinct ones with NVRTC for compute
  * capability `arch` (103 for sm_103a).  *n_kernels receives their number.
  * TQD_ERR_UNSUPPORTED when NVRTC cannot be loaded; TQD_ERR_CUDA when a kernel
- * fails to compile (tqd_last_error holds the start of the compiler log).  The
- * paper has no counterpart: this checks code the library writes at run time. */
+ * fails to compile (tqd_last_error holds the start of the compiler log).  With
+ * the environment variable TQD_JIT_DUMP_DIR set to a directory, every distinct
+ * generated source is also written there (pass_<i>.cu).  The paper has no
+ * counterpart: this checks code the library writes at run time. */
 tqd_status tqd_jit_check(int n_qubits, const tqd_gate *gates, size_t n_gates, int n_params,
                          const double *matrices, size_t n_matrix_entries, int arch, int *n_kernels);
 

@@ -742,6 +742,13 @@ tqd_status jit_check_host(tqd_circuit *c, int arch, int *n_kernels) {
                             }
                         }
     }
+    // TQD_JIT_DUMP_DIR: write every distinct generated source there (pass_<i>.cu)
+    if (const char *dir = getenv("TQD_JIT_DUMP_DIR")) {
+        for (size_t i = 0; i < srcs.size(); ++i) {
+            std::ofstream f(std::string(dir) + "/pass_" + std::to_string(i) + ".cu");
+            f << srcs[i];
+        }
+    }
     std::vector<std::string> logs(srcs.size());
     std::vector<char> ok(srcs.size(), 0);
     const int nt = std::max(1, std::min<int>((int)srcs.size(), (int)std::thread::hardware_concurrency()));

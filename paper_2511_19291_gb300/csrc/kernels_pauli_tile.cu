@@ -382,9 +382,11 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
             const bool real = (S.D.real_groups >> g) & 1u;
             const bool any_zr = zf[16] > zf[1];
             // u_r = conj(psi_{l ^ x}) psi_l, l = r * 256 + tid; the partner
-            // sits at register index r ^ xr of thread tid ^ xt
+            // sits at register index r ^ xr of thread tid ^ xt (this
+            // thread's own registers when xt = 0)
             const float2 *pt = tile + (tid ^ (xl & 0xFFu));
             const uint32_t xr = xl >> 8;
+            const bool own = (xl & 0xFFu) == 0;
             if (!any_zr) {
                 // every term's factor is constant over r: one sum of u
                 float sr, si = 0.f;
@@ -395,6 +397,18 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
                 if (xl == 0) {
 #pragma unroll
                     for (int r = 0; r < PPER; ++r) s2[r & 3] = f2_fma(a[r], a[r], s2[r & 3]);
+                } else if (real && own && (xr == 1 || xr == 2 || xr == 4 || xr == 8)) {
+                    // partner in the same thread: each pair once, doubled
+                    with_xr(xr, [&](auto XR_) {
+                        constexpr int XR = decltype(XR_)::value;
+                        if constexpr (XR > 0) {
+#pragma unroll
+                            for (int r = 0; r < PPER; ++r)
+                                if (!(r & XR)) s2[r & 3] = f2_fma(a[r ^ XR], a[r], s2[r & 3]);
+                        }
+                    });
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) s2[q] = make_float2(2.f * s2[q].x, 2.f * s2[q].y);
                 } else if (real) {
                     with_xr(xr, [&](auto XR_) {
                         constexpr int XR = decltype(XR_)::value;
