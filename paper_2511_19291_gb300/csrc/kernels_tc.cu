@@ -8,8 +8,9 @@
 //     U~[2r][2c] = Re U_rc   U~[2r][2c+1] = -Im U_rc
 //     U~[2r+1][2c] = Im U_rc U~[2r+1][2c+1] = Re U_rc.
 // tcgen05.mma (kind::tf32, M = 128, N = 64, K = 8 per instruction) takes U~
-// and a tile of 64 state columns from shared memory (K-major, 128-byte
-// swizzle, loaded by TMA) and accumulates in TMEM.  TF32 keeps 10 mantissa
+// from tensor memory (written there once per block) and a tile of 64 state
+// columns from shared memory (K-major, 128-byte swizzle, loaded by TMA) and
+// accumulates in TMEM.  TF32 keeps 10 mantissa
 // bits, so both operands are split, a = a_hi + a_lo, and three products
 // a_hi b_hi + a_hi b_lo + a_lo b_hi are accumulated in FP32 (split
 // precision, about 21 bits per product).
@@ -25,21 +26,18 @@
 
 namespace tqd {
 
-constexpr int TC_K = 128;                  // floats per column (64 complex amplitudes)
-constexpr int TC_N = 64;                   // columns per tile
-constexpr int TC_KB = TC_K / 32;           // 128-byte K blocks
-constexpr int TC_A_BYTES = 128 * TC_K * 4; // 64 KiB
+constexpr int TC_K = 128;                    // floats per column (64 complex amplitudes)
+constexpr int TC_N = 64;                     // columns per tile
+constexpr int TC_KB = TC_K / 32;             // 128-byte K blocks
 constexpr int TC_B_BYTES = TC_N * TC_K * 4;  // 32 KiB
 constexpr int TC_THREADS = 256;
-
-// Byte offset of element (row, k) of a K-major operand with `rows` rows:
-// K blocks of 128 bytes, 8-row swizzle atoms of 1024 bytes, 16-byte chunk
-// index XORed with the row inside the atom.
-__host__ __device__ inline uint32_t tc_off(int row, int k, int rows) {
-    const int kb = k >> 5, kk = k & 31;
-    const int chunk = kk >> 2, within = (kk & 3) * 4;
-    return (uint32_t)(kb * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4) + within);
-}
+constexpr int TC_NB = 4;                     // state tile buffers (loads in flight)
+constexpr int TC_NLO = 2;                    // lo-half buffers
+// Tensor memory: the operand U~ as TF32 hi and lo halves (128 lanes = rows,
+// one 32-bit column per K element), then two 64-column accumulators.
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr uint32_t TC_A_HI = 0, TC_A_LO = 128, TC_ACC = 256;
+constexpr int TC_SMEM = (TC_NB + TC_NLO) * TC_B_BYTES + 1024 + 128;
 
 __device__ __forceinline__ uint32_t tc_sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -47,7 +45,8 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__flo
 
 // ------------------------------------------------------------- block prep
 // One block: thread c builds column c of U by applying the block's gates to
-// e_c in FP64, then writes U~ as TF32 hi / lo halves in the operand layout.
+// e_c in FP64, then writes U~ row-major (row m, column k at m * 128 + k) as
+// TF32 hi / lo halves.
 __global__ void k_tc_prep(const TcGate *__restrict__ gates, int ng, const double *__restrict__ mats64,
                           float *__restrict__ a_hi, float *__restrict__ a_lo) {
     extern __shared__ double2 col[];  // [64 amplitudes][64 columns]: thread c owns column c
@@ -84,7 +83,7 @@ __global__ void k_tc_prep(const TcGate *__restrict__ gates, int ng, const double
             }
         }
     }
-    // U[r][c] = v[r]; write the four real entries of each complex entry
+    // U[r][c] = v[r]; the four real entries of each complex entry
     for (int r = 0; r < 64; ++r) {
         const double re = V(r).x, im = V(r).y;
         const double e[4] = {re, -im, im, re};  // (2r,2c) (2r,2c+1) (2r+1,2c) (2r+1,2c+1)
@@ -93,9 +92,8 @@ __global__ void k_tc_prep(const TcGate *__restrict__ gates, int ng, const double
         for (int q = 0; q < 4; ++q) {
             const float hi = tf32_hi((float)e[q]);
             const float lo = (float)(e[q] - (double)hi);
-            const uint32_t o = tc_off(rows[q], ks[q], 128) / 4;
-            a_hi[o] = hi;
-            a_lo[o] = lo;
+            a_hi[rows[q] * TC_K + ks[q]] = hi;
+            a_lo[rows[q] * TC_K + ks[q]] = lo;
         }
     }
 #undef V
@@ -129,59 +127,78 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
-// Pipelined over the block's tiles (one block per SM): two TMA buffers for
-// the state tiles and two TMEM accumulators.  Iteration i: wait for tile i,
-// split it (lo half into Blo), issue tile i's 48 MMAs into accumulator i % 2,
-// write tile i - 1's result from the other accumulator to HBM while they
-// run, wait for them, then refill tile i's buffer with tile i + 2.  So the
-// MMAs of one tile overlap the previous tile's epilogue and the loads of the
-// next two tiles.
+// One block per SM over its tiles (blockIdx.x + k * gridDim.x).  U~ (hi and
+// lo) sits in tensor memory for the whole kernel, which leaves the shared
+// memory to four state-tile buffers and two lo-half buffers.  Iteration k:
+// wait for tile k, split its lo half (lo buffer k % 2, free since tile
+// k - 2's MMAs completed), issue its 48 MMAs into accumulator k % 2, then
+// wait for tile k - 1's MMAs, write its result to HBM from the other
+// accumulator and refill its buffer with tile k + 3.  So tile k's MMAs run
+// while tile k - 1 leaves and tile k + 1 is split, with three tiles loading.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_apply(const __grid_constant__ CUtensorMap map, float *__restrict__ state, const float *__restrict__ a_hi,
                const float *__restrict__ a_lo, uint64_t n_tiles, int *__restrict__ err) {
     extern __shared__ unsigned char tc_raw[];
     const uint32_t pad = (1024u - (tc_sptr(tc_raw) & 1023u)) & 1023u;
     unsigned char *sm = tc_raw + pad;
-    float *Ahi = reinterpret_cast<float *>(sm);
-    float *Alo = reinterpret_cast<float *>(sm + TC_A_BYTES);
-    float *Bbuf = reinterpret_cast<float *>(sm + 2 * TC_A_BYTES);                  // 2 tiles
-    float *Blo = reinterpret_cast<float *>(sm + 2 * TC_A_BYTES + 2 * TC_B_BYTES);  // 1 tile
-    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + 2 * TC_A_BYTES + 3 * TC_B_BYTES);  // [2]
-    uint64_t *bar_mma = bar_ld + 2;
-    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_ld + 3);
+    float *Bbuf = reinterpret_cast<float *>(sm);                          // TC_NB tiles
+    float *Blo = reinterpret_cast<float *>(sm + TC_NB * TC_B_BYTES);      // TC_NLO tiles
+    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + (TC_NB + TC_NLO) * TC_B_BYTES);  // [TC_NB]
+    uint64_t *bar_mma = bar_ld + TC_NB;                                   // [2]
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_mma + 2);
+    __shared__ int s_ok[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    {
-        const uint4 *s0 = reinterpret_cast<const uint4 *>(a_hi), *s1 = reinterpret_cast<const uint4 *>(a_lo);
-        uint4 *d0 = reinterpret_cast<uint4 *>(Ahi), *d1 = reinterpret_cast<uint4 *>(Alo);
-        for (int i = tid; i < TC_A_BYTES / 16; i += TC_THREADS) {
-            d0[i] = s0[i];
-            d1[i] = s1[i];
-        }
-    }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_ld)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_ld + 1)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_mma)));
+        for (int i = 0; i < TC_NB; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_ld + i)));
+        for (int i = 0; i < 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_mma + i)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_sptr(slot)),
-                     "r"(2 * TC_N));
+                     "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *slot;
+    // U~ into tensor memory: warp w writes rows 32 (w % 4) .. + 31 (its lane
+    // quarter) of the hi half (w < 4) or the lo half, 32 columns at a time
+    {
+        const int q = warp & 3, h = warp >> 2;
+        const float4 *src = reinterpret_cast<const float4 *>((h ? a_lo : a_hi) + (size_t)(32 * q + lane) * TC_K);
+        for (int c = 0; c < TC_K / 32; ++c) {
+            uint32_t r[32];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 v = src[c * 8 + j];
+                r[4 * j] = __float_as_uint(v.x);
+                r[4 * j + 1] = __float_as_uint(v.y);
+                r[4 * j + 2] = __float_as_uint(v.z);
+                r[4 * j + 3] = __float_as_uint(v.w);
+            }
+            const uint32_t ta = taddr + ((uint32_t)(32 * q) << 16) + (h ? TC_A_LO : TC_A_HI) + 32u * c;
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(ta),
+                "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+                "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+                "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+                "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+                : "memory");
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
     // instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    // this block's tiles: blockIdx.x + k * gridDim.x, k < n_local
     const uint64_t n_local = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     auto issue_load = [&](uint64_t k) {
-        const int b = (int)(k & 1);
+        const int b = (int)(k % TC_NB);
         const uint64_t tile = blockIdx.x + k * gridDim.x;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_sptr(bar_ld + b)),
                      "r"((uint32_t)TC_B_BYTES)
@@ -197,44 +214,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     };
     // result of tile k (accumulator k % 2) to HBM: warp w reads TMEM lanes
-    // 32 (w % 4) .. 32 (w % 4) + 31 (floats of a column) of columns
-    // 32 (w / 4) .. 32 (w / 4) + 31
+    // 32 (w % 4) .. + 31 (floats of a column) of columns 32 (w / 4) .. + 31
     auto epilogue = [&](uint64_t k) {
         const uint64_t tile = blockIdx.x + k * gridDim.x;
         float *out = state + tile * TC_N * TC_K;
-        const uint32_t tcol = taddr + (uint32_t)(k & 1) * TC_N;
-        const int q = warp & 3;
-        {
-            const int c = warp >> 2;
-            uint32_t r[32];
-            const uint32_t ta = tcol + ((uint32_t)(q * 32) << 16) + c * 32;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const uint32_t tcol = taddr + TC_ACC + (uint32_t)(k & 1) * TC_N;
+        const int q = warp & 3, c = warp >> 2;
+        uint32_t r[32];
+        const uint32_t ta = tcol + ((uint32_t)(q * 32) << 16) + c * 32;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) out[(c * 32 + j) * TC_K + q * 32 + lane] = __uint_as_float(r[j]);
-        }
+        for (int j = 0; j < 32; ++j) out[(c * 32 + j) * TC_K + q * 32 + lane] = __uint_as_float(r[j]);
     };
-
-    if (tid == 0) {
-        if (n_local > 0) issue_load(0);
-        if (n_local > 1) issue_load(1);
-    }
-    uint32_t ph_ld = 0, ph_mma = 0;  // bit b: phase parity of load barrier b
-    bool failed = false;
     // Thread 0 waits (bounded) and the block learns the outcome at the
     // barrier, so every thread takes the same branch; the others then acquire
-    // the completed phase themselves.
-    // (one flag per barrier kind: a flag is rewritten only after two more
-    // block barriers, so every thread has read it by then)
-    __shared__ int s_ok[2];
+    // the completed phase themselves.  One flag per barrier kind, rewritten
+    // only after two more block barriers.
     auto wait_all = [&](uint64_t *bar, uint32_t parity, int which) -> bool {
         if (tid == 0) s_ok[which] = tc_wait(bar, parity) ? 1 : 0;
         __syncthreads();
@@ -242,20 +246,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (ok && tid != 0) tc_wait(bar, parity);
         return ok;
     };
+
+    uint64_t loads = 0;  // tiles whose load was issued (tile j is in buffer j % TC_NB)
+    if (tid == 0)
+        for (; loads < (uint64_t)TC_NB && loads < n_local; ++loads) issue_load(loads);
+    uint64_t mmas = 0, mmas_done = 0;  // tiles whose MMAs were issued / completed and waited
+    bool failed = false;
     for (uint64_t k = 0; k < n_local; ++k) {
-        const int b = (int)(k & 1);
+        const int b = (int)(k % TC_NB), l = (int)(k % TC_NLO), d = (int)(k & 1);
         const float *B = Bbuf + b * (TC_B_BYTES / 4);
-        if (!wait_all(bar_ld + b, (ph_ld >> b) & 1u, 0)) {
+        float *L = Blo + l * (TC_B_BYTES / 4);
+        if (!wait_all(bar_ld + b, (uint32_t)(k / TC_NB) & 1u, 0)) {
             failed = true;
             break;
         }
-        ph_ld ^= 1u << b;
-        // lo half of the state tile (same positions as B, 16 bytes at a
-        // time); Blo is free: the previous tile's MMAs completed before the
-        // last iteration ended
+        // lo half of the state tile (same positions as B, 16 bytes at a time)
         for (int i = tid; i < TC_B_BYTES / 16; i += TC_THREADS) {
             const float4 x = reinterpret_cast<const float4 *>(B)[i];
-            reinterpret_cast<float4 *>(Blo)[i] =
+            reinterpret_cast<float4 *>(L)[i] =
                 make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z), x.w - tf32_hi(x.w));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -263,44 +271,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (tid == 0) {
-            const uint32_t dcol = taddr + (uint32_t)b * TC_N;
-            // operand descriptors: the start-address field (bits 0..13, in
-            // 16-byte units) of each K step is the base plus a constant
-            const uint64_t dahi = tc_desc(tc_sptr(Ahi)), dalo = tc_desc(tc_sptr(Alo));
-            const uint64_t dbhi = tc_desc(tc_sptr(B)), dblo = tc_desc(tc_sptr(Blo));
+            const uint32_t dcol = taddr + TC_ACC + (uint32_t)d * TC_N;
+            const uint64_t dbhi = tc_desc(tc_sptr(B)), dblo = tc_desc(tc_sptr(L));
 #pragma unroll
             for (int p = 0; p < 3; ++p) {  // hi*hi, hi*lo, lo*hi
-                const uint64_t da = p == 2 ? dalo : dahi;
+                const uint32_t acol = taddr + (p == 2 ? TC_A_LO : TC_A_HI);
                 const uint64_t db = p == 1 ? dblo : dbhi;
 #pragma unroll
                 for (int s = 0; s < TC_K / 8; ++s) {
-                    const uint64_t ad = da + (uint64_t)(((s >> 2) * 128 * 128 + (s & 3) * 32) >> 4);
+                    const uint32_t a = acol + 8u * s;
                     const uint64_t bd = db + (uint64_t)(((s >> 2) * TC_N * 128 + (s & 3) * 32) >> 4);
                     const uint32_t acc = (p | s) != 0;
                     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}" ::"r"(dcol),
-                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n}" ::"r"(dcol),
+                                 "r"(a), "l"(bd), "r"(idesc), "r"(acc));
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                tc_sptr(bar_mma)));
+                tc_sptr(bar_mma + d)));
         }
-        // the previous tile's result leaves while these MMAs run
-        if (k > 0) epilogue(k - 1);
-        if (!wait_all(bar_mma, ph_mma, 1)) {
-            failed = true;
-            break;
+        mmas = k + 1;
+        if (k > 0) {
+            // tile k - 1: its MMAs, its result, its buffer refilled with tile k + 3
+            if (!wait_all(bar_mma + ((k - 1) & 1), (uint32_t)((k - 1) >> 1) & 1u, 1)) {
+                failed = true;
+                break;
+            }
+            mmas_done = k;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            epilogue(k - 1);
+            if (tid == 0 && loads < n_local) issue_load(loads++);
         }
-        ph_mma ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // tile k's buffer (read by the MMAs just completed) takes tile k + 2
-        if (tid == 0 && k + 2 < n_local) issue_load(k + 2);
     }
-    if (!failed && n_local > 0) epilogue(n_local - 1);
-    if (failed && tid == 0) atomicExch(err, 1);
+    if (!failed && n_local > 0) {
+        if (wait_all(bar_mma + ((n_local - 1) & 1), (uint32_t)((n_local - 1) >> 1) & 1u, 1)) {
+            mmas_done = n_local;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            epilogue(n_local - 1);
+        } else {
+            failed = true;
+        }
+    }
+    if (failed && tid == 0) {
+        atomicExch(err, 1);
+        // before the tensor memory and the buffers go: the MMAs issued and
+        // the copies in flight end (or their waits run out too)
+        for (uint64_t j = mmas_done; j < mmas; ++j) tc_wait(bar_mma + (j & 1), (uint32_t)(j >> 1) & 1u);
+        for (uint64_t j = mmas; j < loads; ++j) tc_wait(bar_ld + (j % TC_NB), (uint32_t)(j / TC_NB) & 1u);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * TC_N));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS));
 }
 
 // ------------------------------------------------------------------- host
@@ -342,7 +363,7 @@ cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock 
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const int smem = 2 * TC_A_BYTES + 3 * TC_B_BYTES + 1024 + 64;
+    const int smem = TC_SMEM;
     static std::once_flag once;
     std::call_once(once, [&] { cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); });
     const uint64_t tiles = cols / TC_N;
