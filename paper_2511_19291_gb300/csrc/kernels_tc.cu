@@ -30,14 +30,13 @@ constexpr int TC_K = 128;                    // floats per column (64 complex am
 constexpr int TC_N = 64;                     // columns per tile
 constexpr int TC_KB = TC_K / 32;             // 128-byte K blocks
 constexpr int TC_B_BYTES = TC_N * TC_K * 4;  // 32 KiB
-constexpr int TC_THREADS = 256;
 constexpr int TC_NB = 4;                     // state tile buffers (loads in flight)
 constexpr int TC_NLO = 2;                    // lo-half buffers
 // Tensor memory: the operand U~ as TF32 hi and lo halves (128 lanes = rows,
 // one 32-bit column per K element), then two 64-column accumulators.
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint32_t TC_A_HI = 0, TC_A_LO = 128, TC_ACC = 256;
-constexpr int TC_SMEM = (TC_NB + TC_NLO) * TC_B_BYTES + 1024 + 128;
+constexpr int TC_SMEM = (TC_NB + TC_NLO) * TC_B_BYTES + 1024 + 256;
 
 __device__ __forceinline__ uint32_t tc_sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -127,14 +126,43 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     }
 }
 
+// Warp-uniform bounded wait: lane 0 waits, the warp learns the outcome.
+__device__ __forceinline__ bool tc_wait_warp(uint64_t *bar, uint32_t parity) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = tc_wait(bar, parity) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok && (threadIdx.x & 31) != 0) tc_wait(bar, parity);  // acquire the completed phase
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tc_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_sptr(bar)) : "memory");
+}
+
 // One block per SM over its tiles (blockIdx.x + k * gridDim.x).  U~ (hi and
 // lo) sits in tensor memory for the whole kernel, which leaves the shared
-// memory to four state-tile buffers and two lo-half buffers.  Iteration k:
-// wait for tile k, split its lo half (lo buffer k % 2, free since tile
-// k - 2's MMAs completed), issue its 48 MMAs into accumulator k % 2, then
-// wait for tile k - 1's MMAs, write its result to HBM from the other
-// accumulator and refill its buffer with tile k + 3.  So tile k's MMAs run
-// while tile k - 1 leaves and tile k + 1 is split, with three tiles loading.
+// memory to four state-tile buffers and two lo-half buffers.  The warps have
+// roles and meet only on mbarriers, never at a block barrier inside the loop:
+//  - warp 13, lane 0 (loader): TMA loads of the state tiles, tile k into
+//    buffer k % 4; tile k + 4 as soon as tile k's MMAs completed;
+//  - warps 1..3 and 8..12 (split): the TF32 lo half of tile k into lo buffer
+//    k % 2, once the tile has landed and tile k - 2's MMAs (which read that
+//    lo buffer) completed; eight 16-byte values a thread;
+//  - warp 0, lane 0 (MMA issuer): once tile k's lo half is written and its
+//    accumulator (k % 2) has been read out, the 48 MMAs and their commits;
+//  - warps 4..7 (epilogue, one per quarter of the TMEM lanes): tile k's result
+//    from accumulator k % 2 to HBM once its MMAs completed, then release the
+//    accumulator.
+// Every wait is bounded in time; a role that gives up sets the error word and
+// leaves, and the roles waiting on it then run out too.
+constexpr int TC_THREADS = 448;
+constexpr int TC_SPLIT_WARPS = 8;
+constexpr int TC_SPLIT_THREADS = 32 * TC_SPLIT_WARPS;
+constexpr int TC_SPLIT_PER = TC_B_BYTES / 16 / TC_SPLIT_THREADS;  // 16-byte values per split thread
+constexpr int TC_EPI_THREADS = 128;
+constexpr int TC_LOADER_WARP = 13;
+static_assert(TC_SPLIT_PER * TC_SPLIT_THREADS * 16 == TC_B_BYTES, "split covers the tile");
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_apply(const __grid_constant__ CUtensorMap map, float *__restrict__ state, const float *__restrict__ a_hi,
                const float *__restrict__ a_lo, uint64_t n_tiles, int *__restrict__ err) {
@@ -143,15 +171,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *sm = tc_raw + pad;
     float *Bbuf = reinterpret_cast<float *>(sm);                          // TC_NB tiles
     float *Blo = reinterpret_cast<float *>(sm + TC_NB * TC_B_BYTES);      // TC_NLO tiles
-    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + (TC_NB + TC_NLO) * TC_B_BYTES);  // [TC_NB]
-    uint64_t *bar_mma = bar_ld + TC_NB;                                   // [2]
-    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_mma + 2);
-    __shared__ int s_ok[2];
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + (TC_NB + TC_NLO) * TC_B_BYTES);  // [TC_NB] tile landed
+    uint64_t *lo_ready = full + TC_NB;      // [TC_NLO] lo half written (TC_SPLIT_THREADS arrivals)
+    uint64_t *mma_done = lo_ready + TC_NLO; // [2] tile's MMAs completed, by accumulator
+    uint64_t *epi_done = mma_done + 2;      // [2] accumulator read out (TC_EPI_THREADS arrivals)
+    uint64_t *freeb = epi_done + 2;         // [TC_NB] tile's MMAs completed, by buffer
+    uint64_t *drain = freeb + TC_NB;        // every MMA issued has completed
+    uint32_t *slot = reinterpret_cast<uint32_t *>(drain + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int i = 0; i < TC_NB; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_ld + i)));
-        for (int i = 0; i < 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(bar_mma + i)));
+        for (int i = 0; i < TC_NB; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(full + i)));
+        for (int i = 0; i < TC_NLO; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_sptr(lo_ready + i)), "r"(TC_SPLIT_THREADS));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(mma_done + i)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_sptr(epi_done + i)), "r"(TC_EPI_THREADS));
+        }
+        for (int i = 0; i < TC_NB; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(freeb + i)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_sptr(drain)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     __syncthreads();
@@ -164,9 +202,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = *slot;
-    // U~ into tensor memory: warp w writes rows 32 (w % 4) .. + 31 (its lane
-    // quarter) of the hi half (w < 4) or the lo half, 32 columns at a time
-    {
+    // U~ into tensor memory: warp w < 8 writes rows 32 (w % 4) .. + 31 (its
+    // lane quarter) of the hi half (w < 4) or the lo half, 32 columns at a time
+    if (warp < 8) {
         const int q = warp & 3, h = warp >> 2;
         const float4 *src = reinterpret_cast<const float4 *>((h ? a_lo : a_hi) + (size_t)(32 * q + lane) * TC_K);
         for (int c = 0; c < TC_K / 32; ++c) {
@@ -194,130 +232,150 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
     const uint64_t n_local = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    auto issue_load = [&](uint64_t k) {
-        const int b = (int)(k % TC_NB);
-        const uint64_t tile = blockIdx.x + k * gridDim.x;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_sptr(bar_ld + b)),
-                     "r"((uint32_t)TC_B_BYTES)
-                     : "memory");
-        const uint64_t m = reinterpret_cast<uint64_t>(&map);
-        for (int kb = 0; kb < TC_KB; ++kb) {
-            const int c0 = kb * 32, c1 = (int)(tile * TC_N);
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                ::"r"(tc_sptr(Bbuf + b * (TC_B_BYTES / 4)) + kb * TC_N * 128), "l"(m), "r"(c0), "r"(c1),
-                "r"(tc_sptr(bar_ld + b))
-                : "memory");
-        }
-    };
-    // result of tile k (accumulator k % 2) to HBM: warp w reads TMEM lanes
-    // 32 (w % 4) .. + 31 (floats of a column) of columns 32 (w / 4) .. + 31
-    auto epilogue = [&](uint64_t k) {
-        const uint64_t tile = blockIdx.x + k * gridDim.x;
-        float *out = state + tile * TC_N * TC_K;
-        const uint32_t tcol = taddr + TC_ACC + (uint32_t)(k & 1) * TC_N;
-        const int q = warp & 3, c = warp >> 2;
-        uint32_t r[32];
-        const uint32_t ta = tcol + ((uint32_t)(q * 32) << 16) + c * 32;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(ta));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int j = 0; j < 32; ++j) out[(c * 32 + j) * TC_K + q * 32 + lane] = __uint_as_float(r[j]);
-    };
-    // Thread 0 waits (bounded) and the block learns the outcome at the
-    // barrier, so every thread takes the same branch; the others then acquire
-    // the completed phase themselves.  One flag per barrier kind, rewritten
-    // only after two more block barriers.
-    auto wait_all = [&](uint64_t *bar, uint32_t parity, int which) -> bool {
-        if (tid == 0) s_ok[which] = tc_wait(bar, parity) ? 1 : 0;
-        __syncthreads();
-        const bool ok = s_ok[which] != 0;
-        if (ok && tid != 0) tc_wait(bar, parity);
-        return ok;
-    };
 
-    uint64_t loads = 0;  // tiles whose load was issued (tile j is in buffer j % TC_NB)
-    if (tid == 0)
-        for (; loads < (uint64_t)TC_NB && loads < n_local; ++loads) issue_load(loads);
-    uint64_t mmas = 0, mmas_done = 0;  // tiles whose MMAs were issued / completed and waited
-    bool failed = false;
-    for (uint64_t k = 0; k < n_local; ++k) {
-        const int b = (int)(k % TC_NB), l = (int)(k % TC_NLO), d = (int)(k & 1);
-        const float *B = Bbuf + b * (TC_B_BYTES / 4);
-        float *L = Blo + l * (TC_B_BYTES / 4);
-        if (!wait_all(bar_ld + b, (uint32_t)(k / TC_NB) & 1u, 0)) {
-            failed = true;
-            break;
-        }
-        // lo half of the state tile (same positions as B, 16 bytes at a time)
-        for (int i = tid; i < TC_B_BYTES / 16; i += TC_THREADS) {
-            const float4 x = reinterpret_cast<const float4 *>(B)[i];
-            reinterpret_cast<float4 *>(L)[i] =
-                make_float4(x.x - tf32_hi(x.x), x.y - tf32_hi(x.y), x.z - tf32_hi(x.z), x.w - tf32_hi(x.w));
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            const uint32_t dcol = taddr + TC_ACC + (uint32_t)d * TC_N;
-            const uint64_t dbhi = tc_desc(tc_sptr(B)), dblo = tc_desc(tc_sptr(L));
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {  // hi*hi, hi*lo, lo*hi
-                const uint32_t acol = taddr + (p == 2 ? TC_A_LO : TC_A_HI);
-                const uint64_t db = p == 1 ? dblo : dbhi;
-#pragma unroll
-                for (int s = 0; s < TC_K / 8; ++s) {
-                    const uint32_t a = acol + 8u * s;
-                    const uint64_t bd = db + (uint64_t)(((s >> 2) * TC_N * 128 + (s & 3) * 32) >> 4);
-                    const uint32_t acc = (p | s) != 0;
-                    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n}" ::"r"(dcol),
-                                 "r"(a), "l"(bd), "r"(idesc), "r"(acc));
+    if (warp == TC_LOADER_WARP) {
+        if (lane == 0) {
+            // ---- loader
+            const uint64_t m = reinterpret_cast<uint64_t>(&map);
+            auto issue_load = [&](uint64_t k) {
+                const int b = (int)(k % TC_NB);
+                const uint64_t tile = blockIdx.x + k * gridDim.x;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_sptr(full + b)),
+                             "r"((uint32_t)TC_B_BYTES)
+                             : "memory");
+                for (int kb = 0; kb < TC_KB; ++kb) {
+                    const int c0 = kb * 32, c1 = (int)(tile * TC_N);
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                        "%3}], [%4];" ::"r"(tc_sptr(Bbuf + b * (TC_B_BYTES / 4)) + kb * TC_N * 128),
+                        "l"(m), "r"(c0), "r"(c1), "r"(tc_sptr(full + b))
+                        : "memory");
                 }
+            };
+            uint64_t loads = 0;
+            for (; loads < (uint64_t)TC_NB && loads < n_local; ++loads) issue_load(loads);
+            for (uint64_t k = 0; loads < n_local; ++k) {
+                // buffer k % TC_NB is free once tile k's MMAs completed; its
+                // next phase needs the load issued here, so the wait cannot
+                // fall a phase behind
+                if (!tc_wait(freeb + (k % TC_NB), (uint32_t)(k / TC_NB) & 1u)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                issue_load(loads++);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                tc_sptr(bar_mma + d)));
+            // the copies still in flight land before the buffers go (at
+            // most one per buffer; on success they all have already)
+            for (uint64_t j = loads > (uint64_t)TC_NB ? loads - TC_NB : 0; j < loads; ++j)
+                tc_wait(full + (j % TC_NB), (uint32_t)(j / TC_NB) & 1u);
         }
-        mmas = k + 1;
-        if (k > 0) {
-            // tile k - 1: its MMAs, its result, its buffer refilled with tile k + 3
-            if (!wait_all(bar_mma + ((k - 1) & 1), (uint32_t)((k - 1) >> 1) & 1u, 1)) {
-                failed = true;
+        __syncwarp();
+    } else if (warp == 0) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            // instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128
+            const uint32_t idesc =
+                (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            bool failed = false;
+            for (uint64_t k = 0; k < n_local; ++k) {
+                const int d = (int)(k & 1), l = (int)(k % TC_NLO), b = (int)(k % TC_NB);
+                // accumulator free, lo half ready (the split saw the tile land
+                // before it wrote the lo half)
+                if (k >= 2 && !tc_wait(epi_done + d, (uint32_t)((k - 2) >> 1) & 1u)) failed = true;
+                if (!failed && !tc_wait(lo_ready + l, (uint32_t)(k / TC_NLO) & 1u)) failed = true;
+                if (failed) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t dcol = taddr + TC_ACC + (uint32_t)d * TC_N;
+                const uint64_t dbhi = tc_desc(tc_sptr(Bbuf + b * (TC_B_BYTES / 4)));
+                const uint64_t dblo = tc_desc(tc_sptr(Blo + l * (TC_B_BYTES / 4)));
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {  // hi*hi, hi*lo, lo*hi
+                    const uint32_t acol = taddr + (p == 2 ? TC_A_LO : TC_A_HI);
+                    const uint64_t db = p == 1 ? dblo : dbhi;
+#pragma unroll
+                    for (int s = 0; s < TC_K / 8; ++s) {
+                        const uint32_t a = acol + 8u * s;
+                        const uint64_t bd = db + (uint64_t)(((s >> 2) * TC_N * 128 + (s & 3) * 32) >> 4);
+                        const uint32_t acc = (p | s) != 0;
+                        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n}" ::"r"(dcol),
+                                     "r"(a), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_sptr(mma_done + d)));
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_sptr(freeb + b)));
+            }
+            // every MMA issued ends before the tensor memory goes: one more
+            // commit tracks them all
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc_sptr(drain)));
+            if (!tc_wait(drain, 0)) failed = true;
+            if (failed) atomicExch(err, 1);
+        }
+        __syncwarp();
+    } else if (warp < 4 || warp >= 8) {
+        // ---- split
+        const int st = (warp < 4 ? warp - 1 : warp - 5) * 32 + lane;
+        for (uint64_t k = 0; k < n_local; ++k) {
+            const int b = (int)(k % TC_NB), l = (int)(k % TC_NLO);
+            if (!tc_wait_warp(full + b, (uint32_t)(k / TC_NB) & 1u)) {
+                if (lane == 0) atomicExch(err, 1);
                 break;
             }
-            mmas_done = k;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            epilogue(k - 1);
-            if (tid == 0 && loads < n_local) issue_load(loads++);
+            if (k >= 2 && !tc_wait_warp(mma_done + (k & 1), (uint32_t)((k - 2) >> 1) & 1u)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            const float4 *B = reinterpret_cast<const float4 *>(Bbuf + b * (TC_B_BYTES / 4));
+            float4 *L = reinterpret_cast<float4 *>(Blo + l * (TC_B_BYTES / 4));
+            float4 x[TC_SPLIT_PER];
+#pragma unroll
+            for (int j = 0; j < TC_SPLIT_PER; ++j) x[j] = B[st + j * TC_SPLIT_THREADS];
+#pragma unroll
+            for (int j = 0; j < TC_SPLIT_PER; ++j)
+                L[st + j * TC_SPLIT_THREADS] = make_float4(x[j].x - tf32_hi(x[j].x), x[j].y - tf32_hi(x[j].y),
+                                                           x[j].z - tf32_hi(x[j].z), x[j].w - tf32_hi(x[j].w));
+            // the MMAs (async proxy) read what was written here
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_arrive(lo_ready + l);
         }
-    }
-    if (!failed && n_local > 0) {
-        if (wait_all(bar_mma + ((n_local - 1) & 1), (uint32_t)((n_local - 1) >> 1) & 1u, 1)) {
-            mmas_done = n_local;
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the
+        // floats of a column), all 64 columns, 32 at a time
+        const int q = warp & 3;
+        for (uint64_t k = 0; k < n_local; ++k) {
+            const int d = (int)(k & 1);
+            if (!tc_wait_warp(mma_done + d, (uint32_t)(k >> 1) & 1u)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            epilogue(n_local - 1);
-        } else {
-            failed = true;
+            const uint64_t tile = blockIdx.x + k * gridDim.x;
+            float *out = state + tile * TC_N * TC_K;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                uint32_t r[32];
+                const uint32_t ta = taddr + TC_ACC + (uint32_t)d * TC_N + ((uint32_t)(q * 32) << 16) + c * 32;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) out[(c * 32 + j) * TC_K + q * 32 + lane] = __uint_as_float(r[j]);
+            }
+            // the accumulator's reads are done: the producer may overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            tc_arrive(epi_done + d);
         }
-    }
-    if (failed && tid == 0) {
-        atomicExch(err, 1);
-        // before the tensor memory and the buffers go: the MMAs issued and
-        // the copies in flight end (or their waits run out too)
-        for (uint64_t j = mmas_done; j < mmas; ++j) tc_wait(bar_mma + (j & 1), (uint32_t)(j >> 1) & 1u);
-        for (uint64_t j = mmas; j < loads; ++j) tc_wait(bar_ld + (j % TC_NB), (uint32_t)(j / TC_NB) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
