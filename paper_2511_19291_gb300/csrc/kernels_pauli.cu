@@ -264,7 +264,7 @@ static cudaError_t expval_t(tqd_state *st, const std::vector<PauliGroup> &groups
         // groups that fit a 12-qubit tile share passes; the rest one pass per group
         std::vector<int> left;
         const std::vector<PauliTileDesc> tiles = plan_pauli_tiles(groups, n, &left);
-        const int tgrid = tiles.empty() ? 0 : pauli_tile_grid(n, st->dtype);
+        const int tgrid = tiles.empty() ? 0 : pauli_tile_expval_width(n, st->dtype);
         size_t launches = 0;
         for (int gi : left) launches += (groups[gi].terms.size() + MAXT - 1) / MAXT;
         const size_t rows = tiles.size() + launches;

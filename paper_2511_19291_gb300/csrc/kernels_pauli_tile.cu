@@ -224,17 +224,40 @@ __global__ void __launch_bounds__(PTHR) k_pauli_tile_apply(const V *__restrict__
 // Walsh-Hadamard transform of the coefficients gathered by zr (and, the
 // other way round, E needs the transform of the per-r products at the
 // terms' zr), with every array index fixed at compile time.
+//
+// E also reads the tile in two more layouts.  Layout L keeps local bits
+// 8..11 (L = 0, the one above), 4..7 (L = 1) or 0..3 (L = 2) in a thread's
+// registers.  A group of X strings alone (no term has a z bit) whose x mask
+// lies inside one layout's register bits then pairs registers of the same
+// thread: its share of E is sum_j c_j * sum_b Re(conj(psi_{b^x}) psi_b), each
+// pair once and doubled, with no sign, no shared-memory partner and no
+// per-term work in the tile loop.  Taken for x masks of one qubit (X_i terms,
+// the transverse fields of spin models); wider X strings stay in the loop over
+// groups (their sixteen register cases would not fit the registers).
+//
+// Terms of a group with the same local z mask have the same sign at every
+// local index: their coefficients, signed by the tile origin, are summed per
+// tile into one class coefficient, and the loops over a group run over its
+// classes.
 struct Pauli2Desc {
-    PauliTileDesc P;                       // terms of each group sorted by zr
-    uint16_t zfirst[PT_MAXG][17];          // terms of group g with zr == m: [zfirst[g][m], zfirst[g][m + 1])
+    PauliTileDesc P;                       // terms of each group sorted by local z mask
+    uint16_t zfirst[PT_MAXG][17];          // classes of group g with zr == m: [zfirst[g][m], zfirst[g][m + 1])
+    uint16_t gcls[PT_MAXG + 1];            // classes of group g: [gcls[g], gcls[g + 1])
+    uint16_t cfirst[PT_MAXT + 1];          // terms of class c: [cfirst[c], cfirst[c + 1])
+    uint16_t czl[PT_MAXT];                 // local z mask of class c
+    int n_cls;
     uint32_t real_groups;                  // bit g: every coefficient of group g is real
+    uint32_t xonly;                        // bit g: group g is an X-only group of one layout (E only)
+    uint8_t xfirst[4];                     // layout L's X-only groups: entries [xfirst[L], xfirst[L + 1])
+    uint8_t xreg[PT_MAXG];                 // an entry's qubit: its bit on the layout's register index (0..3)
+    float xcoef[PT_MAXG];                  // an entry's sum of coefficients
 };
 
 struct Pauli2Smem {
     Pauli2Desc D;
     uint64_t hoff[256];
     uint64_t tz[PT_MAXT];                  // z bits outside Q as tile-index bits
-    float2 ce[PT_MAXT];                    // this tile's coefficients (weights, scale, origin sign)
+    float2 ce[PT_MAXT];                    // this tile's class coefficients (weights, scale, origin sign)
     float2 cw[PT_MAXT];                    // coefficients with weights and scale
 };
 
@@ -290,17 +313,22 @@ __device__ __forceinline__ void p2_load(const Pauli2Smem &S, const float2 *__res
     }
 }
 
-__device__ __forceinline__ uint64_t p2_origin(const PauliTileDesc &P, uint64_t t) {
-    uint64_t g = 0;
-    for (int i = 0; i < P.n - PK; ++i) g |= ((t >> i) & 1ull) << P.out_q[i];
-    return g;
-}
-
-// Tile t's coefficients: weights, scale and the origin's sign.
+// Tile t's class coefficients: the class's terms with weights, scale and
+// the origin's sign.
 __device__ __forceinline__ void p2_coeffs(Pauli2Smem &S, uint64_t t) {
-    for (int j = threadIdx.x; j < S.D.P.n_terms; j += blockDim.x) {
-        const float2 c = S.cw[j];
-        S.ce[j] = (__popcll(t & S.tz[j]) & 1) ? make_float2(-c.x, -c.y) : c;
+    for (int c = threadIdx.x; c < S.D.n_cls; c += blockDim.x) {
+        float2 e = make_float2(0.f, 0.f);
+        for (int j = S.D.cfirst[c]; j < S.D.cfirst[c + 1]; ++j) {
+            const float2 w = S.cw[j];
+            if (__popcll(t & S.tz[j]) & 1) {
+                e.x -= w.x;
+                e.y -= w.y;
+            } else {
+                e.x += w.x;
+                e.y += w.y;
+            }
+        }
+        S.ce[c] = e;
     }
 }
 
@@ -343,6 +371,20 @@ __device__ __forceinline__ uint64_t p2_origin_t(const P2Origin &O, uint64_t t) {
     return O.t[0][t & 255] | O.t[1][(t >> 8) & 255] | O.t[2][(t >> 16) & 255];
 }
 
+// sum_r Re(conj(a[r ^ XR]) a[r]) over the 16 registers: each pair {r, r ^ XR}
+// once (r without XR's highest bit), doubled; two accumulators.
+template <int XR> __device__ __forceinline__ float pair_dot(const float2 (&a)[PPER]) {
+    constexpr int TOP = XR >= 8 ? 8 : XR >= 4 ? 4 : XR >= 2 ? 2 : 1;
+    float2 s[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    int c = 0;
+#pragma unroll
+    for (int r = 0; r < PPER; ++r)
+        if (!(r & TOP)) {
+            s[c & 1] = f2_fma(a[r ^ XR], a[r], s[c & 1]);
+            ++c;
+        }
+    return 2.f * ((s[0].x + s[1].x) + (s[0].y + s[1].y));
+}
 // E over the tiles of one launch (complex64).
 __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restrict__ psi, const Pauli2Desc Dg,
                                                            double *__restrict__ partials) {
@@ -358,7 +400,7 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
     const uint64_t n_tiles = (uint64_t)1 << (P.n - PK);
     // this thread's sign of every term (local bits 0..7 = thread bits)
     uint64_t tpar = 0;
-    for (int j = 0; j < P.n_terms; ++j) tpar |= (uint64_t)(__popc(tid & P.zl[j] & 0xFFu) & 1) << j;
+    for (int c = 0; c < S.D.n_cls; ++c) tpar |= (uint64_t)(__popc(tid & S.D.czl[c] & 0xFFu) & 1) << c;
     uint64_t t = blockIdx.x;
     if (t < n_tiles) p2_load(S, psi, bufs, p2_origin_t(O, t), tid);
     cp_async_commit();
@@ -372,13 +414,34 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
         __syncthreads();
         const float2 *tile = bufs + cur * PTS;
         float2 a[PPER];
-#pragma unroll
-        for (int r = 0; r < PPER; ++r) a[r] = tile[r * PTHR + tid];
         float part = 0.f;
+        // X-only groups, layout by layout, layout 0 last (the loop over the
+        // other groups below reads it too): layout 1 holds
+        // l = (tid / 16) * 256 + r * 16 + tid % 16, layout 2
+        // l = tid * 16 + (r ^ (tid % 16)) (the XOR spreads a half-warp's
+        // loads over the banks; the pairs r, r ^ x are the same either way)
+#pragma unroll
+        for (int L = 2; L >= 0; --L) {
+            const int i0 = S.D.xfirst[L], i1 = S.D.xfirst[L + 1];
+            if (L > 0 && i0 == i1) continue;
+#pragma unroll
+            for (int r = 0; r < PPER; ++r)
+                a[r] = tile[L == 0   ? (uint32_t)r * PTHR + tid
+                            : L == 1 ? ((tid >> 4) << 8) | ((uint32_t)r << 4) | (tid & 15u)
+                                     : (tid << 4) | ((uint32_t)r ^ (tid & 15u))];
+            if (i0 == i1) continue;
+            // the four one-qubit pair sums of this layout, then each group's
+            const float d0 = pair_dot<1>(a), d1 = pair_dot<2>(a), d2 = pair_dot<4>(a), d3 = pair_dot<8>(a);
+            for (int i = i0; i < i1; ++i) {
+                const int k = S.D.xreg[i];
+                part = fmaf(S.D.xcoef[i], k == 0 ? d0 : k == 1 ? d1 : k == 2 ? d2 : d3, part);
+            }
+        }
         for (int g = 0; g < P.n_groups; ++g) {
+            if ((S.D.xonly >> g) & 1u) continue;  // below, in its layout
             const uint32_t xl = P.gx[g];
             const uint16_t *zf = S.D.zfirst[g];
-            const int j0 = P.gfirst[g], j1 = P.gfirst[g + 1];
+            const int j0 = S.D.gcls[g], j1 = S.D.gcls[g + 1];
             const bool real = (S.D.real_groups >> g) & 1u;
             const bool any_zr = zf[16] > zf[1];
             // u_r = conj(psi_{l ^ x}) psi_l, l = r * 256 + tid; the partner
@@ -454,13 +517,23 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
                     });
                 }
                 wht16(ur);
-                if (xl != 0 && !real) wht16(ui);
+                if (real) {
+                    // real coefficients: only the real parts meet
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    for (int j = zf[m]; j < zf[m + 1]; ++j) {
-                        float2 c = S.ce[j];
-                        if ((tpar >> j) & 1) c = make_float2(-c.x, -c.y);
-                        part = fmaf(c.x, ur[m], fmaf(-c.y, ui[m], part));
+                    for (int m = 0; m < 16; ++m)
+                        for (int j = zf[m]; j < zf[m + 1]; ++j) {
+                            const float cx = S.ce[j].x;
+                            part = fmaf((tpar >> j) & 1 ? -cx : cx, ur[m], part);
+                        }
+                } else {
+                    if (xl != 0) wht16(ui);
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        for (int j = zf[m]; j < zf[m + 1]; ++j) {
+                            float2 c = S.ce[j];
+                            if ((tpar >> j) & 1) c = make_float2(-c.x, -c.y);
+                            part = fmaf(c.x, ur[m], fmaf(-c.y, ui[m], part));
+                        }
                     }
                 }
             }
@@ -469,6 +542,148 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_expval(const float2 *__restr
         __syncthreads();
     }
     const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// E of a launch whose groups are X-only groups of the three layouts (one-qubit
+// X terms; the transverse-field part of a spin Hamiltonian) and at most one
+// diagonal group with real coefficients (the Z strings).  Nothing in the
+// X-only part depends on a coefficient or a sign, so each thread only sums,
+// per layout L and register bit k, sum_r Re(conj(a[r ^ 2^k]) a[r]) over its
+// tiles, and weighs the twelve sums once at the end.  The diagonal group takes
+// the thread's probabilities in layout 0 through the 16-point transform
+// (like the loop over groups of k_pauli2_expval) with its class coefficients
+// signed per tile.  Few registers: three blocks per SM, each with two tile
+// buffers.
+struct PauliXDesc {
+    int n;                 // qubits of the state
+    uint32_t lmask;        // bit L: some group lies in layout L
+    uint8_t hi[8];         // Q's qubits above qubit 3
+    uint8_t out_q[32];     // qubits outside Q (tile index bit i -> qubit)
+    float coef[3][4];      // weight of layout L's pair sum over register bit k (0: no group)
+    // the diagonal group (DIAG kernels): its classes of equal local z mask
+    int n_cls;
+    uint32_t mmask;              // bit m: some class has register mask m
+    uint16_t zfirst[17];         // classes with register mask m: [zfirst[m], zfirst[m + 1])
+    uint16_t czl[PT_MAXT];       // local z mask of class c
+    uint16_t cfirst[PT_MAXT + 1];  // terms of class c: [cfirst[c], cfirst[c + 1])
+    uint64_t tz[PT_MAXT];        // a term's z bits outside Q, as tile-index bits
+    float cw[PT_MAXT];           // a term's coefficient
+};
+
+struct PauliXSmem {
+    uint64_t hoff[256];    // offsets of the values of Q's high qubits
+    uint64_t otab[6][16];  // tile origin, four tile-index bits at a time
+};
+
+template <bool DIAG>
+__global__ void __launch_bounds__(PTHR, 3) k_pauli2_xonly(const float2 *__restrict__ psi, const __grid_constant__ PauliXDesc D,
+                                                          double *__restrict__ partials) {
+    __shared__ PauliXSmem S;
+    __shared__ double sh[PTHR / 32];
+    __shared__ float ce[DIAG ? PT_MAXT : 1];  // the tile's class coefficients
+    extern __shared__ __align__(16) unsigned char pt_dyn[];
+    float2 *bufs = reinterpret_cast<float2 *>(pt_dyn);  // 2 x PTS amplitudes
+    const uint32_t tid = threadIdx.x;
+    const int nt = D.n - PK;
+    for (int h = tid; h < 256; h += PTHR) {
+        uint64_t o = 0;
+        for (int i = 0; i < 8; ++i) o |= (uint64_t)((h >> i) & 1) << D.hi[i];
+        S.hoff[h] = o;
+    }
+    for (int i = tid; i < 6 * 16; i += PTHR) {
+        const int k = i >> 4, v = i & 15;
+        uint64_t g = 0;
+        for (int b = 0; b < 4; ++b)
+            if (4 * k + b < nt && ((v >> b) & 1)) g |= 1ull << D.out_q[4 * k + b];
+        S.otab[k][v] = g;
+    }
+    // this thread's sign of every class (local bits 0..7 = thread bits)
+    uint64_t tpar = 0;
+    if (DIAG)
+        for (int c = 0; c < D.n_cls; ++c) tpar |= (uint64_t)(__popc(tid & D.czl[c] & 0xFFu) & 1) << c;
+    __syncthreads();
+    auto origin = [&](uint64_t t) {
+        uint64_t g = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) g |= S.otab[k][(t >> (4 * k)) & 15u];
+        return g;
+    };
+    // this thread's 8 copies of 2 amplitudes: local indices k * 512 + 2 * tid
+    auto load = [&](float2 *buf, uint64_t o) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t l = (uint32_t)k * 512u + 2u * tid;
+            cp_async16(smem_u32(buf + l), psi + (o | S.hoff[l >> 4] | (l & 15u)));
+        }
+    };
+    const uint64_t n_tiles = (uint64_t)1 << nt;
+    uint64_t t = blockIdx.x;
+    if (t < n_tiles) load(bufs, origin(t));
+    cp_async_commit();
+    float acc[3][4];
+#pragma unroll
+    for (int L = 0; L < 3; ++L)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[L][k] = 0.f;
+    float dacc = 0.f;  // the diagonal group's share
+    for (int cur = 0; t < n_tiles; t += gridDim.x, cur ^= 1) {
+        const uint64_t tn = t + gridDim.x;
+        if (tn < n_tiles) load(bufs + (cur ^ 1) * PTS, origin(tn));
+        cp_async_commit();
+        if (DIAG)
+            // tile t's class coefficients: the class's terms signed by the origin
+            for (int c = tid; c < D.n_cls; c += PTHR) {
+                float e = 0.f;
+                for (int j = D.cfirst[c]; j < D.cfirst[c + 1]; ++j)
+                    e += (__popcll(t & D.tz[j]) & 1) ? -D.cw[j] : D.cw[j];
+                ce[c] = e;
+            }
+        cp_async_wait1();
+        __syncthreads();
+        const float2 *tile = bufs + cur * PTS;
+#pragma unroll
+        for (int L = 2; L >= 0; --L) {
+            if ((DIAG && L == 0) || ((D.lmask >> L) & 1u)) {
+                float2 a[PPER];
+#pragma unroll
+                for (int r = 0; r < PPER; ++r)
+                    a[r] = tile[L == 0   ? (uint32_t)r * PTHR + tid
+                                : L == 1 ? ((tid >> 4) << 8) | ((uint32_t)r << 4) | (tid & 15u)
+                                         : (tid << 4) | ((uint32_t)r ^ (tid & 15u))];
+                if ((D.lmask >> L) & 1u) {
+                    acc[L][0] += pair_dot<1>(a);
+                    acc[L][1] += pair_dot<2>(a);
+                    acc[L][2] += pair_dot<4>(a);
+                    acc[L][3] += pair_dot<8>(a);
+                }
+                if (DIAG && L == 0) {
+                    // probabilities at l = r * 256 + tid, transformed over r
+                    float u[PPER];
+#pragma unroll
+                    for (int r = 0; r < PPER; ++r) u[r] = fmaf(a[r].x, a[r].x, a[r].y * a[r].y);
+                    wht16(u);
+                    float part = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        if (!((D.mmask >> m) & 1u)) continue;
+                        float cm = 0.f;
+                        for (int c = D.zfirst[m]; c < D.zfirst[m + 1]; ++c)
+                            cm += ((tpar >> c) & 1) ? -ce[c] : ce[c];
+                        part = fmaf(cm, u[m], part);
+                    }
+                    dacc += part;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    double part = (double)dacc;
+#pragma unroll
+    for (int L = 0; L < 3; ++L)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) part += (double)D.coef[L][k] * (double)acc[L][k];
+    const double tot = block_sum(part, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
@@ -494,8 +709,8 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
     // (tid ^ x) and the register part x's own parity (group's x)
     uint64_t tpar = 0;
     for (int g = 0; g < P.n_groups; ++g)
-        for (int j = P.gfirst[g]; j < P.gfirst[g + 1]; ++j) {
-            const uint32_t z = P.zl[j];
+        for (int j = S.D.gcls[g]; j < S.D.gcls[g + 1]; ++j) {
+            const uint32_t z = S.D.czl[j];
             const int par = (__popc((tid ^ P.gx[g]) & z & 0xFFu) + __popc((P.gx[g] >> 8) & (z >> 8))) & 1;
             tpar |= (uint64_t)par << j;
         }
@@ -524,7 +739,7 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
         for (int g = 0; g < P.n_groups; ++g) {
             const uint32_t xl = P.gx[g];
             const uint16_t *zf = S.D.zfirst[g];
-            const int j0 = P.gfirst[g], j1 = P.gfirst[g + 1];
+            const int j0 = S.D.gcls[g], j1 = S.D.gcls[g + 1];
             const bool real = (S.D.real_groups >> g) & 1u;
             const float2 *pt = tile + (tid ^ (xl & 0xFFu));
             const uint32_t xr = xl >> 8;
@@ -621,8 +836,9 @@ int tile_grid_pauli(int n, int dtype) {
     return (int)std::min<uint64_t>(g, tiles);
 }
 
-// The complex64 kernels' descriptor: each group's terms sorted by their z
-// bits on the register index (local bits 8..11), with the range of each value.
+// The complex64 kernels' descriptor: each group's terms sorted by their local
+// z mask (so by its bits on the register index, local bits 8..11, first),
+// runs of equal masks as classes, the range of classes of each register mask.
 Pauli2Desc make_pauli2(const PauliTileDesc &src) {
     Pauli2Desc d;
     memset(&d, 0, sizeof(d));
@@ -631,7 +847,7 @@ Pauli2Desc make_pauli2(const PauliTileDesc &src) {
         const int a = src.gfirst[g], b = src.gfirst[g + 1];
         std::vector<int> ord;
         for (int j = a; j < b; ++j) ord.push_back(j);
-        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return (src.zl[x] >> 8) < (src.zl[y] >> 8); });
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return src.zl[x] < src.zl[y]; });
         for (int k = 0; k < b - a; ++k) {
             const int j = ord[k], t = a + k;
             d.P.zl[t] = src.zl[j];
@@ -643,12 +859,45 @@ Pauli2Desc make_pauli2(const PauliTileDesc &src) {
         bool real = true;
         for (int j = a; j < b; ++j) real = real && d.P.cim[j] == 0.0;
         if (real) d.real_groups |= 1u << g;
-        int k = a;
+        d.gcls[g] = (uint16_t)d.n_cls;
+        for (int j = a; j < b; ++j)
+            if (j == a || d.P.zl[j] != d.P.zl[j - 1]) {
+                d.czl[d.n_cls] = d.P.zl[j];
+                d.cfirst[d.n_cls++] = (uint16_t)j;
+            }
+        d.gcls[g + 1] = (uint16_t)d.n_cls;
+        d.cfirst[d.n_cls] = (uint16_t)b;
+        int k = d.gcls[g];
         for (int m = 0; m <= 16; ++m) {
-            while (m < 16 && k < b && (d.P.zl[k] >> 8) < m) ++k;
-            d.zfirst[g][m] = (uint16_t)(m == 16 ? b : k);
+            while (m < 16 && k < d.gcls[g + 1] && (d.czl[k] >> 8) < m) ++k;
+            d.zfirst[g][m] = (uint16_t)(m == 16 ? d.gcls[g + 1] : k);
         }
     }
+    // X-only groups and their layouts
+    int per[3][PT_MAXG], cnt[3] = {0, 0, 0};
+    for (int g = 0; g < src.n_groups; ++g) {
+        const uint32_t x = src.gx[g];
+        bool xo = x != 0;
+        for (int j = src.gfirst[g]; j < src.gfirst[g + 1] && xo; ++j)
+            xo = d.P.zl[j] == 0 && d.P.zo[j] == 0 && d.P.cim[j] == 0.0;
+        if (!xo) continue;
+        const int L = (x & 0xF00u) == x ? 0 : (x & 0xF0u) == x ? 1 : (x & 0xFu) == x ? 2 : -1;
+        if (L < 0 || __builtin_popcount(x) != 1) continue;
+        per[L][cnt[L]++] = g;
+        d.xonly |= 1u << g;
+    }
+    int e = 0;
+    for (int L = 0; L < 3; ++L) {
+        d.xfirst[L] = (uint8_t)e;
+        for (int i = 0; i < cnt[L]; ++i, ++e) {
+            const int g = per[L][i];
+            double c = 0.0;
+            for (int j = src.gfirst[g]; j < src.gfirst[g + 1]; ++j) c += d.P.cre[j];
+            d.xreg[e] = (uint8_t)__builtin_ctz((src.gx[g] >> (L == 0 ? 8 : L == 1 ? 4 : 0)) & 15u);
+            d.xcoef[e] = (float)c;
+        }
+    }
+    d.xfirst[3] = (uint8_t)e;
     return d;
 }
 
@@ -767,14 +1016,80 @@ std::vector<PauliTileDesc> plan_pauli_tiles(const std::vector<PauliGroup> &group
     return out;
 }
 
+// Blocks of the X-only launches (three per SM) and of the others (two).
+static int xonly_grid(int n) {
+    const uint64_t tiles = (uint64_t)1 << (n - PK);
+    return (int)std::min<uint64_t>((uint64_t)device_sm_count() * 3, tiles);
+}
+
 static cudaError_t tile_expval_c64(const tqd_state *st, const std::vector<PauliTileDesc> &launches,
                                    double *partials, int pblk, cudaStream_t s) {
-    const int grid = tile_grid_pauli(st->n, TQD_C64);
+    const int grid = tile_grid_pauli(st->n, TQD_C64), xgrid = xonly_grid(st->n);
+    const int width = std::max(grid, xgrid);  // partials summed per launch
     allow_tile_smem(k_pauli2_expval, 2 * PTS * sizeof(float2));
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_pauli2_xonly<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * PTS * (int)sizeof(float2));
+        cudaFuncSetAttribute(k_pauli2_xonly<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * PTS * (int)sizeof(float2));
+    });
     for (size_t i = 0; i < launches.size(); ++i) {
         const Pauli2Desc d = make_pauli2(launches[i]);
+        double *row = partials + i * pblk;
         ProfScope ps(PK_EXPVAL, (double)((uint64_t)1 << st->n) * sizeof(float2), s);
-        k_pauli2_expval<<<grid, PTHR, 2 * PTS * sizeof(float2), s>>>((const float2 *)st->amps, d, partials + i * pblk);
+        // every group X-only, or the diagonal group with real coefficients
+        int diag = -1;
+        bool lean = d.P.n_groups > 0;
+        for (int g = 0; g < d.P.n_groups && lean; ++g) {
+            if ((d.xonly >> g) & 1u) continue;
+            if (d.P.gx[g] == 0 && ((d.real_groups >> g) & 1u) && diag < 0) diag = g;
+            else lean = false;
+        }
+        int used;
+        if (lean) {
+            PauliXDesc x;
+            memset(&x, 0, sizeof(x));
+            x.n = d.P.n;
+            memcpy(x.hi, d.P.hi, sizeof(x.hi));
+            memcpy(x.out_q, d.P.out_q, sizeof(x.out_q));
+            for (int L = 0; L < 3; ++L)
+                for (int e = d.xfirst[L]; e < d.xfirst[L + 1]; ++e) {
+                    x.coef[L][d.xreg[e]] += d.xcoef[e];
+                    x.lmask |= 1u << L;
+                }
+            if (diag >= 0) {
+                // the group's classes, renumbered from 0, and their terms
+                const int c0 = d.gcls[diag], c1 = d.gcls[diag + 1], j0 = d.cfirst[c0];
+                const int nt = d.P.n - PK;
+                x.n_cls = c1 - c0;
+                for (int c = c0; c < c1; ++c) {
+                    x.czl[c - c0] = d.czl[c];
+                    x.cfirst[c - c0] = (uint16_t)(d.cfirst[c] - j0);
+                    x.mmask |= 1u << (d.czl[c] >> 8);
+                }
+                x.cfirst[c1 - c0] = (uint16_t)(d.cfirst[c1] - j0);
+                for (int m = 0; m <= 16; ++m) x.zfirst[m] = (uint16_t)(d.zfirst[diag][m] - c0);
+                for (int j = j0; j < d.cfirst[c1]; ++j) {
+                    uint64_t tz = 0;
+                    for (int b = 0; b < nt; ++b) tz |= ((d.P.zo[j] >> d.P.out_q[b]) & 1ull) << b;
+                    x.tz[j - j0] = tz;
+                    x.cw[j - j0] = (float)d.P.cre[j];
+                }
+                k_pauli2_xonly<true><<<xgrid, PTHR, 2 * PTS * sizeof(float2), s>>>((const float2 *)st->amps, x, row);
+            } else {
+                k_pauli2_xonly<false><<<xgrid, PTHR, 2 * PTS * sizeof(float2), s>>>((const float2 *)st->amps, x, row);
+            }
+            used = xgrid;
+        } else {
+            k_pauli2_expval<<<grid, PTHR, 2 * PTS * sizeof(float2), s>>>((const float2 *)st->amps, d, row);
+            used = grid;
+        }
+        // the row's remaining entries count as zero
+        if (used < width) {
+            cudaError_t e = cudaMemsetAsync(row + used, 0, (size_t)(width - used) * sizeof(double), s);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaGetLastError();
 }
@@ -799,6 +1114,10 @@ cudaError_t launch_pauli_tile_expval(const tqd_state *st, const std::vector<Paul
 }
 
 int pauli_tile_grid(int n, int dtype) { return tile_grid_pauli(n, dtype); }
+
+int pauli_tile_expval_width(int n, int dtype) {
+    return dtype == TQD_C64 ? std::max(tile_grid_pauli(n, dtype), xonly_grid(n)) : tile_grid_pauli(n, dtype);
+}
 
 static cudaError_t tile_apply_c64(const tqd_state *psi, const std::vector<PauliTileDesc> &launches,
                                   const double *weights, double scale, tqd_state *out, bool accumulate,

@@ -37,6 +37,9 @@ std::vector<PauliTileDesc> plan_pauli_tiles(const std::vector<PauliGroup> &group
 
 // Blocks of one tile launch; launch i writes partials[i * pblk + block].
 int pauli_tile_grid(int n, int dtype);
+// Partials of one expectation launch: launch i fills partials[i * pblk + j]
+// for j < this width (blocks it did not have are written as zero).
+int pauli_tile_expval_width(int n, int dtype);
 cudaError_t launch_pauli_tile_expval(const tqd_state *st, const std::vector<PauliTileDesc> &launches,
                                      double *partials, int pblk, cudaStream_t s);
 // out = (accumulate ? out : 0) + scale * sum w_j c_j P_j psi over the launches' groups.
