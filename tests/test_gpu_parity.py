@@ -374,7 +374,13 @@ def tensor_core_case(n, blocks, seed, **kw):
     S.profile_enable(False)
     assert prof.get("tc_block", {}).get("launches", 0) >= 1
     ref = oracle.run(circ, params)
-    np.testing.assert_allclose(to_numpy(st), ref, atol=1e-5, rtol=0)
+    # the amplitude bar of the other parity tests: TF32 hi/lo products with
+    # FP32 accumulation lose about 2^-21 of each 128-term dot product, well
+    # inside it
+    err = float(np.max(np.abs(to_numpy(st) - ref)))
+    tol = AMP_TOL["c64"] * math.sqrt(len(circ.gates) / 100 + 1)
+    print(f"\ntensor-core block, n={n}: max amplitude error {err:.2e} (bar {tol:.2e})")
+    assert err <= tol, (err, tol)
     e_ref, g_ref = oracle.grad_stored(circ, params, terms)
     assert abs(S.expval(st, terms).item() - e_ref) < 1e-5
     lam = S.State(n, torch.complex64)
