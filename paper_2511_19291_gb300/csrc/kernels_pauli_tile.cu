@@ -237,11 +237,13 @@ __global__ void __launch_bounds__(PTHR) k_pauli_tile_apply(const V *__restrict__
 //
 // Terms of a group with the same local z mask have the same sign at every
 // local index: their coefficients, signed by the tile origin, are summed per
-// tile into one class coefficient, and the loops over a group run over its
-// classes.
+// tile into one class coefficient, and the E kernel's loops over a group run
+// over its classes (the H psi kernel keeps one coefficient per term: its
+// per-tile class sums would sit on the tile's critical path).
 struct Pauli2Desc {
     PauliTileDesc P;                       // terms of each group sorted by local z mask
     uint16_t zfirst[PT_MAXG][17];          // classes of group g with zr == m: [zfirst[g][m], zfirst[g][m + 1])
+    uint16_t tzfirst[PT_MAXG][17];         // terms of group g with zr == m (the H psi kernel works per term)
     uint16_t gcls[PT_MAXG + 1];            // classes of group g: [gcls[g], gcls[g + 1])
     uint16_t cfirst[PT_MAXT + 1];          // terms of class c: [cfirst[c], cfirst[c + 1])
     uint16_t czl[PT_MAXT];                 // local z mask of class c
@@ -310,6 +312,15 @@ __device__ __forceinline__ void p2_load(const Pauli2Smem &S, const float2 *__res
     for (int k = 0; k < 8; ++k) {
         const uint32_t l = (uint32_t)k * 512u + 2u * tid;
         cp_async16(smem_u32(buf + l), psi + (origin | S.hoff[l >> 4] | (l & 15u)));
+    }
+}
+
+// Tile t's term coefficients: weights, scale and the origin's sign, one
+// thread per term (the H psi kernel).
+__device__ __forceinline__ void p2_coeffs_terms(Pauli2Smem &S, uint64_t t) {
+    for (int j = threadIdx.x; j < S.D.P.n_terms; j += blockDim.x) {
+        const float2 c = S.cw[j];
+        S.ce[j] = (__popcll(t & S.tz[j]) & 1) ? make_float2(-c.x, -c.y) : c;
     }
 }
 
@@ -709,8 +720,8 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
     // (tid ^ x) and the register part x's own parity (group's x)
     uint64_t tpar = 0;
     for (int g = 0; g < P.n_groups; ++g)
-        for (int j = S.D.gcls[g]; j < S.D.gcls[g + 1]; ++j) {
-            const uint32_t z = S.D.czl[j];
+        for (int j = P.gfirst[g]; j < P.gfirst[g + 1]; ++j) {
+            const uint32_t z = P.zl[j];
             const int par = (__popc((tid ^ P.gx[g]) & z & 0xFFu) + __popc((P.gx[g] >> 8) & (z >> 8))) & 1;
             tpar |= (uint64_t)par << j;
         }
@@ -732,14 +743,14 @@ __global__ void __launch_bounds__(PTHR, 2) k_pauli2_apply(const float2 *__restri
 #pragma unroll
             for (int r = 0; r < PPER; ++r) o[r] = make_float2(0.f, 0.f);
         }
-        p2_coeffs(S, t);
+        p2_coeffs_terms(S, t);
         cp_async_wait1();
         __syncthreads();
         const float2 *tile = bufs + cur * PTS;
         for (int g = 0; g < P.n_groups; ++g) {
             const uint32_t xl = P.gx[g];
-            const uint16_t *zf = S.D.zfirst[g];
-            const int j0 = S.D.gcls[g], j1 = S.D.gcls[g + 1];
+            const uint16_t *zf = S.D.tzfirst[g];
+            const int j0 = P.gfirst[g], j1 = P.gfirst[g + 1];
             const bool real = (S.D.real_groups >> g) & 1u;
             const float2 *pt = tile + (tid ^ (xl & 0xFFu));
             const uint32_t xr = xl >> 8;
@@ -867,6 +878,11 @@ Pauli2Desc make_pauli2(const PauliTileDesc &src) {
             }
         d.gcls[g + 1] = (uint16_t)d.n_cls;
         d.cfirst[d.n_cls] = (uint16_t)b;
+        int kt = a;
+        for (int m = 0; m <= 16; ++m) {
+            while (m < 16 && kt < b && (d.P.zl[kt] >> 8) < m) ++kt;
+            d.tzfirst[g][m] = (uint16_t)(m == 16 ? b : kt);
+        }
         int k = d.gcls[g];
         for (int m = 0; m <= 16; ++m) {
             while (m < 16 && k < d.gcls[g + 1] && (d.czl[k] >> 8) < m) ++k;
