@@ -54,6 +54,43 @@ def test_expval_parity(dtype, n, seed):
     np.testing.assert_allclose(per, per_ref, atol=E_TOL[dtype], rtol=0)
 
 
+def spin_terms(rng, n, kind):
+    """Observables of the shapes the tile expectation kernels distinguish:
+    one-qubit X fields alone; Z strings (ZZ chain, Z fields, a long Z string)
+    with X fields; and the same plus two-qubit X strings and a Y term (the
+    general kernel).  Coefficients random in [-1, 1)."""
+    c = lambda: rng.uniform01() * 2.0 - 1.0
+    xs = [W.PauliTerm(c(), ((i, "X"),)) for i in range(n)]
+    if kind == "x":
+        return xs
+    zs = [W.PauliTerm(c(), ((i, "Z"), (i + 1, "Z"))) for i in range(n - 1)]
+    zs += [W.PauliTerm(c(), ((i, "Z"),)) for i in range(0, n, 3)]
+    zs += [W.PauliTerm(c(), tuple((q, "Z") for q in range(0, n, 2)))]
+    if kind == "zx":
+        return zs + xs
+    return zs + xs + [W.PauliTerm(c(), ((i, "X"), (i + 5, "X"))) for i in range(0, n - 5, 4)] + \
+        [W.PauliTerm(c(), ((1, "Y"), (n - 1, "Z")))]
+
+
+@pytest.mark.parametrize("kind", ["x", "zx", "general"])
+@pytest.mark.parametrize("n", [12, 14, 17])
+def test_expval_tile_kernels_parity(kind, n):
+    """E of the spin-model shapes on 12..17 qubits (every tile launch: the
+    X-only kernel with its three register layouts, the one that also carries
+    the real diagonal group, and the general kernel) against the oracle, in
+    complex64 and complex128."""
+    S = sim()
+    rng = W.SplitMix64(5100 + n)
+    circ, params = W.random_circuit(rng, n, 60 + 10 * n)
+    terms = spin_terms(rng, n, kind)
+    psi = oracle.run(circ, params)
+    e_ref, _ = oracle.expval(n, psi, terms)
+    for dtype in ("c64", "c128"):
+        st, _, _ = gpu_state(circ, params, "fused", dtype)
+        e = S.expval(st, terms).item()
+        assert abs(e - e_ref) <= E_TOL[dtype], (dtype, e, e_ref)
+
+
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("n,seed", [(2, 1), (7, 2), (13, 3)])
 def test_apply_observable_parity(dtype, n, seed):
