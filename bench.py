@@ -537,14 +537,17 @@ def tc_bench(S, torch, dev, n, n_gates, barrier, reps=5):
 
 
 # ------------------------------------------------ QFT + ansatz at 32 qubits
-def qft_bench(S, torch, dev, n, barrier, layers=8):
+def qft_bench(S, torch, dev, n, barrier, layers=8, mode="fused"):
     """One gradient evaluation of the QFT followed by `layers` ansatz layers
     (Ising H) on an n-qubit complex64 state: psi and lambda (2 x 2^n x 8 B,
     64 GiB at 32 qubits) resident in HBM.  Reports the step time and the
-    fused passes' achieved bandwidth (algorithmic bytes over CUDA-event time)."""
+    fused passes' achieved bandwidth (algorithmic bytes over CUDA-event time).
+    mode "tc": the same workload planned with tensor-core blocks for runs of
+    at least 16 gates on qubits 0..5 (forward, and the reverse sweep of such
+    a block when its gates are fixed)."""
     from paper_2511_19291_gb300 import workloads as W
     w = W.workload_qft(n, layers)
-    c = S.Circuit(w.circuit, device=dev)
+    c = S.Circuit(w.circuit, mode=mode, device=dev)
     obs = S.Observable(w.terms)
     psi = S.State(n, torch.complex64, dev)
     lam = S.State(n, torch.complex64, dev)
@@ -570,8 +573,9 @@ def qft_bench(S, torch, dev, n, barrier, layers=8):
     S.profile_enable(False)
     peak, src = peaks()
     out = {"n_qubits": n, "layers": layers, "gates": len(w.circuit.gates), "n_params": w.circuit.n_params,
-           "ms_per_grad_eval": ms, "energy": float(e.item()), "peak": peak, "peak_source": f"{src} hbm_gbs"}
-    for k in ("tile_fwd", "tile_adj"):
+           "plan": mode, "passes": c.info()["passes"], "ms_per_grad_eval": ms, "energy": float(e.item()),
+           "peak": peak, "peak_source": f"{src} hbm_gbs"}
+    for k in ("tile_fwd", "tile_adj", "tc_block"):
         if k in prof and prof[k]["ms"] > 0:
             gbs = prof[k]["bytes"] / (prof[k]["ms"] / 1000.0) / 1e9
             out[k] = {"launches": prof[k]["launches"], "ms": prof[k]["ms"], "gbs": gbs, "frac": gbs / peak}
@@ -732,6 +736,11 @@ def main():
         del psi, lam
         torch.cuda.empty_cache()
         qft = qft_bench(S, torch, dev, args.qft_n, barrier)
+        # the same workload planned with tensor-core blocks: which passes and
+        # tensor-core launches that plan makes, and its time
+        t = qft_bench(S, torch, dev, args.qft_n, barrier, mode="tc")
+        qft["tc_plan"] = {"passes": t["passes"], "tc_block_launches": t.get("tc_block", {}).get("launches", 0),
+                          "ms_per_grad_eval": t["ms_per_grad_eval"], "energy": t["energy"]}
         psi = S.State(n, torch.complex64, dev)
         lam = S.State(n, torch.complex64, dev)
 

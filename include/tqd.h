@@ -88,14 +88,20 @@ typedef enum {
     TQD_PLAN_PLAIN = 0, /* one full-state sweep per gate (gate-by-gate path) */
     TQD_PLAN_FUSED = 1, /* fused passes: low-qubit and mixed tiles, diagonal runs */
     TQD_PLAN_TC = 2     /* as FUSED, and runs of >= 16 gates on qubits 0..5 become one fused
-                           64 x 64 unitary applied on the tensor cores (complex64 forward;
-                           split-precision TF32 products) */
+                           64 x 64 unitary applied on the tensor cores (complex64, split-
+                           precision TF32 products): in the forward pass, and in the reverse
+                           sweep when the block's gates are fixed (no angle: un-applying it is
+                           one product with U^dagger per state; a block with angles is
+                           un-applied by a tile pass, which also takes its derivatives) */
 } tqd_plan_mode;
 
 typedef struct {
     uint32_t mode;        /* tqd_plan_mode */
-    uint32_t tile_qubits; /* fused tiles hold 2^tile_qubits amplitudes; 0 = default */
-    uint32_t low_qubits;  /* contiguous low qubits in every mixed tile; 0 = default */
+    uint32_t tile_qubits; /* fused tiles hold 2^tile_qubits amplitudes: 0 or 12, the width the
+                             tile kernels are laid out for (16 amplitudes in registers x 256
+                             threads); other values are TQD_ERR_INVALID_ARG */
+    uint32_t low_qubits;  /* contiguous low qubits in every tile (128-byte runs of complex64):
+                             0 or 4; other values are TQD_ERR_INVALID_ARG */
     uint32_t buffers;     /* tile buffers in the fused passes: 1 = each block loads, computes and
                              stores one tile at a time; 2 = each block loads its next tile while
                              the current one is computed (twice the shared memory); 3 = ring:

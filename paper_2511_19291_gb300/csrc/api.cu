@@ -167,6 +167,11 @@ static tqd_status validate_circuit(int n_qubits, const tqd_gate *gates, size_t n
                   "tqd_circuit_create: unknown plan mode");
         CHECK_ARG(o.buffers <= 4, "tqd_circuit_create: buffers %u not in {0, ..., 4}", o.buffers);
         CHECK_ARG(o.jit <= 2, "tqd_circuit_create: jit %u not in {0, 1, 2}", o.jit);
+        CHECK_ARG(o.tile_qubits == 0 || o.tile_qubits == (uint32_t)tqd::TILE_K,
+                  "tqd_circuit_create: tile_qubits %u not in {0, %d} (the tile kernels hold 2^%d amplitudes)",
+                  o.tile_qubits, tqd::TILE_K, tqd::TILE_K);
+        CHECK_ARG(o.low_qubits == 0 || o.low_qubits == (uint32_t)tqd::TILE_LOW,
+                  "tqd_circuit_create: low_qubits %u not in {0, %d}", o.low_qubits, tqd::TILE_LOW);
         CHECK_ARG(o.reserved[0] == 0, "tqd_circuit_create: reserved opts not zero");
     }
     std::vector<GateH> &gs = *gs_out;

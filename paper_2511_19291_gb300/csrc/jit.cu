@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "jit.h"
+#include "tc.h"
 #include "plan.h"
 #include "prof.h"
 #include "tile.h"
@@ -616,7 +617,8 @@ static cudaError_t prepare(const tqd_circuit *c, int dt, bool adj, bool ring, bo
     {
         std::lock_guard<std::mutex> lk(g_cache_mu);
         for (int p = 0; p < np; ++p) {
-            if (!adj && dt == 0 && c->tile_passes[p].tc >= 0) continue;  // forward runs on the tensor cores
+            // forward (and, for fixed gates, reverse) runs on the tensor cores
+            if (dt == 0 && (adj ? tc_reverse_pass(c->tile_passes[p]) : c->tile_passes[p].tc >= 0)) continue;
             srcs[p] = jit_source(c, p, dt, adj, ring, tmaw, psi_ro);
             if (g_cache.count({dev, srcs[p]}) || first.count(srcs[p])) continue;
             first[srcs[p]] = p;

@@ -41,13 +41,23 @@ constexpr int TC_SMEM = (TC_NB + TC_NLO) * TC_B_BYTES + 1024 + 256;
 __device__ __forceinline__ uint32_t tc_sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (10 stored mantissa bits; ties away from
+// zero): half a TF32 unit in the last place added to the magnitude's bits,
+// then the 13 low bits cleared.  The operand U~'s hi half uses it, so that its
+// lo half has either sign and the split's error does not lean one way (the
+// state's halves are split by truncation, as the tensor core reads a float).
+__device__ __forceinline__ float tf32_rn(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
 
 // ------------------------------------------------------------- block prep
 // One block: thread c builds column c of U by applying the block's gates to
 // e_c in FP64, then writes U~ row-major (row m, column k at m * 128 + k) as
-// TF32 hi / lo halves.
+// TF32 hi / lo halves.  adj: the embedding of U^dagger instead (the reverse
+// sweep's x = U^dagger y, Sec. 4.4): row c of U^dagger is the conjugate of
+// column c of U, so thread c writes rows 2c and 2c + 1.
 __global__ void k_tc_prep(const TcGate *__restrict__ gates, int ng, const double *__restrict__ mats64,
-                          float *__restrict__ a_hi, float *__restrict__ a_lo) {
+                          float *__restrict__ a_hi, float *__restrict__ a_lo, int adj) {
     extern __shared__ double2 col[];  // [64 amplitudes][64 columns]: thread c owns column c
     const int c = threadIdx.x;        // 64 threads
 #define V(r) col[(r) * 64 + c]
@@ -82,14 +92,16 @@ __global__ void k_tc_prep(const TcGate *__restrict__ gates, int ng, const double
             }
         }
     }
-    // U[r][c] = v[r]; the four real entries of each complex entry
+    // U[r][c] = v[r]; the four real entries of each complex entry (of
+    // U^dagger[c][r] = conj(v[r]) when adj)
     for (int r = 0; r < 64; ++r) {
-        const double re = V(r).x, im = V(r).y;
-        const double e[4] = {re, -im, im, re};  // (2r,2c) (2r,2c+1) (2r+1,2c) (2r+1,2c+1)
-        const int rows[4] = {2 * r, 2 * r, 2 * r + 1, 2 * r + 1};
-        const int ks[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
+        const double re = V(r).x, im = adj ? -V(r).y : V(r).y;
+        const int i = adj ? c : r, j = adj ? r : c;  // the entry's row and column
+        const double e[4] = {re, -im, im, re};  // (2i,2j) (2i,2j+1) (2i+1,2j) (2i+1,2j+1)
+        const int rows[4] = {2 * i, 2 * i, 2 * i + 1, 2 * i + 1};
+        const int ks[4] = {2 * j, 2 * j + 1, 2 * j, 2 * j + 1};
         for (int q = 0; q < 4; ++q) {
-            const float hi = tf32_hi((float)e[q]);
+            const float hi = tf32_rn((float)e[q]);
             const float lo = (float)(e[q] - (double)hi);
             a_hi[rows[q] * TC_K + ks[q]] = hi;
             a_lo[rows[q] * TC_K + ks[q]] = lo;
@@ -383,6 +395,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------- host
+static cudaError_t tc_apply_state(tqd_state *psi, const tqd_circuit *c, const TcBlock &blk, cudaStream_t s);
+
 static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
     static std::once_flag once;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -397,8 +411,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
     return fn;
 }
 
-cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock &blk, cudaStream_t s) {
+cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock &blk, cudaStream_t s, bool adj,
+                            tqd_state *second) {
     if (psi->dtype != TQD_C64 || psi->n < 6) return cudaErrorInvalidValue;
+    if (second && (second->dtype != TQD_C64 || second->n != psi->n)) return cudaErrorInvalidValue;
     cudaError_t e;
     static std::once_flag prep_once;
     std::call_once(prep_once, [] {
@@ -406,9 +422,17 @@ cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock 
     });
     {
         ProfScope ps(PK_PREP, 0.0, s);
-        k_tc_prep<<<1, 64, 64 * 64 * sizeof(double2), s>>>(blk.d_gates, blk.n_gates, c->d_mats64, blk.d_ahi, blk.d_alo);
+        k_tc_prep<<<1, 64, 64 * 64 * sizeof(double2), s>>>(blk.d_gates, blk.n_gates, c->d_mats64, blk.d_ahi, blk.d_alo,
+                                                           adj ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    e = tc_apply_state(psi, c, blk, s);
+    if (e == cudaSuccess && second) e = tc_apply_state(second, c, blk, s);
+    return e;
+}
+
+// U~ (as last prepared) applied to every 64-amplitude column of one state.
+static cudaError_t tc_apply_state(tqd_state *psi, const tqd_circuit *c, const TcBlock &blk, cudaStream_t s) {
     auto fn = tc_encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const uint64_t cols = ((uint64_t)1 << psi->n) / 64;

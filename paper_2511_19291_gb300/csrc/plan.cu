@@ -283,7 +283,16 @@ cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, c
         const int np = pass_end < 0 ? (int)c->tile_passes.size() : pass_end;
         const int first = use_ck ? np - ck->count : np;
         for (int p = np - 1; p >= 0; --p) {
-            e = p >= first ? launch_tile_pass(psi, lam, c, p, s, ck->at(p - first)) : launch_tile_pass(psi, lam, c, p, s);
+            const TilePlanPass &pp = c->tile_passes[p];
+            if (psi->dtype == TQD_C64 && tc_reverse_pass(pp)) {
+                // no derivative to take: lambda <- U^dagger lambda on the tensor
+                // cores, and psi too unless it is read from a checkpoint
+                const TcBlock &b = *(const TcBlock *)c->tc_blocks[pp.tc];
+                e = p >= first ? launch_tc_block(lam, c, b, s, true) : launch_tc_block(psi, c, b, s, true, lam);
+            } else {
+                e = p >= first ? launch_tile_pass(psi, lam, c, p, s, ck->at(p - first))
+                               : launch_tile_pass(psi, lam, c, p, s);
+            }
             if (e != cudaSuccess) return e;
         }
         return launch_grad_finalize(c, tile_grid(c, psi->dtype == TQD_C64 ? 0 : 1, true), dev_grads, s);

@@ -23,8 +23,15 @@ struct TcBlock {
     float *d_alo;
 };
 
-// Builds the block's fused unitary from the current angles and applies it to
-// every 64-amplitude column of psi (complex64, n >= 12).
-cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock &blk, cudaStream_t s);
+// Builds the block's fused unitary U from the current angles (U^dagger when
+// adj) and applies it to every 64-amplitude column of psi (complex64,
+// n >= 12), then of `second` when given (the reverse sweep's lambda).
+cudaError_t launch_tc_block(tqd_state *psi, const tqd_circuit *c, const TcBlock &blk, cudaStream_t s,
+                            bool adj = false, tqd_state *second = nullptr);
+
+// A pass the reverse sweep runs on the tensor cores: a tensor-core block with
+// no angle derivative to take (its gates are fixed), so un-applying it is one
+// product with U^dagger per state.
+inline bool tc_reverse_pass(const TilePlanPass &p) { return p.tc >= 0 && p.dev[0].h.n_grad == 0; }
 
 }  // namespace tqd

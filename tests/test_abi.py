@@ -67,6 +67,27 @@ def test_circuit_validation(lib, specs, n, n_params, needle):
     assert not h.value
 
 
+@pytest.mark.parametrize("field,value,needle", [
+    ("tile_qubits", 10, b"tile_qubits 10"),
+    ("low_qubits", 3, b"low_qubits 3"),
+    ("buffers", 5, b"buffers 5"),
+    ("jit", 3, b"jit 3"),
+    ("mode", 7, b"unknown plan mode"),
+])
+def test_plan_option_validation(lib, field, value, needle):
+    """Plan options outside what the kernels implement are rejected on the
+    host, before any device work (the tile width is fixed at 12 qubits)."""
+    arr = make_gates([("RY", [0], 0)])
+    opts = _lib.PlanOpts()
+    opts.mode = _lib.PLAN_FUSED
+    setattr(opts, field, value)
+    h = C.c_void_p()
+    st = lib.tqd_circuit_create(14, C.cast(arr, C.c_void_p), 1, 1, None, 0, C.byref(opts), C.byref(h))
+    assert st == 1, st
+    assert needle in lib.tqd_last_error()
+    assert not h.value
+
+
 def test_wrong_arity_and_qubit_range(lib):
     arr = make_gates([("RY", [0], -1)])
     arr[0].nwires = 2

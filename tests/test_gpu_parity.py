@@ -596,6 +596,76 @@ def test_value_and_grad_checkpoints_tensor_core():
     assert back[0] == 1 and np.count_nonzero(back) == 1
 
 
+def tc_fixed_circuit(seed, n, blocks):
+    """As tc_circuit, but every block is 40 fixed gates (no angle) on qubits
+    0..5: the reverse sweep then un-applies each block on the tensor cores."""
+    rng = W.SplitMix64(seed)
+    gates, n_params = [], 0
+    for _ in range(blocks):
+        c6, _ = W.random_circuit(rng, 6, 40, n_params=1, fixed_fraction=1.0)
+        gates.extend(c6.gates)
+        for q in range(6, n):
+            gates.append(W.Gate("RY", (q,), param=n_params))
+            n_params += 1
+        gates.append(W.Gate("CNOT", (5, 6)))
+        gates.append(W.Gate("CNOT", (n - 1, 0)))
+    return W.Circuit(n, gates, n_params), rng.angles(n_params)
+
+
+@pytest.mark.parametrize("checkpoints", [None, 0])
+def test_reverse_sweep_tensor_core_fixed_blocks(checkpoints):
+    """Blocks of fixed gates have no angle derivative, so the reverse sweep
+    un-applies them as x = U^dagger y (Sec. 4.4) with one tensor-core product
+    per state: lambda only when psi comes from a forward checkpoint, psi and
+    lambda when psi is recomputed in place.  E and the gradient against the
+    oracle's parameter shift, psi restored, and the launch count of the
+    tensor-core kernel."""
+    S = sim()
+    n, blocks = 14, 3
+    circ, params = tc_fixed_circuit(8200, n, blocks)
+    terms = W.ising(n) + W.random_pauli_terms(W.SplitMix64(9), n, 4)
+    e_ref, g_ref = oracle.grad_stored(circ, params, terms)
+    c = S.Circuit(circ, mode="tc", checkpoints=checkpoints)
+
+    def tc_launches(run):
+        S.profile_enable(True)
+        out = run()
+        torch.cuda.synchronize()
+        prof = {q["name"]: q for q in S.profile_read()}
+        S.profile_enable(False)
+        return out, prof.get("tc_block", {}).get("launches", 0)
+
+    psi = S.State(n, torch.complex64).reset(0)
+    _, n_blocks = tc_launches(lambda: S.apply(psi, c, params_tensor(params)))
+    assert n_blocks >= 1
+    psi.reset(0)
+    lam = S.State(n, torch.complex64)
+    (e, g), launches = tc_launches(lambda: S.value_and_grad(psi, lam, c, params_tensor(params), terms))
+    # forward: one launch per block; reverse: lambda, and psi without checkpoints
+    assert launches == n_blocks * (2 if checkpoints is None else 3), (launches, n_blocks)
+    assert abs(e.item() - e_ref) < 1e-5
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4)
+    assert ok, worst
+    # psi back at e_0: the amplitude bar of the tensor-core forward test for
+    # the 2 x ng gates of the round trip, twice (the reverse sweep's rounding
+    # adds to the forward's rather than cancelling it)
+    bar = 2 * AMP_TOL["c64"] * math.sqrt(2 * len(circ.gates) / 100 + 1)
+    e0 = np.zeros(2 ** n, dtype=np.complex128)
+    e0[0] = 1
+    err = float(np.max(np.abs(to_numpy(psi) - e0)))
+    # tqd_backward over the same plan: psi_L in, psi_0 back, the same gradient
+    st, c2, p = gpu_state(circ, params, "tc", "c64")
+    lam2 = S.State(n, torch.complex64)
+    g2 = torch.zeros(circ.n_params, dtype=torch.float64, device="cuda")
+    S.backward(st, lam2, c2, p, terms, g2)
+    ok, worst = grad_close(g2.cpu().numpy(), g_ref, 1e-4)
+    assert ok, worst
+    err2 = float(np.max(np.abs(to_numpy(st) - e0)))
+    print(f"\ntensor-core reverse, {n_blocks} blocks: psi restored to {err:.2e} (value_and_grad), "
+          f"{err2:.2e} (backward); bar {bar:.2e}")
+    assert err <= bar and err2 <= bar, (err, err2, bar)
+
+
 @pytest.mark.parametrize("nq,dtype", [(6, "c128"), (12, "c64")])
 def test_main_example_ladder_encoder_batch(nq, dtype):
     """The appendix's main example: a batch of 16 inputs x[b, i] fed to RY
