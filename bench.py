@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=512, help="circuits of the batched measurement (0 = skip)")
     ap.add_argument("--tc-gates", type=int, default=200, help="gates of the tensor-core block measurement (0 = skip)")
     ap.add_argument("--qft-n", type=int, default=32, help="qubits of the QFT + ansatz measurement (0 = skip)")
+    ap.add_argument("--small", type=int, default=1, choices=(0, 1),
+                    help="time the 12-qubit, 4-layer workload's forward and gradient evaluations (0 = skip)")
     ap.add_argument("--forward-expval", type=int, default=1, choices=[0, 1],
                     help="time the workload's forward evaluation with E = <H> alone, fused and gate by gate (0 = skip)")
     ap.add_argument("--grad-fn", type=int, default=1, choices=[0, 1],
@@ -496,6 +498,120 @@ def forward_expval_bench(S, torch, dev, w, barrier, reps=5):
     return out
 
 
+def small_bench(S, torch, dev, barrier, reps=200):
+    """The small workload (12 qubits, 4 layers, 96 angles, sum_i Z_i: one
+    2^12-amplitude tile, so launch- and latency-bound): time per forward
+    evaluation (reset, circuit, tqd_expval) and per gradient evaluation
+    (tqd_value_and_grad), each over `reps` back-to-back calls, and both results
+    against the stored oracle values (tests/golden/hea12x4_sumz_grad.json)."""
+    import numpy as np
+    from paper_2511_19291_gb300 import workloads as W
+    w = W.workload_small()
+    n = w.circuit.n_qubits
+    c = S.Circuit(w.circuit, device=dev)
+    obs = S.Observable(w.terms)
+    params = torch.tensor(w.params, dtype=torch.float64, device=dev)
+    psi = S.State(n, torch.complex64, dev)
+    lam = S.State(n, torch.complex64, dev)
+    e = torch.zeros((), dtype=torch.float64, device=dev)
+    eg = torch.zeros((), dtype=torch.float64, device=dev)
+    g = torch.zeros(w.circuit.n_params, dtype=torch.float64, device=dev)
+
+    def fwd():
+        psi.reset(0)
+        S.apply(psi, c, params)
+        S.expval(psi, obs, out=e)
+
+    def grad():
+        psi.reset(0)
+        S.value_and_grad(psi, lam, c, params, obs, eg, g)
+
+    out = {"workload": w.name, "n_qubits": n, "layers": 4, "n_params": w.circuit.n_params,
+           "observable": "sum_i Z_i", "reps": reps}
+    for name, fn in (("forward", fwd), ("gradient", grad)):
+        for _ in range(3):
+            fn()
+        barrier()
+        S.profile_enable(True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        launches = sum(p["launches"] for p in S.profile_read())
+        S.profile_enable(False)
+        out[name] = {"us_per_eval": a.elapsed_time(b) * 1000.0 / reps, "launches_per_eval": launches / reps}
+        out[name]["api_calls"] = "through the Python binding, one library call after another (host-bound)"
+    # the same calls captured once into a CUDA graph (the circuit's matrices are
+    # built on the device from the angles, so the graph stays valid), replayed
+    for name, fn in (("forward", fwd), ("gradient", grad)):
+        per = 50
+        try:
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(side):
+                fn()
+            torch.cuda.current_stream(dev).wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                for _ in range(per):
+                    fn()
+            graph.replay()
+            barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps // per):
+                graph.replay()
+            b.record()
+            torch.cuda.synchronize(dev)
+            out[name]["graph_us_per_eval"] = a.elapsed_time(b) * 1000.0 / ((reps // per) * per)
+            del graph
+        except Exception as ex:  # a call that cannot be captured: report it
+            out[name]["graph_us_per_eval"] = None
+            out[name]["graph_error"] = str(ex)[:200]
+    # the batch path with this one circuit: the whole circuit in one block's
+    # shared memory, forward + E + gradient in one graph launch
+    try:
+        bt = S.Batch([c], [w.terms])
+        bt.set_params([w.params])
+        bt.run()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            bt.run()
+        b.record()
+        torch.cuda.synchronize(dev)
+        out["batch_one_circuit"] = {"us_per_grad_eval": a.elapsed_time(b) * 1000.0 / reps,
+                                    "energy": float(bt.energies[0].item()), **{k: v for k, v in bt.info().items()
+                                                                              if k != "tiling"}}
+        del bt
+    except Exception as ex:
+        out["batch_one_circuit"] = {"error": str(ex)[:200]}
+    # one clean gradient evaluation (g accumulates) for the error statement
+    g.zero_()
+    grad()
+    e_f, e_g, g_h = float(e.item()), float(eg.item()), g.cpu().numpy()
+    path = os.path.join(ROOT, "tests", "golden", "hea12x4_sumz_grad.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            ref = json.load(f)
+        g_ref = np.array(ref["grad"])
+        out["error"] = {"reference": "complex128 oracle, tests/golden/hea12x4_sumz_grad.json (E and every "
+                                     "dE/dtheta by parameter shift)",
+                        "energy_forward_abs_err": abs(e_f - ref["energy"]),
+                        "energy_grad_eval_abs_err": abs(e_g - ref["energy"]),
+                        "grad_max_abs_err": float(np.max(np.abs(g_h - g_ref))),
+                        "grad_norm_rel_err": float(np.max(np.abs(g_h - g_ref)) / np.max(np.abs(g_ref)))}
+    del psi, lam, c
+    torch.cuda.empty_cache()
+    return out
+
+
 def tc_bench(S, torch, dev, n, n_gates, barrier, reps=5):
     """One run of `n_gates` gates on qubits 0..5 of an n-qubit complex64 state:
     the fused 64 x 64 block on the tensor cores against the same gates in one
@@ -731,6 +847,8 @@ def main():
 
     fwd_e = forward_expval_bench(S, torch, dev, w, barrier) if args.forward_expval else None
 
+    small = small_bench(S, torch, dev, barrier) if args.small else None
+
     qft = None
     if args.qft_n > 0:
         del psi, lam
@@ -808,6 +926,7 @@ def main():
         "grad24": grad_fn,
         "forward_expval": fwd_e,
         "qft32": qft,
+        "small12": small,
         "clocks": clk.summary(),
         "kernels": kernels,
         "energy": e_step,

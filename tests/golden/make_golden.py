@@ -16,6 +16,9 @@ Files (all under ``tests/golden/``):
   seed index 3): E and the same kind of sample.
 * ``hea20x10_ising_grad.json`` -- the same family at 20 qubits, 10 layers
   (400 angles, seed index 3): E and the whole parameter-shift gradient.
+* ``hea12x4_sumz_grad.json`` -- the small workload: 12 qubits, 4 layers (96
+  angles, seed index 1) with the observable sum_i Z_i: E and the whole
+  parameter-shift gradient.
 
 Each evaluation is one gate-by-gate oracle run (Sec. 4.1, Algorithm 1)
 followed by the oracle's expectation value (Sec. 2.2.1); the derivatives use
@@ -78,6 +81,8 @@ def _workload(W, name):
         return W.workload_grad()
     if name == "hea20x10_ising":
         return W.workload_hea(3, 20, 10, "ising")
+    if name == "hea12x4_sumz":
+        return W.workload_small()
     raise KeyError(name)
 
 
@@ -85,7 +90,8 @@ def _describe(W, name):
     wl = _workload(W, name)
     c = wl.circuit
     return {"workload": wl.name, "n_qubits": c.n_qubits, "gates": len(c.gates), "n_params": c.n_params,
-            "observable": "open-chain Ising: sum_i Z_i Z_{i+1} + 0.5 sum_i X_i",
+            "observable": ("sum_i Z_i" if name.endswith("sumz")
+                           else "open-chain Ising: sum_i Z_i Z_{i+1} + 0.5 sum_i X_i"),
             "terms": len(wl.terms)}
 
 
@@ -155,18 +161,18 @@ def main() -> None:
         procs = max(1, min(procs, int(avail_gb // 2.5)))
     except (ValueError, OSError):
         pass
-    todo = [a.only] if a.only else ["hea20x10_ising", "hea24x10_ising", "hea26x20_ising"]
+    todo = [a.only] if a.only else ["hea12x4_sumz", "hea20x10_ising", "hea24x10_ising", "hea26x20_ising"]
     for name in todo:
         t0 = time.time()
         print(f"{name}: {procs} processes", flush=True)
-        if name == "hea20x10_ising":
+        if name in ("hea20x10_ising", "hea12x4_sumz"):
             data = full_gradient(name)
         elif name == "hea24x10_ising":
             data = sampled(name, 24, 10, procs)
         else:
             data = sampled(name, 26, 20, procs)
         data["script"] = "python tests/golden/make_golden.py --only " + name
-        write(name + ("_grad" if name == "hea20x10_ising" else ""), data)
+        write(name + ("_grad" if name in ("hea20x10_ising", "hea12x4_sumz") else ""), data)
         print(f"{name}: {time.time() - t0:.0f} s", flush=True)
 
 

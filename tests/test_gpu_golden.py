@@ -95,3 +95,26 @@ def test_grad_workload_form_20q_full_gradient_against_oracle():
     assert abs(e - ref["energy"]) <= E_TOL["c64"]
     ok, worst = grad_close(g, g_ref, G_REL["c64"])
     assert ok, worst
+
+
+def test_small_workload_12q_against_oracle():
+    """12 qubits, 4 layers, sum_i Z_i (one tile: the launch-bound end of the
+    range): the forward evaluation's E through tqd_expval and the whole
+    gradient through tqd_value_and_grad against the oracle's stored values."""
+    S = sim()
+    ref = load("hea12x4_sumz_grad.json")
+    w = W.workload_small()
+    assert ref["n_params"] == w.circuit.n_params
+    c = S.Circuit(w.circuit)
+    st = S.State(12, torch.complex64).reset(0)
+    S.apply(st, c, params_tensor(w.params))
+    e_fwd = S.expval(st, w.terms).item()
+    e, g = value_and_grad_c64(w)
+    g_ref = np.array(ref["grad"])
+    err = grad_error(g, g_ref)
+    print(f"\n12q: |E - E_oracle| = {abs(e_fwd - ref['energy']):.3e} (forward), {abs(e - ref['energy']):.3e} "
+          f"(value_and_grad); gradient max abs err {err['max_abs']:.3e}, max rel err {err['max_rel']:.3e}")
+    assert abs(e_fwd - ref["energy"]) <= E_TOL["c64"]
+    assert abs(e - ref["energy"]) <= E_TOL["c64"]
+    ok, worst = grad_close(g, g_ref, G_REL["c64"])
+    assert ok, worst
