@@ -221,36 +221,50 @@ uint16_t sync_level(const std::vector<std::array<uint32_t, 1 << TILE_R>> &a,
 
 }  // namespace
 
-bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L) {
-    // box bits start as all of Q; extras are taken from the top runs until the
-    // stricter (complex128, 3-bit inner dimension) layout has <= 5 dimensions.
-    std::vector<char> box(inQ);
-    L.extra.clear();
+// Box bits of a tile for a tensor map whose inner dimension holds the qubits
+// below `low`: all of Q, less the extras, taken from the top runs until the
+// map has <= 5 dimensions.  The extras are always Q's highest runs.
+static bool tile_box(int n, const std::vector<char> &inQ, int low, std::vector<char> &box, std::vector<int> &extra) {
+    box = inQ;
+    extra.clear();
     for (int iter = 0; iter < 16; ++iter) {
-        const std::vector<Seg> s128 = segments(box, TILE_LOW - 1, n);
-        const int dims = 1 + (int)s128.size();
+        const std::vector<Seg> s = segments(box, low, n);
+        const int dims = 1 + (int)s.size();
         if (dims <= TILE_MAX_DIMS) break;
         // move the highest in-run of the box to the extras
         int hi = -1;
-        for (int i = (int)s128.size() - 1; i >= 0; --i)
-            if (s128[i].in) { hi = i; break; }
+        for (int i = (int)s.size() - 1; i >= 0; --i)
+            if (s[i].in) { hi = i; break; }
         if (hi < 0) return false;
-        for (int b = s128[hi].lo; b < s128[hi].lo + s128[hi].len; ++b) {
+        for (int b = s[hi].lo; b < s[hi].lo + s[hi].len; ++b) {
             box[b] = 0;
-            L.extra.push_back(b);
+            extra.push_back(b);
         }
     }
-    std::sort(L.extra.begin(), L.extra.end());
-    if ((int)L.extra.size() > 4) return false;
-    // local order: box bits ascending, then extra bits ascending
+    std::sort(extra.begin(), extra.end());
+    return (int)extra.size() <= 4;
+}
+
+bool tile_layout(int n, const std::vector<char> &inQ, TileLayout &L) {
+    // Extras per precision: complex128's 3-bit inner dimension can need more
+    // dimensions than complex64's 4-bit one, so complex64 takes its own (a
+    // subset: both are Q's highest runs).  The local order is box bits
+    // ascending, then extra bits ascending; extras being the highest runs,
+    // that is Q ascending either way, so both precisions share it.
+    std::vector<char> box[2];
+    for (int dt = 0; dt < 2; ++dt)
+        if (!tile_box(n, inQ, dt == 0 ? TILE_LOW : TILE_LOW - 1, box[dt], L.extra_dt[dt])) return false;
+    L.extra = L.extra_dt[1];
     L.qubit_of_local.clear();
     for (int b = 0; b < n; ++b)
-        if (box[b]) L.qubit_of_local.push_back(b);
+        if (box[1][b]) L.qubit_of_local.push_back(b);
     for (int b : L.extra) L.qubit_of_local.push_back(b);
     if ((int)L.qubit_of_local.size() != TILE_K) return false;
+    for (size_t i = 1; i < L.qubit_of_local.size(); ++i)
+        if (L.qubit_of_local[i] <= L.qubit_of_local[i - 1]) return false;  // not Q ascending
     for (int dt = 0; dt < 2; ++dt) {
         const int low = dt == 0 ? TILE_LOW : TILE_LOW - 1;
-        const std::vector<Seg> s = segments(box, low, n);
+        const std::vector<Seg> s = segments(box[dt], low, n);
         L.rank[dt] = 1 + (int)s.size();
         if (L.rank[dt] > TILE_MAX_DIMS) return false;
         L.dim_lo[dt][0] = 0;
@@ -645,14 +659,14 @@ bool encode_tile_pass(const tqd_circuit *c, TilePlanPass &P) {
         memset(&D, 0, sizeof(D));
         D.h.n = n;
         D.h.n_tiles_log2 = n - TILE_K;
-        D.h.n_extra = (int)lay.extra.size();
+        D.h.n_extra = (int)lay.extra_dt[dt].size();
         D.h.rank = lay.rank[dt];
         for (int d = 0; d < TILE_MAX_DIMS; ++d) {
             D.h.dim_lo[d] = d < D.h.rank ? lay.dim_lo[dt][d] : 0;
             D.h.dim_len[d] = d < D.h.rank ? lay.dim_len[dt][d] : 0;
         }
         for (size_t i = 0; i < lay.out.size(); ++i) D.h.out_bits[i] = lay.out[i];
-        for (size_t i = 0; i < lay.extra.size(); ++i) D.h.extra_bits[i] = lay.extra[i];
+        for (size_t i = 0; i < lay.extra_dt[dt].size(); ++i) D.h.extra_bits[i] = lay.extra_dt[dt][i];
         D.h.n_stages = (int)stages.size();
         int pool = 0, ngrad = 0, nops = 0, nsubs = 0;
         D.h.n_dg = 0;

@@ -13,7 +13,9 @@ namespace tqd {
 // Host-side plan of one pass.
 struct TileLayout {
     std::vector<int> qubit_of_local;  // local bit -> qubit (box bits ascending, then extras)
-    std::vector<int> extra;           // Q qubits copied by separate TMA operations
+    std::vector<int> extra;           // Q qubits copied by separate TMA operations (complex128)
+    std::vector<int> extra_dt[2];     // the same per precision: complex64's wider inner dimension
+                                      // leaves fewer dimensions, so fewer (or no) separate copies
     std::vector<int> out;             // qubits outside Q, ascending
     int rank[2];                      // tensor-map rank for c64 / c128
     int dim_lo[2][TILE_MAX_DIMS];
