@@ -299,15 +299,21 @@ tqd_status tqd_expval_noalloc(const tqd_state *state, const tqd_pauli_term *term
  * E = <psi_L|H|psi_L> for H = sum_j coeff_j P_j written to dev_energy[0]
  * (device, FP64), and the adjoint gradient of E added to dev_grads (as
  * tqd_backward with unit weights and grad_scale 1); on return psi holds its
- * input state again and lambda holds U^dagger H psi_L.  E is read off
- * lambda = H psi_L as Re <psi_L|lambda>, the seed the reverse sweep needs
- * anyway (Sec. 2.2.1, Sec. 4.4), so no separate expectation pass runs; it
- * equals tqd_expval's value up to rounding.
+ * input state again and lambda holds the reverse sweep's adjoint state
+ * V^dagger H psi_L, where V is U less the fused passes before its first
+ * pass with an angle (V = U for the gate-by-gate plan, and whenever the
+ * first pass has an angle).  E is read off lambda = H psi_L as Re <psi_L|lambda>, the seed the
+ * reverse sweep needs anyway (Sec. 2.2.1, Sec. 4.4), so no separate
+ * expectation pass runs; it equals tqd_expval's value up to rounding.
  *
  * Fused plans keep forward checkpoints (tqd_plan_opts.checkpoints): the
  * states after the last K passes go to device memory the circuit owns, the
  * reverse sweep reads psi there, and psi itself is only read when K covers
- * every pass.  The first call for a state size allocates that memory
+ * every pass.  The reverse sweep ends at the first pass with an angle (the
+ * passes before it have no derivative to take, e.g. a QFT that prepares the
+ * ansatz's input); when some pass runs in place, one checkpoint slot then
+ * keeps a copy of the input state, copied back at the end, instead of a
+ * pass's output.  The first call for a state size allocates that memory
  * (cudaMemGetInfo, cudaMalloc): make it outside any stream capture.  Calls on
  * one circuit whose GPU work overlaps race on it (as on its gradient
  * partials). */

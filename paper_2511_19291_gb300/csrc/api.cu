@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -478,9 +479,19 @@ tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circu
     GUARD(psi->device);
     const cudaStream_t s = (cudaStream_t)stream;
     const bool tail = c->fused && c->prefix_passes < (int)c->tile_passes.size();
+    const int np = c->fused ? (tail ? c->prefix_passes : (int)c->tile_passes.size()) : 0;
+    // Passes before the first one with an angle have no derivative to take:
+    // the reverse sweep ends there.  psi is then restored from a copy of the
+    // input state kept in a checkpoint slot, when some pass runs in place.
+    const int lead = c->fused ? std::min(c->first_grad_pass, np) : 0;
     // forward checkpoints of the passes that run (the last ones that fit)
     Checkpoints ck;
-    CHECK_CUDA(checkpoints_for(c, psi, tail ? c->prefix_passes : (int)c->tile_passes.size(), &ck));
+    CHECK_CUDA(checkpoints_for(c, psi, np, &ck, lead > 0));
+    const bool in_place = np - ck.count > 0;
+    const int pass_begin = lead > 0 && (!in_place || ck.psi0) ? lead : 0;
+    const bool restore = pass_begin > 0 && in_place;
+    const size_t sb = ((size_t)1 << psi->n) * (psi->dtype == TQD_C64 ? 8 : 16);
+    if (restore) CHECK_CUDA(cudaMemcpyAsync(ck.psi0, psi->amps, sb, cudaMemcpyDeviceToDevice, s));
     if (tail) {
         // the circuit ends with a permutation P (its tail passes): E and its
         // gradient from psi' = U' psi (the gates before P) with
@@ -488,12 +499,13 @@ tqd_status tqd_value_and_grad(tqd_state *psi, tqd_state *lambda, const tqd_circu
         const std::vector<tqd_pauli_term> hp = conjugate_by_tail(c, terms, n_terms);
         CHECK_CUDA(run_forward(psi, c, dev_params, s, c->prefix_passes, &ck));
         CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(hp.data(), hp.size()), nullptr, 1.0,
-                                dev_grads, s, dev_energy, true, c->prefix_passes, false, &ck));
-        return TQD_OK;
+                                dev_grads, s, dev_energy, true, c->prefix_passes, false, &ck, pass_begin));
+    } else {
+        CHECK_CUDA(run_forward(psi, c, dev_params, s, -1, &ck));
+        CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(terms, n_terms), nullptr, 1.0, dev_grads, s,
+                                dev_energy, true, -1, false, &ck, pass_begin));
     }
-    CHECK_CUDA(run_forward(psi, c, dev_params, s, -1, &ck));
-    CHECK_CUDA(run_backward(psi, lambda, c, dev_params, group_terms(terms, n_terms), nullptr, 1.0, dev_grads, s,
-                            dev_energy, true, -1, false, &ck));
+    if (restore) CHECK_CUDA(cudaMemcpyAsync(psi->amps, ck.psi0, sb, cudaMemcpyDeviceToDevice, s));
     return TQD_OK;
 }
 

@@ -113,6 +113,7 @@ struct tqd_circuit {
     bool fused;                  // tile passes (n >= 12) instead of the gate-by-gate plan
     int prefix_passes;           // fused: passes of the gates before the permutation tail
     int tail_gate;               // fused: first gate of the permutation tail (gates.size(): none)
+    int first_grad_pass;         // fused: first pass with an angle (passes before it have none)
     std::vector<tqd::TilePlanPass> tile_passes;
     std::vector<void *> tc_blocks;   // tqd::TcBlock*, forward of passes whose gates all act on qubits 0..5
     tqd::TilePassDev *d_tile_desc;  // [pass][c64, c128] descriptors in device memory

@@ -66,6 +66,7 @@ tqd_status build_circuit(tqd_circuit *c) {
     c->fused = false;
     c->prefix_passes = 0;
     c->tail_gate = (int)c->gates.size();
+    c->first_grad_pass = 0;
 
     std::vector<std::vector<int>> by_param = assign_grad_slots(c);
     std::vector<int> ptr(c->n_params + 1, 0), slots;
@@ -147,6 +148,10 @@ tqd_status build_circuit(tqd_circuit *c) {
             c->tile_passes = std::move(passes);
             c->prefix_passes = prefix;
             c->tail_gate = permutation_tail(c);
+            c->first_grad_pass = 0;
+            while (c->first_grad_pass < (int)c->tile_passes.size() &&
+                   c->tile_passes[c->first_grad_pass].dev[0].h.n_grad == 0)
+                ++c->first_grad_pass;
             c->fused = true;
             c->n_passes = (int)c->tile_passes.size();
             c->launches_apply = c->n_passes + 1;
@@ -193,7 +198,7 @@ void release_circuit(tqd_circuit *c) {
     c->ck_bytes = c->ck_state_bytes = 0;
 }
 
-cudaError_t checkpoints_for(const tqd_circuit *c, const tqd_state *psi, int np, Checkpoints *out) {
+cudaError_t checkpoints_for(const tqd_circuit *c, const tqd_state *psi, int np, Checkpoints *out, bool want_psi0) {
     *out = Checkpoints();
     const uint32_t opt = c->opts.checkpoints;
     if (!c->fused || np <= 0 || opt == TQD_CHECKPOINTS_NONE) return cudaSuccess;
@@ -224,7 +229,13 @@ cudaError_t checkpoints_for(const tqd_circuit *c, const tqd_state *psi, int np, 
     }
     out->base = (char *)c->ck_buf;
     out->stride = sb;
-    out->count = (int)std::min<size_t>((size_t)want, c->ck_buf ? c->ck_bytes / sb : 0);
+    const int slots = c->ck_buf ? (int)(c->ck_bytes / sb) : 0;
+    out->count = std::min(want, slots);
+    if (want_psi0 && out->count < np && slots > 0) {
+        // some pass runs in place: the last slot keeps the input state
+        if (out->count == slots) --out->count;
+        out->psi0 = out->at(slots - 1);
+    }
     return cudaSuccess;
 }
 
@@ -268,7 +279,7 @@ cudaError_t run_forward(tqd_state *psi, const tqd_circuit *c, const double *dev_
 cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, const double *dev_params,
                          const std::vector<PauliGroup> &groups, const double *dev_weights, double scale,
                          double *dev_grads, cudaStream_t s, double *dev_energy, bool prepared, int pass_end,
-                         bool seeded, const Checkpoints *ck) {
+                         bool seeded, const Checkpoints *ck, int pass_begin) {
     cudaError_t e = prepared ? cudaSuccess : launch_prep(c, dev_params, s);
     if (e != cudaSuccess) return e;
     const bool use_ck = c->fused && ck && ck->count > 0;
@@ -282,7 +293,7 @@ cudaError_t run_backward(tqd_state *psi, tqd_state *lam, const tqd_circuit *c, c
     if (c->fused) {
         const int np = pass_end < 0 ? (int)c->tile_passes.size() : pass_end;
         const int first = use_ck ? np - ck->count : np;
-        for (int p = np - 1; p >= 0; --p) {
+        for (int p = np - 1; p >= pass_begin; --p) {
             const TilePlanPass &pp = c->tile_passes[p];
             if (psi->dtype == TQD_C64 && tc_reverse_pass(pp)) {
                 // no derivative to take: lambda <- U^dagger lambda on the tensor

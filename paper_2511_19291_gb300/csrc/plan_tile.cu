@@ -334,7 +334,10 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
         int qn = 0;
         for (int q = 0; q < TILE_LOW; ++q) { inQ[q] = 1; ++qn; }
         TileLayout lay;
-        auto try_add = [&](const int *ws, int cnt) {
+        // strict: refuse qubits whose padded set needs separate box copies in
+        // complex64 (such passes copy each tile as 2^e small boxes, several
+        // times slower than one box); the first gate's qubits are always taken
+        auto try_add = [&](const int *ws, int cnt, bool strict) {
             int newq = 0;
             for (int a = 0; a < cnt; ++a) newq += inQ[ws[a]] ? 0 : 1;
             if (newq == 0) return true;
@@ -352,6 +355,7 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
                 if (!pad[q]) { pad[q] = 1; ++have; }
             TileLayout tl;
             if (!tile_layout(n, pad, tl)) return false;
+            if (strict && !tl.extra_dt[0].empty()) return false;
             inQ.swap(t);
             qn += newq;
             return true;
@@ -362,12 +366,13 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
             ++scanned;
             const GateH &gh = c->gates[g];
             if (gate_diagonal(gh.kind)) continue;  // needs none of its qubits in Q
-            if (!try_add(gh.w, gh.nw) && g == first) break;
+            if (!try_add(gh.w, gh.nw, g != first) && g == first) break;
         }
-        // fill: qubits that extend an existing run first, then any
-        for (int pass2 = 0; pass2 < 2 && qn < TILE_K; ++pass2)
+        // fill: qubits that extend an existing run first, then any; without
+        // box copies if possible
+        for (int pass2 = 0; pass2 < 4 && qn < TILE_K; ++pass2)
             for (int q = TILE_LOW; q < n && qn < TILE_K; ++q)
-                if (!inQ[q] && (pass2 == 1 || inQ[q - 1] || (q + 1 < n && inQ[q + 1]))) try_add(&q, 1);
+                if (!inQ[q] && ((pass2 & 1) || inQ[q - 1] || (q + 1 < n && inQ[q + 1]))) try_add(&q, 1, pass2 < 2);
         if (qn < TILE_K || !tile_layout(n, inQ, lay)) return {};
         {
             const GateH &g0 = c->gates[first];

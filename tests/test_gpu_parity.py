@@ -572,6 +572,66 @@ def test_value_and_grad_checkpoints_ring(kw):
     np.testing.assert_allclose(out[5][1], out[0][1], atol=1e-5 * W.observable_l1(terms), rtol=0)
 
 
+def prefix_then_hea(n, rounds, layers, seed):
+    """An angle-free state preparation (rounds of H on every qubit, a CNOT
+    ring and a fixed controlled phase) that fills whole fused passes, then
+    the ansatz with the Ising observable."""
+    gates = []
+    for r in range(rounds):
+        gates += [W.Gate("H", (q,)) for q in range(n)]
+        gates += [W.Gate("CNOT", (q, (q + 1) % n)) for q in range(n)]
+        gates.append(W.Gate("CPHASE", (0, n - 1), angle=0.3 + r))
+    h = W.hea_ansatz(n, layers)
+    circ = W.Circuit(n, gates + list(h.gates), h.n_params)
+    return W.Workload(f"prefix+hea n={n}", circ, W.config_rng(seed).angles(h.n_params), W.ising(n))
+
+
+@pytest.mark.parametrize("checkpoints", [None, 0, 1, 2])
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_value_and_grad_angle_free_prefix(checkpoints, dtype):
+    """A prefix without angles (it fills the first fused pass), then the
+    ansatz: the reverse sweep of tqd_value_and_grad ends at the first pass
+    with an angle (Sec. 4.4: the gradient needs lambda and psi only where an
+    angle acts).  psi comes back as the input state: untouched when every
+    pass is checkpointed, else from a copy kept in a checkpoint slot
+    (checkpoints 1: every pass in place; 2: one checkpoint and the copy);
+    checkpoints 0 (none) keeps the whole sweep.  E and the gradient against
+    the oracle, psi restored, and the number of reverse passes."""
+    S = sim()
+    n = 14
+    w = prefix_then_hea(n, 2, 2, 31)
+    e_ref, g_ref = oracle.grad_stored(w.circuit, w.params, w.terms)
+    c = S.Circuit(w.circuit, checkpoints=checkpoints)
+    full = S.Circuit(w.circuit, checkpoints=0)
+    psi = S.State(n, DTYPES[dtype]).reset(0)
+    lam = S.State(n, DTYPES[dtype])
+    S.profile_enable(True)
+    e_full, g_full = S.value_and_grad(psi, lam, full, params_tensor(w.params), w.terms)
+    torch.cuda.synchronize()
+    adj_full = {q["name"]: q for q in S.profile_read()}.get("tile_adj", {}).get("launches", 0)
+    psi.reset(0)
+    e, g = S.value_and_grad(psi, lam, c, params_tensor(w.params), w.terms)
+    torch.cuda.synchronize()
+    adj = {q["name"]: q for q in S.profile_read()}.get("tile_adj", {}).get("launches", 0)
+    S.profile_enable(False)
+    assert adj_full >= 1
+    if checkpoints == 0:
+        assert adj == adj_full
+    else:
+        assert 1 <= adj < adj_full, (adj, adj_full)  # the QFT's passes are not un-applied
+    assert abs(e.item() - e_ref) <= E_TOL[dtype]
+    ok, worst = grad_close(g.cpu().numpy(), g_ref, G_REL[dtype])
+    assert ok, worst
+    # the same passes take the derivatives either way (psi from a checkpoint
+    # or recomputed in place: rounding only)
+    ok, worst = grad_close(g.cpu().numpy(), g_full.cpu().numpy(), G_REL[dtype])
+    assert ok, worst
+    e0 = np.zeros(2 ** n, dtype=np.complex128)
+    e0[0] = 1
+    back = np.max(np.abs(to_numpy(psi) - e0))
+    assert back <= (1e-12 if dtype == "c128" else AMP_TOL["c64"] * math.sqrt(2 * len(w.circuit.gates) / 100 + 1)), back
+
+
 def test_value_and_grad_checkpoints_tensor_core():
     """Forward passes on the tensor cores write their checkpoint through a copy
     of the previous state (the kernel works in place)."""
@@ -598,7 +658,9 @@ def test_value_and_grad_checkpoints_tensor_core():
 
 def tc_fixed_circuit(seed, n, blocks):
     """As tc_circuit, but every block is 40 fixed gates (no angle) on qubits
-    0..5: the reverse sweep then un-applies each block on the tensor cores."""
+    0..5: the reverse sweep then un-applies each block on the tensor cores
+    (tqd_value_and_grad's sweep ends at the first pass with an angle, so it
+    does not reach the first block)."""
     rng = W.SplitMix64(seed)
     gates, n_params = [], 0
     for _ in range(blocks):
@@ -641,8 +703,12 @@ def test_reverse_sweep_tensor_core_fixed_blocks(checkpoints):
     psi.reset(0)
     lam = S.State(n, torch.complex64)
     (e, g), launches = tc_launches(lambda: S.value_and_grad(psi, lam, c, params_tensor(params), terms))
-    # forward: one launch per block; reverse: lambda, and psi without checkpoints
-    assert launches == n_blocks * (2 if checkpoints is None else 3), (launches, n_blocks)
+    # forward: one launch per block; reverse: every block but the first (the
+    # circuit opens with it: no angle before it, so the sweep ends there) on
+    # lambda when psi comes from checkpoints; without checkpoints the whole
+    # sweep runs, on psi and lambda
+    want = 2 * n_blocks - 1 if checkpoints is None else 3 * n_blocks
+    assert launches == want, (launches, n_blocks)
     assert abs(e.item() - e_ref) < 1e-5
     ok, worst = grad_close(g.cpu().numpy(), g_ref, 1e-4)
     assert ok, worst
@@ -657,7 +723,8 @@ def test_reverse_sweep_tensor_core_fixed_blocks(checkpoints):
     st, c2, p = gpu_state(circ, params, "tc", "c64")
     lam2 = S.State(n, torch.complex64)
     g2 = torch.zeros(circ.n_params, dtype=torch.float64, device="cuda")
-    S.backward(st, lam2, c2, p, terms, g2)
+    _, back_launches = tc_launches(lambda: S.backward(st, lam2, c2, p, terms, g2))
+    assert back_launches == 2 * n_blocks  # tqd_backward un-applies every block, on psi and lambda
     ok, worst = grad_close(g2.cpu().numpy(), g_ref, 1e-4)
     assert ok, worst
     err2 = float(np.max(np.abs(to_numpy(st) - e0)))
