@@ -545,8 +545,24 @@ def small_bench(S, torch, dev, barrier, reps=200):
         out[name] = {"us_per_eval": a.elapsed_time(b) * 1000.0 / reps, "launches_per_eval": launches / reps}
         out[name]["api_calls"] = "through the Python binding, one library call after another (host-bound)"
     # the same calls captured once into a CUDA graph (the circuit's matrices are
-    # built on the device from the angles, so the graph stays valid), replayed
-    for name, fn in (("forward", fwd), ("gradient", grad)):
+    # built on the device from the angles, so the graph stays valid), replayed;
+    # then with the pass-specialised kernels (compiled at run time; by default
+    # they serve states of 22 qubits and more)
+    cs = S.Circuit(w.circuit, device=dev, jit=2)
+
+    def fwd_s():
+        psi.reset(0)
+        S.apply(psi, cs, params)
+        S.expval(psi, obs, out=e)
+
+    def grad_s():
+        psi.reset(0)
+        S.value_and_grad(psi, lam, cs, params, obs, eg, g)
+
+    out["passes"] = c.info()["passes"]
+    for name, fn, key in (("forward", fwd, "graph_us_per_eval"), ("gradient", grad, "graph_us_per_eval"),
+                          ("forward", fwd_s, "graph_specialised_us_per_eval"),
+                          ("gradient", grad_s, "graph_specialised_us_per_eval")):
         per = 50
         try:
             side = torch.cuda.Stream(dev)
@@ -567,10 +583,10 @@ def small_bench(S, torch, dev, barrier, reps=200):
                 graph.replay()
             b.record()
             torch.cuda.synchronize(dev)
-            out[name]["graph_us_per_eval"] = a.elapsed_time(b) * 1000.0 / ((reps // per) * per)
+            out[name][key] = a.elapsed_time(b) * 1000.0 / ((reps // per) * per)
             del graph
         except Exception as ex:  # a call that cannot be captured: report it
-            out[name]["graph_us_per_eval"] = None
+            out[name][key] = None
             out[name]["graph_error"] = str(ex)[:200]
     # the batch path with this one circuit: the whole circuit in one block's
     # shared memory, forward + E + gradient in one graph launch
@@ -607,7 +623,7 @@ def small_bench(S, torch, dev, barrier, reps=200):
                         "energy_grad_eval_abs_err": abs(e_g - ref["energy"]),
                         "grad_max_abs_err": float(np.max(np.abs(g_h - g_ref))),
                         "grad_norm_rel_err": float(np.max(np.abs(g_h - g_ref)) / np.max(np.abs(g_ref)))}
-    del psi, lam, c
+    del psi, lam, c, cs
     torch.cuda.empty_cache()
     return out
 

@@ -384,12 +384,13 @@ std::vector<TilePlanPass> plan_tile_passes(const tqd_circuit *c, int g_begin, in
         P.layout = lay;
         std::vector<char> blocked(n, 0);
         int blocked_in_q = 0, ngrad = 0, ndiag = 0;
+        const int max_grad = n <= TILE_SMALL_QUBITS ? TILE_MAX_GRAD_SMALL : TILE_MAX_GRAD;
         for (int g = first; g < L; ++g) {
             if (done[g]) continue;
             const GateH &gh = c->gates[g];
             const bool is_grad = c->grad_slot[g] >= 0;
             const bool diag = gate_diagonal(gh.kind);
-            bool ok = (int)P.gates.size() < TILE_MAX_GATES && (!is_grad || ngrad < TILE_MAX_GRAD) &&
+            bool ok = (int)P.gates.size() < TILE_MAX_GATES && (!is_grad || ngrad < max_grad) &&
                       (diag ? ndiag < TILE_MAX_SUBS : (int)P.gates.size() - ndiag < TILE_MAX_OPS);
             for (int a = 0; a < gh.nw && ok; ++a) ok = (diag || inQ[gh.w[a]]) && !blocked[gh.w[a]];
             if (ok) {

@@ -118,6 +118,12 @@ static_assert(sizeof(TileStage) % 4 == 0, "stages are copied to shared memory in
 enum : uint16_t { SYNC_NONE = 0, SYNC_GROUP = 1, SYNC_WARP = 2 };
 constexpr int TILE_TB = 2 * (32 + TILE_THREADS / 32);  // per-stage lane/warp table entries
 constexpr int TILE_MAX_GRAD = 32;                        // gradient ops per pass
+// States of at most this many qubits (4 tiles, so launches of at most 4 blocks,
+// where the shared memory of the gradient columns costs no occupancy) take up
+// to TILE_MAX_GRAD_SMALL gradient ops per pass: fewer, longer passes where
+// launch latency, not HBM, sets the time.
+constexpr int TILE_SMALL_QUBITS = 14;
+constexpr int TILE_MAX_GRAD_SMALL = 104;
 
 // Ring kernels (complex64): groups of 256 threads per block, plus one warp
 // that issues the TMA copies, and tile buffers in the ring.  Forward: 3 groups, 6 buffers of 32 KiB (three tiles being
