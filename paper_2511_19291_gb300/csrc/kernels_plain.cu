@@ -94,6 +94,11 @@ cudaError_t launch_reset(tqd_state *st, uint64_t j, cudaStream_t s) {
 // -------------------------------------------------------- 1-qubit dense
 // Pairs (b, b + 2^t).  For t >= 1 a unit is four amplitudes b, b+1 (bit 0
 // vectorised) and their partners; for t = 0 a unit is two adjacent pairs.
+// Complex64 with t <= 1 (n >= 6): each thread moves one 16-byte chunk (two
+// amplitudes) per access and consecutive lanes consecutive chunks, so every
+// warp access is one contiguous 512 bytes: for t = 0 the chunk is a pair; for
+// t = 1 chunks 2k and 2k + 1 are partners, held by lanes 2k and 2k + 1, which
+// exchange them with one shuffle per float.
 template <typename V>
 __global__ void __launch_bounds__(TPB) k_dense1(V *__restrict__ a, int n, int t, const RT<V> *__restrict__ mat,
                                                 int dag) {
@@ -102,6 +107,49 @@ __global__ void __launch_bounds__(TPB) k_dense1(V *__restrict__ a, int n, int t,
     const uint64_t units = (uint64_t)1 << (n - 2);
     const uint64_t S = (uint64_t)gridDim.x * blockDim.x;
     uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if constexpr (sizeof(V) == 8) {
+        if (t <= 1 && n >= 6) {
+            // chunks: 2^(n-1), a multiple of 32, and every warp starts at a
+            // multiple of 32, so the loop runs the same count in all its lanes
+            const uint64_t C = (uint64_t)1 << (n - 1);
+            const bool hi = threadIdx.x & 1;  // t = 1: this lane's chunk has bit 1 set
+            for (uint64_t c = i; c < C; c += 2 * S) {
+                const uint64_t c2 = c + S;
+                const bool two = c2 < C;
+                V x0, x1, y0, y1;
+                ld2(a + 2 * c, x0, x1);
+                if (two) ld2(a + 2 * c2, y0, y1);
+                if (t == 0) {
+                    mv2(m, x0, x1);
+                    if (two) mv2(m, y0, y1);
+                } else {
+                    // partner chunk from the neighbouring lane (all lanes take part)
+                    V p0, p1, q0 = x0, q1 = x1;
+                    p0.x = __shfl_xor_sync(0xffffffffu, x0.x, 1);
+                    p0.y = __shfl_xor_sync(0xffffffffu, x0.y, 1);
+                    p1.x = __shfl_xor_sync(0xffffffffu, x1.x, 1);
+                    p1.y = __shfl_xor_sync(0xffffffffu, x1.y, 1);
+                    // bit-1 = 0 lane: a*mine + b*partner; bit-1 = 1 lane: c*partner + d*mine
+                    x0 = hi ? cfma(m.c, p0, cmul(m.d, q0)) : cfma(m.a, q0, cmul(m.b, p0));
+                    x1 = hi ? cfma(m.c, p1, cmul(m.d, q1)) : cfma(m.a, q1, cmul(m.b, p1));
+                    if (two) {
+                        V r0, r1;
+                        q0 = y0;
+                        q1 = y1;
+                        r0.x = __shfl_xor_sync(0xffffffffu, y0.x, 1);
+                        r0.y = __shfl_xor_sync(0xffffffffu, y0.y, 1);
+                        r1.x = __shfl_xor_sync(0xffffffffu, y1.x, 1);
+                        r1.y = __shfl_xor_sync(0xffffffffu, y1.y, 1);
+                        y0 = hi ? cfma(m.c, r0, cmul(m.d, q0)) : cfma(m.a, q0, cmul(m.b, r0));
+                        y1 = hi ? cfma(m.c, r1, cmul(m.d, q1)) : cfma(m.a, q1, cmul(m.b, r1));
+                    }
+                }
+                st2(a + 2 * c, x0, x1);
+                if (two) st2(a + 2 * c2, y0, y1);
+            }
+            return;
+        }
+    }
     if (t >= 1) {
         const uint64_t T = (uint64_t)1 << t;
         for (; i < units; i += S) {
