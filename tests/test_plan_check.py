@@ -150,3 +150,36 @@ def test_qft_passes(n):
     them the bit-reversal swaps."""
     r = check(W.qft_circuit(n), np.zeros(1))
     assert r["passes"] <= -(-(n - 4) // 8) + 2, r
+
+
+@pytest.mark.parametrize("n,seed", [(17, 1), (19, 2), (20, 3)])
+def test_scattered_qubit_plans(n, seed):
+    """Dense two-qubit gates between distant qubits: passes whose first gate
+    forces a scattered qubit set (runs and gaps beyond the tensor map's five
+    dimensions, so separate box copies in one precision or both), while the
+    rest of each set avoids them; every pass still reproduces the gates."""
+    rng = W.SplitMix64(9300 + seed)
+    gates, p = [], 0
+    for layer in range(4):
+        for k in range(n // 2):
+            a = rng.randint(4, n - 1)
+            b = rng.randint(4, n - 1)
+            if a == b:
+                continue
+            gates.append(W.Gate("UNITARY2", (a, b), matrix=W.random_unitary(rng, 4)))
+            gates.append(W.Gate("RY", (a,), param=p))
+            p += 1
+        gates += [W.Gate("CNOT", (q, (q + 7) % n)) for q in range(0, n, 3)]
+    circ = W.Circuit(n, gates, p)
+    check(circ, W.config_rng(6).angles(p), seed)
+
+
+@pytest.mark.parametrize("n,layers", [(12, 4), (14, 6)])
+def test_small_state_long_passes(n, layers):
+    """States of at most 14 qubits take up to 104 angles per pass: the
+    12-qubit, 4-layer ansatz plans to its 96 angles' pass and the closing
+    CNOT ring's pass."""
+    circ = W.hea_ansatz(n, layers)
+    r = check(circ, W.config_rng(1).angles(circ.n_params))
+    if (n, layers) == (12, 4):
+        assert r["passes"] == 2, r
